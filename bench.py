@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Benchmark of the frPCA hot path on GB300.
+
+One step = one pass of the whole method over the resident 200,000 x 50,000
+power-law CSR (~20M nnz, tf-idf-like FP32 values): the device A^T rebuild, the
+Gaussian test matrix, q = 5 SpMM passes with A and A^T, LU, two eigSVDs and the
+final products (k = 100, l = 120, FP32 path, Alg. 6).  Metric: seconds per
+rank-k frPCA run (lower is better), device-timed with CUDA events.  The JSON
+line also carries the SpMM passes' HBM roofline (algorithmic bytes over their
+measured device time), an end-to-end time through the public API with host
+buffers, and the FP64 CPU oracle timed on the host cores.
+
+Multi-GPU (torchrun): every rank runs its own independent problem (weak
+scaling, no collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "powerlaw_200000x50000_deg100"
+L2_BYTES = 129 * 2**20
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, world, rank):
+    """The FP64 CPU oracle as it stands, on the host cores, same workload."""
+    if rank != 0:
+        return 0
+    import oracle
+    import synthetic
+    oracle.build()
+    w = synthetic.WORKLOADS[args.workload]
+    A = synthetic.make_workload(args.workload, seed=1)
+    vals = A.data.astype(np.float64)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.frpca(A.m, A.n, A.indptr, A.indices, vals, w["k"], w["l"], args.q, 0)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    v = float(np.mean(times))
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": "frpca_seconds", "value": v, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(args, w),
+        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+                         "sample": f"the whole workload, one frPCA run per step (q={args.q})"},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(args, w):
+    return {"workload": args.workload, "m": w["m"], "n": w["n"], "k": w["k"], "l": w["l"], "q": args.q,
+            "precision": args.precision, "alg": "Alg. 6 (m >= n)", "l2": "inputs larger than L2 (CSR alone "
+            "exceeds 129 MB), no flush between steps", "parallelism": f"independent replicas x{args.gpus}"}
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_1810_06825_gb300 as frpca
+    import synthetic
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synthetic.WORKLOADS[args.workload]
+    k, l, q = w["k"], w["l"], args.q
+    dt_np = np.float64 if args.precision == "fp64" else np.float32
+    A = synthetic.make_workload(args.workload, seed=1 + rank, dtype=dt_np)
+    indptr = torch.from_numpy(A.indptr).to(dev)
+    indices = torch.from_numpy(A.indices).to(dev)
+    values = torch.from_numpy(A.data).to(dev)
+    stream = torch.cuda.current_stream()
+    mat = frpca.FrPCA(indptr, indices, values, (A.m, A.n), stream=stream)
+    tdt = torch.float64 if args.precision == "fp64" else torch.float32
+    U = torch.empty((A.m, k), dtype=tdt, device=dev)
+    S = torch.empty((k,), dtype=torch.float64, device=dev)
+    V = torch.empty((A.n, k), dtype=tdt, device=dev)
+
+    def step():
+        mat.refresh()
+        mat.run(k, l, q, seed=0, precision=args.precision, out=(U, S, V), sync=False)
+
+    for _ in range(args.warmup):
+        step()
+    frpca.frpca_sync(mat.handle)
+    mat.set_timing(True)
+    mat.reset_stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(world)
+    clk = clocks.stop()
+    frpca.frpca_sync(mat.handle)
+    ms = e0.elapsed_time(e1) / args.steps
+    st = mat.stats()
+    ms_max = _max_over_ranks(ms, world)
+
+    # End to end through the public API: pinned host CSR -> device, create the
+    # handle (validation + A^T + plan), run, read U, S, V back.
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+        h_ip, h_ix, h_v = pin(A.indptr), pin(A.indices), pin(A.data)
+        h_U = torch.empty((A.m, k), dtype=tdt).pin_memory()
+        h_S = torch.empty((k,), dtype=torch.float64).pin_memory()
+        h_V = torch.empty((A.n, k), dtype=tdt).pin_memory()
+        h2d = h_ip.numel() * 8 + h_ix.numel() * 4 + h_v.numel() * h_v.element_size()
+        d2h = h_U.numel() * h_U.element_size() + h_S.numel() * 8 + h_V.numel() * h_V.element_size()
+
+        def e2e_step():
+            d_ip = h_ip.to(dev, non_blocking=True)
+            d_ix = h_ix.to(dev, non_blocking=True)
+            d_v = h_v.to(dev, non_blocking=True)
+            m2 = frpca.FrPCA(d_ip, d_ix, d_v, (A.m, A.n), stream=stream)
+            Ud, Sd, Vd = m2.run(k, l, q, seed=0, precision=args.precision, sync=False)
+            h_U.copy_(Ud, non_blocking=True)
+            h_S.copy_(Sd, non_blocking=True)
+            h_V.copy_(Vd, non_blocking=True)
+            frpca.frpca_sync(m2.handle)
+            m2.close()
+
+        e2e_step()
+        n_e2e = max(1, min(args.steps, 5))
+        _barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = _max_over_ranks((time.perf_counter() - t0) / n_e2e, world)
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": n_e2e}
+
+    peak, peak_kind = _peaks()
+    spmm_ms_per_pass = st["spmm_ms"] / max(st["spmm_passes"], 1)
+    achieved = (st["spmm_bytes"] / max(st["spmm_passes"], 1)) / (spmm_ms_per_pass * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "spmm_kernel (+ fix-up), one SpMM pass", "achieved": achieved,
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "ms_per_pass": spmm_ms_per_pass,
+                "bytes_per_pass": st["spmm_bytes"] / max(st["spmm_passes"], 1),
+                "fp32_tflops": st["spmm_flops"] / max(st["spmm_ms"], 1e-9) / 1e9}
+    phases = {key: st[key] / args.steps for key in ("spmm_ms", "lu_ms", "gram_ms", "eig_ms", "apply_ms",
+                                                    "gaussian_ms", "transpose_ms", "finish_ms")}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        vals = A.data.astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.frpca(A.m, A.n, A.indptr, A.indices, vals, k, l, q, 0)
+        cpu_s = time.perf_counter() - t0
+        cpu = {"value": cpu_s, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"the whole workload, one FP64 frPCA run (q={q})"}
+
+    if rank == 0:
+        line = {
+            "metric": "frpca_seconds", "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+            "config": _config(args, w), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(st["kernel_launches"]), "clocks": clk, "phases_ms_per_step": phases,
+            "nnz": int(A.nnz),
+        }
+        print(json.dumps(line), flush=True)
+    mat.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--q", type=int, default=5)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = _dist()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

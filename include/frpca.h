@@ -1,0 +1,195 @@
+/*
+ * frpca.h -- C ABI of the GB300 (sm_103a) implementation of fast randomized
+ * PCA for sparse data: frPCA (Alg. 5) and frPCAt (Alg. 6) of Feng, Xie, Song,
+ * Yu and Tang, "Fast Randomized PCA for Sparse Data", ACML 2018.
+ *
+ * Given a sparse m x n matrix A (CSR), frpca_run computes an approximate rank-k
+ * truncated SVD A ~ U diag(S) V^T (Sec. 2.1, Eq. 2) with q passes over A
+ * (Sec. 3.3).  Every step runs in this library's CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point:
+ *  - Dense blocks are row-major with an explicit leading dimension ld (in
+ *    elements).  Device pointers to dense blocks must be 16-byte aligned and ld
+ *    a multiple of 4 (FP32) or 2 (FP64), so each row starts on 16 bytes.
+ *  - "stream" is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Work is enqueued on it; functions that report a device-detected
+ *    status synchronize that stream before returning (noted per function).
+ *  - Ownership: the library never frees caller memory.  Device buffers the
+ *    library allocates belong to the handle and are freed by frpca_destroy.
+ *  - Errors: every function returns an frpca_status and never aborts; the
+ *    message of the last failure is available from frpca_last_error.  Outputs
+ *    are unspecified when a call fails.
+ */
+#ifndef FRPCA_H
+#define FRPCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum frpca_status {
+    FRPCA_OK = 0,
+    FRPCA_ERR_INVALID_ARG = 1,      /* k < 1, k > l, l > min(m,n), q < 2, bad sizes or alignment  */
+    FRPCA_ERR_INVALID_CSR = 2,      /* rowptr[0] != 0, non-monotone rowptr, rowptr[m] != nnz,
+                                       column out of [0,n), unsorted or repeated column in a row    */
+    FRPCA_ERR_OOM = 3,              /* device allocation failed                                    */
+    FRPCA_ERR_CUDA = 4,             /* a CUDA runtime call failed (message in frpca_last_error)    */
+    FRPCA_ERR_SINGULAR_PIVOT = 5,   /* LU found a column whose remaining entries are all zero      */
+    FRPCA_ERR_RANK_DEFICIENT = 6,   /* eigSVD met an eigenvalue <= l*eps*lambda_max (Sec. 3.1)     */
+    FRPCA_ERR_TIMEOUT = 7,          /* a bounded device-side wait ran out                          */
+    FRPCA_ERR_NOT_CONVERGED = 8,    /* the l x l eigensolver did not converge                      */
+    FRPCA_ERR_UNSUPPORTED = 9       /* size outside what this build supports (e.g. l > 160)        */
+} frpca_status;
+
+typedef enum frpca_dtype { FRPCA_F32 = 0, FRPCA_F64 = 1 } frpca_dtype;
+
+/* Arithmetic of a run.  FP64: every step in double.  FP32: SpMM, LU, Gram and
+ * the apply step in float; the l x l eigendecomposition always returns double
+ * precision eigenpairs.  FP32_SPLITGRAM: FP32 with the Gram matrix of eigSVD
+ * formed on the tensor cores from split-BF16 operands. */
+typedef enum frpca_precision {
+    FRPCA_PREC_FP64 = 0,
+    FRPCA_PREC_FP32 = 1,
+    FRPCA_PREC_FP32_SPLITGRAM = 2
+} frpca_precision;
+
+typedef struct frpca_ctx *frpca_handle;
+
+/* Sparse matrix A in CSR form: row i holds entries rowptr[i] .. rowptr[i+1]-1,
+ * with column indices strictly increasing inside a row (explicit zeros are
+ * allowed and kept).  Sec. 3.2 notes the row-compressed storage; the
+ * transpose that Alg. 5/6 multiply by is built on the device. */
+typedef struct frpca_csr {
+    int64_t m, n, nnz;        /* 1 <= m, n < 2^31; 0 <= nnz < 2^31                         */
+    const int64_t *rowptr;    /* m + 1 entries                                              */
+    const int32_t *colidx;    /* nnz entries                                                */
+    const void *values;       /* nnz entries of type dtype                                  */
+    frpca_dtype dtype;
+    int on_device;            /* 1: the three arrays are device pointers; 0: host pointers  */
+} frpca_csr;
+
+typedef struct frpca_create_opts {
+    void *stream;             /* stream of every call on the handle                         */
+    int borrow;               /* on_device only: 1 = use the caller's arrays in place (they
+                                 must stay valid until frpca_destroy); 0 = copy them        */
+    int validate;             /* 1 = check the CSR structure (on the device), 0 = trust it  */
+} frpca_create_opts;
+
+/* Creates a handle.  csr may be NULL: the handle then serves only the
+ * step-level entry points below that take no matrix.  With a matrix, the
+ * structure is validated (FRPCA_ERR_INVALID_CSR), values are copied or borrowed,
+ * and the CSR of A^T is built on the device (stable: each row of A^T lists the
+ * rows of A in ascending order).  Synchronizes the stream. */
+frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, frpca_handle *out);
+
+/* Frees every device buffer the handle owns.  Accepts NULL. */
+frpca_status frpca_destroy(frpca_handle h);
+
+/* Message of the last failure on h (h == NULL: the calling thread's last
+ * failure of frpca_create).  Valid until the next call on the same handle. */
+const char *frpca_last_error(frpca_handle h);
+
+typedef struct frpca_run_opts {
+    int k;                      /* rank, 1 <= k <= l                                        */
+    int l;                      /* k + oversampling s, l <= min(m, n), l <= 160             */
+    int q;                      /* passes over A, q >= 2 (Alg. 5/6 "pass parameter")        */
+    uint64_t seed;              /* Philox key of the Gaussian test matrix                   */
+    frpca_precision precision;
+    int alg;                    /* 0: shape rule (Alg. 6 if m >= n else Alg. 5); 5 or 6     */
+} frpca_run_opts;
+
+/* The method (Alg. 5 / Alg. 6).  Outputs are device buffers owned by the
+ * caller: U (m x k, ld k) and V (n x k, ld k) of type float for the FP32
+ * precisions and double for FP64; S (k doubles) in descending order.
+ * Sign convention: for each j, the entry of largest magnitude (smallest index
+ * on ties) of the singular vector of length min(m, n) -- v_j when m >= n, u_j
+ * otherwise -- is positive.  Synchronizes the handle's stream once to read the
+ * device status. */
+frpca_status frpca_run(frpca_handle h, const frpca_run_opts *opts, void *U, double *S, void *V);
+
+/* Same as frpca_run without the final synchronization: the status of the
+ * device-side checks is returned by the next frpca_sync(h). */
+frpca_status frpca_run_async(frpca_handle h, const frpca_run_opts *opts, void *U, double *S, void *V);
+frpca_status frpca_sync(frpca_handle h);
+
+/* Rebuilds the device CSR of A^T from A (same structure; values may have been
+ * changed in place in borrowed arrays).  Synchronizes. */
+frpca_status frpca_refresh(frpca_handle h);
+
+/* ---- instrumentation --------------------------------------------------------- */
+
+/* Per-phase device time of the runs on a handle, measured with CUDA events on
+ * its stream while timing is enabled.  spmm_bytes counts the algorithmic bytes
+ * of the passes (CSR arrays once, the input and output blocks once each;
+ * repeated gathers of input rows not counted). */
+typedef struct frpca_stats {
+    int64_t runs;
+    int64_t kernel_launches;   /* kernels this library launched on the handle    */
+    int64_t spmm_passes;
+    double spmm_ms, spmm_bytes, spmm_flops;
+    int64_t lu_calls;
+    double lu_ms;
+    int64_t eigsvd_calls;
+    double gram_ms, eig_ms, apply_ms;
+    double gaussian_ms, transpose_ms, finish_ms;
+} frpca_stats;
+
+/* enable != 0 records events around every phase (adds a few microseconds per
+ * phase); frpca_get_stats synchronizes and returns the sums since the last
+ * frpca_reset_stats. */
+frpca_status frpca_set_timing(frpca_handle h, int enable);
+frpca_status frpca_get_stats(frpca_handle h, frpca_stats *out);
+frpca_status frpca_reset_stats(frpca_handle h);
+
+/* ---- step-level entry points (device pointers, handle's stream) ------------ */
+
+/* Gaussian test matrix randn (Sec. 2.2; drawn as in Alg. 5/6 steps 2 and 6):
+ * out is R x l (ld) of dtype dt.  Generator: Philox4x64-10 (Salmon et al.,
+ * SC'11), key (seed, 0), counter (e / 4, 0, 0, 0) for element e = row * l + col,
+ * word e mod 4; a word x gives u = (floor(x / 2^12) + 1/2) 2^-52; Box-Muller on
+ * word pairs (0,1), (2,3): sqrt(-2 ln u_a) (cos, sin)(2 pi u_b).  FP32 output
+ * evaluates the same formula in float arithmetic. */
+frpca_status frpca_gaussian(frpca_handle h, int64_t R, int l, int64_t ld, uint64_t seed,
+                            frpca_dtype dt, void *out);
+
+/* Y = A X (trans = 0, X n x l, Y m x l) or Y = A^T X (trans = 1, X m x l,
+ * Y n x l) with the handle's matrix; dt must match the precision the values
+ * are held in (values are converted once and cached if needed). */
+frpca_status frpca_spmm(frpca_handle h, int trans, int l, const void *X, int64_t ldx,
+                        void *Y, int64_t ldy, frpca_dtype dt);
+
+/* Copies the device-built CSR of A^T (n + 1, nnz, nnz entries) into caller
+ * device buffers; values in the dtype A was given in. */
+frpca_status frpca_get_transpose(frpca_handle h, int64_t *rowptrT, int32_t *colidxT, void *valuesT);
+
+/* lu() of Alg. 5/6 (Lemma 3, Eq. 8): in-place LU with partial pivoting of the
+ * R x l block M (R >= l), returning P^T L in M's original row order: the pivot
+ * row of column j has 1 at j and 0 to its right; the pivot of column j is the
+ * not-yet-pivoted row of largest |M(i,j)|, the smallest row index on equal
+ * magnitudes.  piv (nullable, device, l int64) receives the pivot rows.
+ * Synchronizes; FRPCA_ERR_SINGULAR_PIVOT when a column has no nonzero pivot. */
+frpca_status frpca_lu(frpca_handle h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv);
+
+/* Step 1 of eigSVD (Alg. 2): B = M^T M, l x l double (ld l), M R x l.  FP32
+ * input is accumulated in float inside a tile of rows and in double across
+ * tiles; FP64 input in double throughout. */
+frpca_status frpca_gram(frpca_handle h, int64_t R, int l, const void *M, int64_t ld, frpca_dtype dt, double *B);
+
+/* Step 2 of eigSVD (Alg. 2): eigenvalues w (ascending) and orthonormal
+ * eigenvectors V (n x n, column c for w[c]) of the symmetric n x n double
+ * matrix B, n <= 160.  Synchronizes; FRPCA_ERR_NOT_CONVERGED on failure. */
+frpca_status frpca_eig(frpca_handle h, int n, const double *B, double *w, double *V);
+
+/* eigSVD (Alg. 2) of the R x l block M, R >= l: S ascending (l doubles),
+ * V (l x l doubles), and U = M V diag(1./S) written over M.  Synchronizes;
+ * FRPCA_ERR_RANK_DEFICIENT as in Sec. 3.1. */
+frpca_status frpca_eigsvd(frpca_handle h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt,
+                          double *S, double *V);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FRPCA_H */

@@ -1,0 +1,393 @@
+"""frPCA / frPCAt on GB300: Python binding of the ``libfrpca.so`` C ABI.
+
+Fast randomized PCA for sparse data (Feng, Xie, Song, Yu, Tang, ACML 2018):
+``frpca_run`` computes a rank-k truncated SVD of a CSR matrix with q passes
+over it (Alg. 5 for wide, Alg. 6 for tall matrices), every step in this
+package's CUDA kernels.  This module only marshals arguments: the functions
+named like the C entry points take raw device pointers; ``FrPCA`` and the
+helpers below take torch CUDA tensors and pass their pointers and the current
+stream.  There is no CPU fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfrpca.so")
+
+FRPCA_OK = 0
+STATUS_NAMES = {
+    0: "OK", 1: "INVALID_ARG", 2: "INVALID_CSR", 3: "OOM", 4: "CUDA", 5: "SINGULAR_PIVOT",
+    6: "RANK_DEFICIENT", 7: "TIMEOUT", 8: "NOT_CONVERGED", 9: "UNSUPPORTED",
+}
+FRPCA_F32, FRPCA_F64 = 0, 1
+PREC = {"fp64": 0, "fp32": 1, "fp32_splitgram": 2}
+
+EXPORTED = [
+    "frpca_create", "frpca_destroy", "frpca_last_error", "frpca_run", "frpca_run_async", "frpca_sync",
+    "frpca_refresh", "frpca_set_timing", "frpca_get_stats", "frpca_reset_stats",
+    "frpca_gaussian", "frpca_spmm", "frpca_get_transpose", "frpca_lu", "frpca_gram", "frpca_eig",
+    "frpca_eigsvd",
+]
+
+
+class FrpcaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class frpca_csr(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("values", ctypes.c_void_p),
+                ("dtype", ctypes.c_int), ("on_device", ctypes.c_int)]
+
+
+class frpca_create_opts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("borrow", ctypes.c_int), ("validate", ctypes.c_int)]
+
+
+class frpca_run_opts(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("l", ctypes.c_int), ("q", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int), ("alg", ctypes.c_int)]
+
+
+class frpca_stats(ctypes.Structure):
+    _fields_ = [("runs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("spmm_passes", ctypes.c_int64),
+                ("spmm_ms", ctypes.c_double), ("spmm_bytes", ctypes.c_double), ("spmm_flops", ctypes.c_double),
+                ("lu_calls", ctypes.c_int64), ("lu_ms", ctypes.c_double), ("eigsvd_calls", ctypes.c_int64),
+                ("gram_ms", ctypes.c_double), ("eig_ms", ctypes.c_double), ("apply_ms", ctypes.c_double),
+                ("gaussian_ms", ctypes.c_double), ("transpose_ms", ctypes.c_double), ("finish_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """The loaded C library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1810_06825_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, I64, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "frpca_create": [P, P, P],
+        "frpca_destroy": [P],
+        "frpca_run": [P, P, P, P, P],
+        "frpca_run_async": [P, P, P, P, P],
+        "frpca_sync": [P],
+        "frpca_refresh": [P],
+        "frpca_set_timing": [P, I],
+        "frpca_get_stats": [P, P],
+        "frpca_reset_stats": [P],
+        "frpca_gaussian": [P, I64, I, I64, U64, I, P],
+        "frpca_spmm": [P, I, I, P, I64, P, I64, I],
+        "frpca_get_transpose": [P, P, P, P],
+        "frpca_lu": [P, I64, I, P, I64, I, P],
+        "frpca_gram": [P, I64, I, P, I64, I, P],
+        "frpca_eig": [P, I, P, P, P],
+        "frpca_eigsvd": [P, I64, I, P, I64, I, P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.frpca_last_error.argtypes = [P]
+    lib.frpca_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int, handle) -> None:
+    if status != FRPCA_OK:
+        msg = library().frpca_last_error(handle)
+        raise FrpcaError(status, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------- raw C-ABI calls
+def frpca_create(csr, opts) -> int:
+    h = ctypes.c_void_p()
+    st = library().frpca_create(ctypes.byref(csr) if csr is not None else None, ctypes.byref(opts), ctypes.byref(h))
+    _check(st, None)
+    return h.value
+
+
+def frpca_destroy(h) -> None:
+    library().frpca_destroy(h)
+
+
+def frpca_last_error(h) -> str:
+    m = library().frpca_last_error(h)
+    return m.decode() if m else ""
+
+
+def frpca_run(h, opts, U, S, V) -> None:
+    _check(library().frpca_run(h, ctypes.byref(opts), U, S, V), h)
+
+
+def frpca_run_async(h, opts, U, S, V) -> None:
+    _check(library().frpca_run_async(h, ctypes.byref(opts), U, S, V), h)
+
+
+def frpca_sync(h) -> None:
+    _check(library().frpca_sync(h), h)
+
+
+def frpca_refresh(h) -> None:
+    _check(library().frpca_refresh(h), h)
+
+
+def frpca_set_timing(h, enable: bool) -> None:
+    _check(library().frpca_set_timing(h, 1 if enable else 0), h)
+
+
+def frpca_get_stats(h) -> frpca_stats:
+    st = frpca_stats()
+    _check(library().frpca_get_stats(h, ctypes.byref(st)), h)
+    return st
+
+
+def frpca_reset_stats(h) -> None:
+    _check(library().frpca_reset_stats(h), h)
+
+
+def frpca_gaussian(h, R, l, ld, seed, dtype, out) -> None:
+    _check(library().frpca_gaussian(h, R, l, ld, seed, dtype, out), h)
+
+
+def frpca_spmm(h, trans, l, X, ldx, Y, ldy, dtype) -> None:
+    _check(library().frpca_spmm(h, trans, l, X, ldx, Y, ldy, dtype), h)
+
+
+def frpca_get_transpose(h, rowptrT, colidxT, valuesT) -> None:
+    _check(library().frpca_get_transpose(h, rowptrT, colidxT, valuesT), h)
+
+
+def frpca_lu(h, R, l, M, ld, dtype, piv) -> None:
+    _check(library().frpca_lu(h, R, l, M, ld, dtype, piv), h)
+
+
+def frpca_gram(h, R, l, M, ld, dtype, B) -> None:
+    _check(library().frpca_gram(h, R, l, M, ld, dtype, B), h)
+
+
+def frpca_eig(h, n, B, w, V) -> None:
+    _check(library().frpca_eig(h, n, B, w, V), h)
+
+
+def frpca_eigsvd(h, R, l, M, ld, dtype, S, V) -> None:
+    _check(library().frpca_eigsvd(h, R, l, M, ld, dtype, S, V), h)
+
+
+# ---------------------------------------------------------------- torch helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return FRPCA_F32
+    if t.dtype == torch.float64:
+        return FRPCA_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if not t.is_cuda:
+            raise ValueError("tensors must be on a CUDA device")
+
+
+def padded_ld(l: int) -> int:
+    """Row length (elements) used for dense blocks: a multiple of 4, so every row starts on 16 bytes."""
+    return (l + 3) // 4 * 4
+
+
+def empty_block(R: int, l: int, dtype, device) -> "torch.Tensor":
+    """R x l view of a zeroed R x padded_ld(l) buffer (rows 16-byte aligned)."""
+    torch = _torch()
+    return torch.zeros((R, padded_ld(l)), dtype=dtype, device=device)[:, :l]
+
+
+class _Context:
+    """Matrix-less handle per (device, stream) for the step-level entry points."""
+    _cache: dict = {}
+
+    @classmethod
+    def get(cls, stream=None) -> int:
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        key = (s.device.index, s.cuda_stream)
+        h = cls._cache.get(key)
+        if h is None:
+            opts = frpca_create_opts(stream=s.cuda_stream, borrow=0, validate=1)
+            h = frpca_create(None, opts)
+            cls._cache[key] = h
+        return h
+
+
+class FrPCA:
+    """A sparse matrix resident on the GPU, ready for frPCA runs.
+
+    ``indptr`` (int64, m+1), ``indices`` (int32, nnz, sorted and unique per
+    row) and ``values`` (float32/float64, nnz) are CUDA tensors; by default they
+    are borrowed (kept alive by this object) and A^T is built on the device.
+    """
+
+    def __init__(self, indptr, indices, values, shape, stream=None, borrow=True, validate=True):
+        torch = _torch()
+        _need_cuda(indptr, indices, values)
+        self.m, self.n = int(shape[0]), int(shape[1])
+        self.indptr = indptr.contiguous().to(torch.int64)
+        self.indices = indices.contiguous().to(torch.int32)
+        self.values = values.contiguous()
+        self.dtype = self.values.dtype
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        csr = frpca_csr(m=self.m, n=self.n, nnz=int(self.indices.numel()), rowptr=self.indptr.data_ptr(),
+                        colidx=self.indices.data_ptr() if self.indices.numel() else None,
+                        values=self.values.data_ptr() if self.values.numel() else None,
+                        dtype=_dtype_code(self.values), on_device=1)
+        opts = frpca_create_opts(stream=self.stream.cuda_stream, borrow=1 if borrow else 0,
+                                 validate=1 if validate else 0)
+        self.handle = frpca_create(csr, opts)
+
+    @classmethod
+    def from_csr(cls, csr, device="cuda", dtype=None, **kw):
+        """From an object with m, n, indptr, indices, data (numpy), e.g. synthetic.CSR."""
+        torch = _torch()
+        data = csr.data if dtype is None else csr.data.astype(dtype)
+        return cls(torch.from_numpy(csr.indptr).to(device), torch.from_numpy(csr.indices).to(device),
+                   torch.from_numpy(data).to(device), (csr.m, csr.n), **kw)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.indices.numel())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            frpca_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, k: int, l: int, q: int, seed: int = 0, precision: str = "fp32", alg: int = 0, out=None,
+            sync: bool = True):
+        """Rank-k frPCA (Alg. 5/6); returns (U m x k, S k descending float64, V n x k)."""
+        torch = _torch()
+        dt = torch.float64 if precision == "fp64" else torch.float32
+        dev = self.values.device
+        if out is None:
+            U = torch.empty((self.m, k), dtype=dt, device=dev)
+            S = torch.empty((k,), dtype=torch.float64, device=dev)
+            V = torch.empty((self.n, k), dtype=dt, device=dev)
+        else:
+            U, S, V = out
+        opts = frpca_run_opts(k=k, l=l, q=q, seed=seed, precision=PREC[precision], alg=alg)
+        fn = frpca_run if sync else frpca_run_async
+        fn(self.handle, opts, U.data_ptr(), S.data_ptr(), V.data_ptr())
+        return U, S, V
+
+    def spmm(self, X, trans: bool = False, out=None):
+        """A X (or A^T X) for a dense block X whose rows start on 16 bytes."""
+        torch = _torch()
+        l = X.shape[1]
+        rows = self.n if trans else self.m
+        Y = out if out is not None else empty_block(rows, l, X.dtype, X.device)
+        frpca_spmm(self.handle, 1 if trans else 0, l, X.data_ptr(), X.stride(0), Y.data_ptr(), Y.stride(0),
+                   _dtype_code(X))
+        return Y
+
+    def refresh(self):
+        """Rebuild A^T on the device (after the borrowed values changed in place)."""
+        frpca_refresh(self.handle)
+
+    def set_timing(self, enable: bool = True):
+        frpca_set_timing(self.handle, enable)
+
+    def stats(self) -> dict:
+        return frpca_get_stats(self.handle).as_dict()
+
+    def reset_stats(self):
+        frpca_reset_stats(self.handle)
+
+    def transpose(self):
+        torch = _torch()
+        dev = self.values.device
+        pT = torch.empty(self.n + 1, dtype=torch.int64, device=dev)
+        cT = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=dev)
+        vT = torch.empty(max(self.nnz, 1), dtype=self.dtype, device=dev)
+        frpca_get_transpose(self.handle, pT.data_ptr(), cT.data_ptr(), vT.data_ptr())
+        return pT, cT[: self.nnz], vT[: self.nnz]
+
+
+def gaussian(R: int, l: int, seed: int, dtype=None, device="cuda"):
+    torch = _torch()
+    dtype = dtype or torch.float64
+    out = empty_block(R, l, dtype, device)
+    frpca_gaussian(_Context.get(), R, l, out.stride(0), seed, _dtype_code(out), out.data_ptr())
+    return out
+
+
+def lu(M):
+    """P^T L of Alg. 5/6's lu() (in a copy of M) and the pivot rows."""
+    torch = _torch()
+    _need_cuda(M)
+    R, l = M.shape
+    A = empty_block(R, l, M.dtype, M.device)
+    A.copy_(M)
+    piv = torch.empty(l, dtype=torch.int64, device=M.device)
+    frpca_lu(_Context.get(), R, l, A.data_ptr(), A.stride(0), _dtype_code(A), piv.data_ptr())
+    return A, piv
+
+
+def gram(M):
+    torch = _torch()
+    _need_cuda(M)
+    R, l = M.shape
+    if M.stride(1) != 1:
+        M = M.contiguous()
+    B = torch.empty((l, l), dtype=torch.float64, device=M.device)
+    frpca_gram(_Context.get(), R, l, M.data_ptr(), M.stride(0), _dtype_code(M), B.data_ptr())
+    return B
+
+
+def eig(B):
+    torch = _torch()
+    _need_cuda(B)
+    n = B.shape[0]
+    B = B.to(torch.float64).contiguous()
+    w = torch.empty(n, dtype=torch.float64, device=B.device)
+    V = torch.empty((n, n), dtype=torch.float64, device=B.device)
+    frpca_eig(_Context.get(), n, B.data_ptr(), w.data_ptr(), V.data_ptr())
+    return w, V
+
+
+def eigsvd(M):
+    """Alg. 2 on a copy of M: (U, S ascending, V)."""
+    torch = _torch()
+    _need_cuda(M)
+    R, l = M.shape
+    U = empty_block(R, l, M.dtype, M.device)
+    U.copy_(M)
+    S = torch.empty(l, dtype=torch.float64, device=M.device)
+    V = torch.empty((l, l), dtype=torch.float64, device=M.device)
+    frpca_eigsvd(_Context.get(), R, l, U.data_ptr(), U.stride(0), _dtype_code(U), S.data_ptr(), V.data_ptr())
+    return U, S, V

@@ -1,0 +1,218 @@
+// apply.cu -- step 5 of eigSVD (Alg. 2), U = M V spdiags(1./S), and the final
+// products of Alg. 5/6 (U = U^(:, ind), V = Q V^(:, ind) with
+// ind = k+s : -1 : s+1), plus the sign convention of the outputs.
+//
+// Y = M W with M tall (R x l) and W small (l x kout): a persistent grid walks
+// row tiles; each block keeps W (converted to the block's type) in shared
+// memory for all its tiles and stages one tile of M rows at a time, so M is
+// read once and may be overwritten in place by Y.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace frpca {
+namespace {
+
+constexpr int kApplyThreads = 256;
+
+// W[a][j] = V[a][col_j] * (scale ? 1/sqrt(w[col_j]) : 1) * (sign ? sign[j] : 1)
+__global__ void make_w_kernel(int l, int kout, const double *__restrict__ w, const double *__restrict__ V,
+                              int descending, int scale, const double *__restrict__ sign, frpca_dtype dt, void *W,
+                              double *__restrict__ S_out, int *status) {
+    if (scale && threadIdx.x == 0 && blockIdx.x == 0) {
+        // Sec. 3.1: eigSVD needs full column rank; refuse tiny or non-finite eigenvalues.
+        const double lmax = w[l - 1];
+        for (int c = 0; c < l; ++c)
+            if (!isfinite(w[c]) || !(w[c] > (double)l * 2.220446049250313e-16 * lmax))
+                set_status(status, FRPCA_ERR_RANK_DEFICIENT);
+    }
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < l * kout; idx += gridDim.x * blockDim.x) {
+        const int a = idx / kout, j = idx - a * kout;
+        const int col = descending ? l - 1 - j : j;
+        double v = V[a * l + col];
+        if (scale) v *= 1.0 / sqrt(w[col]);
+        if (sign) v *= sign[j];
+        if (dt == FRPCA_F32)
+            ((float *)W)[idx] = (float)v;
+        else
+            ((double *)W)[idx] = v;
+        if (S_out && a == 0) S_out[j] = sqrt(w[col]);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kApplyThreads)
+apply_kernel(int64_t R, int l, const T *M, int64_t ldm, const T *__restrict__ W, int kout, T *Y, int64_t ldy,
+             int tile_rows) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int kp = (int)round_up(kout, 4);
+    T *Ws = reinterpret_cast<T *>(smem_raw);       // l x kp
+    T *Ms = Ws + (size_t)l * kp;                    // tile_rows x l
+    for (int idx = threadIdx.x; idx < l * kp; idx += kApplyThreads) {
+        const int a = idx / kp, j = idx - a * kp;
+        Ws[idx] = (j < kout) ? W[a * kout + j] : T(0);
+    }
+    const int groups = kp / 4;
+    const int64_t ntile = ceil_div(R, tile_rows);
+    for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
+        const int64_t row0 = t * tile_rows;
+        const int rows = (int)std::min<int64_t>(tile_rows, R - row0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < rows * l; idx += kApplyThreads) {
+            const int r = idx / l, a = idx - r * l;
+            Ms[idx] = M[(row0 + r) * ldm + a];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < rows * groups; idx += kApplyThreads) {
+            const int r = idx / groups, g = idx - r * groups;
+            const T *mr = Ms + r * l;
+            T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+            for (int a = 0; a < l; ++a) {
+                const T m = mr[a];
+                const T *wr = Ws + a * kp + 4 * g;
+                acc0 = fma(m, wr[0], acc0);
+                acc1 = fma(m, wr[1], acc1);
+                acc2 = fma(m, wr[2], acc2);
+                acc3 = fma(m, wr[3], acc3);
+            }
+            T *yr = Y + (row0 + r) * ldy + 4 * g;
+            const int j0 = 4 * g;
+            if (j0 + 0 < kout) yr[0] = acc0;
+            if (j0 + 1 < kout) yr[1] = acc1;
+            if (j0 + 2 < kout) yr[2] = acc2;
+            if (j0 + 3 < kout) yr[3] = acc3;
+        }
+    }
+}
+
+// Per block: for every column j, the largest |X(i,j)| over the block's rows,
+// ties to the smaller i; partial (absval, row, value sign) per block.
+struct ColBest {
+    double absval;
+    int64_t row;
+    double sgn;
+};
+
+__device__ inline bool col_better(const ColBest &a, const ColBest &b) {
+    if (a.row < 0) return false;
+    if (b.row < 0) return true;
+    return a.absval > b.absval || (a.absval == b.absval && a.row < b.row);
+}
+
+template <typename T>
+__global__ void col_best_kernel(int64_t R, int k, const T *__restrict__ X, int64_t ld, ColBest *__restrict__ part) {
+    const int64_t G = gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * R / G, r1 = (int64_t)(blockIdx.x + 1) * R / G;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        ColBest b{-1.0, -1, 1.0};
+        for (int64_t i = r0; i < r1; ++i) {
+            const double v = (double)X[i * ld + j];
+            ColBest c{fabs(v), i, v < 0 ? -1.0 : 1.0};
+            if (col_better(c, b)) b = c;
+        }
+        part[(int64_t)blockIdx.x * k + j] = b;
+    }
+}
+
+__global__ void col_sign_kernel(int k, int nparts, const ColBest *__restrict__ part, double *__restrict__ sign) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
+        ColBest b{-1.0, -1, 1.0};
+        for (int p = 0; p < nparts; ++p)
+            if (col_better(part[(int64_t)p * k + j], b)) b = part[(int64_t)p * k + j];
+        sign[j] = b.sgn;
+    }
+}
+
+template <typename T>
+__global__ void scale_columns_kernel(int64_t R, int k, T *X, int64_t ld, const double *__restrict__ sign) {
+    const int64_t total = R * k;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / k;
+        const int j = (int)(idx - i * k);
+        if (sign[j] < 0) X[i * ld + j] = -X[i * ld + j];
+    }
+}
+
+int sign_blocks(int num_sms) { return 4 * num_sms; }
+
+}  // namespace
+
+cudaError_t launch_make_w(int l, int kout, const double *w, const double *V, int descending, int scale,
+                          const double *sign, frpca_dtype dt, void *W, double *S_out, int *d_status, cudaStream_t s) {
+    make_w_kernel<<<(l * kout + 255) / 256, 256, 0, s>>>(l, kout, w, V, descending, scale, sign, dt, W, S_out,
+                                                         d_status); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply(int64_t R, int l, const void *M, int64_t ldm, const void *W, int kout, void *Y, int64_t ldy,
+                         frpca_dtype dt, cudaStream_t s) {
+    if (R == 0) return cudaSuccess;
+    const size_t es = dt == FRPCA_F32 ? 4 : 8;
+    const int kp = (int)round_up(kout, 4);
+    const size_t wbytes = es * (size_t)l * kp;
+    // Largest tile that fits next to W in shared memory.
+    const size_t budget = 220 * 1024;
+    if (wbytes + es * l * 8 > budget) return cudaErrorInvalidValue;
+    int tile = (int)std::min<size_t>(64, (budget - wbytes) / (es * l));
+    tile = std::max(8, tile - tile % 8);
+    const size_t smem = wbytes + es * (size_t)tile * l;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ntile = ceil_div(R, tile);
+    cudaError_t e;
+    if (dt == FRPCA_F32) {
+        if ((e = cudaFuncSetAttribute(apply_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        int per = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_kernel<float>, kApplyThreads, smem);
+        const int64_t G = std::max<int64_t>(1, std::min<int64_t>(ntile, (int64_t)std::max(per, 1) * sms));
+        apply_kernel<float><<<(unsigned)G, kApplyThreads, smem, s>>>(R, l, (const float *)M, ldm, (const float *)W,
+                                                                    kout, (float *)Y, ldy, tile); count_launch();
+    } else {
+        if ((e = cudaFuncSetAttribute(apply_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        int per = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_kernel<double>, kApplyThreads, smem);
+        const int64_t G = std::max<int64_t>(1, std::min<int64_t>(ntile, (int64_t)std::max(per, 1) * sms));
+        apply_kernel<double><<<(unsigned)G, kApplyThreads, smem, s>>>(R, l, (const double *)M, ldm,
+                                                                     (const double *)W, kout, (double *)Y, ldy, tile); count_launch();
+    }
+    return cudaGetLastError();
+}
+
+size_t sign_workspace_bytes(int k, int num_sms) { return sizeof(ColBest) * (size_t)sign_blocks(num_sms) * k; }
+
+cudaError_t launch_column_signs(int64_t R, int k, const void *X, int64_t ld, frpca_dtype dt, double *sign, void *ws,
+                                int num_sms, cudaStream_t s) {
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(sign_blocks(num_sms), R));
+    ColBest *part = (ColBest *)ws;
+    if (dt == FRPCA_F32)
+        col_best_kernel<float><<<G, 128, 0, s>>>(R, k, (const float *)X, ld, part);
+    else
+        col_best_kernel<double><<<G, 128, 0, s>>>(R, k, (const double *)X, ld, part);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    col_sign_kernel<<<(k + 127) / 128, 128, 0, s>>>(k, G, part, sign); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_columns(int64_t R, int k, void *X, int64_t ld, frpca_dtype dt, const double *sign,
+                                 cudaStream_t s) {
+    const int64_t total = R * k;
+    if (total == 0) return cudaSuccess;
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(total, 256), 1 << 20);
+    if (dt == FRPCA_F32)
+        scale_columns_kernel<float><<<g, 256, 0, s>>>(R, k, (float *)X, ld, sign);
+    else
+        scale_columns_kernel<double><<<g, 256, 0, s>>>(R, k, (double *)X, ld, sign);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace frpca

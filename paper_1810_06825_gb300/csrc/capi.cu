@@ -1,0 +1,602 @@
+// capi.cu -- the C ABI (include/frpca.h): handle lifetime, validation, the
+// device-built transpose, and the pass schedule of Alg. 5 / Alg. 6.
+//
+// Alg. 5 on A (m <= n) is Alg. 6 on A^T with U and V exchanged (same Gaussian
+// shapes, same products), so one driver runs Alg. 6 over a "forward" CSR F and
+// a "backward" CSR Bk: Alg. 6 uses (F, Bk) = (A, A^T), Alg. 5 (A^T, A).
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace frpca;
+
+struct frpca_ctx {
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    int *d_status = nullptr;
+    bool has_matrix = false;
+    DeviceCSR A, AT;
+    DevBuf own_rowptr, own_colidx, own_vals;    // copies of A (when not borrowed)
+    DevBuf t_rowptr, t_colidx, t_vals;          // A^T
+    DevBuf alt_A, alt_AT;                        // values converted to the other dtype
+    bool alt_ready = false;
+    SpmmPlan planA, planAT;
+    DevBuf ws_q, ws_w, ws_spmm, ws_gram, ws_eig, ws_lu, ws_small, ws_sign, ws_scratch, ws_scan;
+    std::string err;
+    // instrumentation
+    bool timing = false;
+    struct Mark {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> pool;
+    frpca_stats acc{};
+    int64_t launch_base = 0;
+};
+
+namespace frpca {
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace frpca
+
+namespace {
+
+thread_local std::string g_create_error;
+
+enum Phase { PH_SPMM, PH_LU, PH_GRAM, PH_EIG, PH_APPLY, PH_GAUSS, PH_TRANSPOSE, PH_FINISH, PH_COUNT };
+
+cudaEvent_t take_event(frpca_ctx *h) {
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Records a device-time interval of one phase on the handle's stream while
+// timing is enabled.
+struct PhaseTimer {
+    frpca_ctx *h;
+    int phase;
+    cudaEvent_t a = nullptr;
+    PhaseTimer(frpca_ctx *h_, int ph) : h(h_), phase(ph) {
+        if (h->timing && (a = take_event(h))) cudaEventRecord(a, h->stream);
+    }
+    void done() {
+        if (!a) return;
+        cudaEvent_t b = take_event(h);
+        if (b) {
+            cudaEventRecord(b, h->stream);
+            h->marks.push_back({phase, a, b});
+        } else {
+            h->pool.push_back(a);
+        }
+        a = nullptr;
+    }
+    ~PhaseTimer() { done(); }
+};
+
+frpca_status fail(frpca_ctx *h, frpca_status st, const std::string &msg) {
+    if (h)
+        h->err = msg;
+    else
+        g_create_error = msg;
+    return st;
+}
+
+frpca_status cuda_fail(frpca_ctx *h, cudaError_t e, const char *where) {
+    std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(h, FRPCA_ERR_OOM, msg);
+    return fail(h, FRPCA_ERR_CUDA, msg);
+}
+
+#define CK(call, where)                                         \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, where);  \
+    } while (0)
+
+size_t dsize(frpca_dtype dt) { return dt == FRPCA_F32 ? 4 : 8; }
+
+frpca_status read_status(frpca_ctx *h) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status read");
+    CK(cudaStreamSynchronize(h->stream), "stream synchronize");
+    if (st != 0) {
+        const char *what = st == FRPCA_ERR_SINGULAR_PIVOT ? "LU: a column has no nonzero pivot"
+                         : st == FRPCA_ERR_RANK_DEFICIENT ? "eigSVD: Gram matrix is rank deficient"
+                         : st == FRPCA_ERR_TIMEOUT        ? "a bounded device wait ran out"
+                         : st == FRPCA_ERR_NOT_CONVERGED  ? "eigensolver did not converge"
+                         : st == FRPCA_ERR_INVALID_CSR    ? "invalid CSR structure"
+                                                          : "device-side failure";
+        return fail(h, (frpca_status)st, what);
+    }
+    return FRPCA_OK;
+}
+
+frpca_status reset_status(frpca_ctx *h) {
+    CK(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream), "status reset");
+    return FRPCA_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+bool ld_ok(int64_t ld, int l, frpca_dtype dt) {
+    const int w = dt == FRPCA_F32 ? 4 : 2;
+    return ld >= l && ld % w == 0;
+}
+
+// Values of A / A^T in dtype dt (converted once if A was given in the other).
+frpca_status values_for(frpca_ctx *h, frpca_dtype dt, const void **va, const void **vat) {
+    if (dt == h->A.dtype) {
+        *va = h->A.vals;
+        *vat = h->AT.vals;
+        return FRPCA_OK;
+    }
+    if (!h->alt_ready) {
+        const size_t bytes = dsize(dt) * (size_t)std::max<int64_t>(h->A.nnz, 1);
+        CK(h->alt_A.ensure(bytes), "alloc converted values");
+        CK(h->alt_AT.ensure(bytes), "alloc converted values");
+        CK(launch_convert(h->A.vals, h->A.dtype, h->alt_A.ptr, dt, h->A.nnz, h->stream), "convert values");
+        CK(launch_convert(h->AT.vals, h->AT.dtype, h->alt_AT.ptr, dt, h->A.nnz, h->stream), "convert values");
+        h->alt_ready = true;
+    }
+    *va = h->alt_A.ptr;
+    *vat = h->alt_AT.ptr;
+    return FRPCA_OK;
+}
+
+// One SpMM pass with the handle's matrix (trans selects A^T).
+frpca_status spmm_pass(frpca_ctx *h, int trans, int l, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                       frpca_dtype dt) {
+    const void *va, *vat;
+    frpca_status st = values_for(h, dt, &va, &vat);
+    if (st != FRPCA_OK) return st;
+    const DeviceCSR &C = trans ? h->AT : h->A;
+    const SpmmPlan &P = trans ? h->planAT : h->planA;
+    CK(h->ws_spmm.ensure(std::max<size_t>(256, spmm_scratch_bytes(P, l, dt))), "alloc spmm scratch");
+    PhaseTimer t(h, PH_SPMM);
+    CK(launch_spmm(C, trans ? vat : va, P, l, X, ldx, Y, ldy, dt, h->ws_spmm.ptr, h->stream), "spmm launch");
+    t.done();
+    // Algorithmic bytes: CSR arrays once, input and output blocks once each.
+    const double sv = (double)dsize(dt);
+    h->acc.spmm_passes += 1;
+    h->acc.spmm_bytes += (double)C.nnz * (sv + 4.0) + (double)(C.rows + 1) * 8.0 +
+                         ((double)C.cols + (double)C.rows) * (double)l * sv;
+    h->acc.spmm_flops += 2.0 * (double)C.nnz * (double)l;
+    return FRPCA_OK;
+}
+
+frpca_status lu_step(frpca_ctx *h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv) {
+    CK(h->ws_lu.ensure(lu_workspace_bytes(R, l)), "alloc lu workspace");
+    PhaseTimer t(h, PH_LU);
+    CK(launch_lu(R, l, M, ld, dt, piv, h->ws_lu.ptr, h->d_status, h->num_sms, h->stream), "lu launch");
+    h->acc.lu_calls += 1;
+    return FRPCA_OK;
+}
+
+// Gram + eig of an R x l block: eigenvalues (ascending) into w, vectors into V.
+frpca_status gram_eig(frpca_ctx *h, int64_t R, int l, const void *M, int64_t ld, frpca_dtype dt, double *B, double *w,
+                      double *V) {
+    CK(h->ws_gram.ensure(gram_workspace_bytes(R, l, h->num_sms)), "alloc gram workspace");
+    CK(h->ws_eig.ensure(eig_workspace_bytes(l)), "alloc eig workspace");
+    {
+        PhaseTimer t(h, PH_GRAM);
+        CK(launch_gram(R, l, M, ld, dt, B, h->ws_gram.ptr, h->num_sms, h->stream), "gram launch");
+    }
+    PhaseTimer t(h, PH_EIG);
+    CK(launch_eig(l, B, w, V, h->ws_eig.ptr, h->d_status, h->stream), "eig launch");
+    h->acc.eigsvd_calls += 1;
+    return FRPCA_OK;
+}
+
+// Small per-run buffers: B (l x l), w (l), V^ (l x l), W matrices, signs.
+struct Small {
+    double *B, *w, *V, *sign;
+    void *W1, *W2;
+};
+
+frpca_status small_bufs(frpca_ctx *h, int l, Small &s) {
+    const size_t ll = (size_t)l * l;
+    CK(h->ws_small.ensure(sizeof(double) * (3 * ll + 3 * (size_t)l) + 2 * 8 * ll + 1024), "alloc small buffers");
+    char *p = (char *)h->ws_small.ptr;
+    s.B = (double *)p; p += sizeof(double) * ll;
+    s.V = (double *)p; p += sizeof(double) * ll;
+    s.w = (double *)p; p += sizeof(double) * round_up(l, 2);
+    s.sign = (double *)p; p += sizeof(double) * round_up(l, 2);
+    p = (char *)round_up((int64_t)(uintptr_t)p, 256);
+    s.W1 = p; p += 8 * ll;
+    s.W2 = p;
+    return FRPCA_OK;
+}
+
+// eigSVD (Alg. 2) in place: M <- U = M V spdiags(1./S).
+frpca_status eigsvd_inplace(frpca_ctx *h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, Small &s,
+                            double *S_out) {
+    frpca_status st = gram_eig(h, R, l, M, ld, dt, s.B, s.w, s.V);
+    if (st != FRPCA_OK) return st;
+    PhaseTimer t(h, PH_APPLY);
+    CK(launch_make_w(l, l, s.w, s.V, /*descending=*/0, /*scale=*/1, nullptr, dt, s.W1, S_out, h->d_status, h->stream),
+       "make_w");
+    CK(launch_apply(R, l, M, ld, s.W1, l, M, ld, dt, h->stream), "apply");
+    return FRPCA_OK;
+}
+
+frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S, void *V) {
+    if (!h) return fail(nullptr, FRPCA_ERR_INVALID_ARG, "null handle");
+    if (!h->has_matrix) return fail(h, FRPCA_ERR_INVALID_ARG, "handle has no matrix");
+    if (!o || !U || !S || !V) return fail(h, FRPCA_ERR_INVALID_ARG, "null argument");
+    const int64_t m = h->A.rows, n = h->A.cols;
+    const int k = o->k, l = o->l, q = o->q;
+    if (k < 1 || l < k || (int64_t)l > std::min(m, n) || q < 2)
+        return fail(h, FRPCA_ERR_INVALID_ARG, "need 1 <= k <= l <= min(m, n) and q >= 2");
+    if (l > FRPCA_MAX_L) return fail(h, FRPCA_ERR_UNSUPPORTED, "l > 160 is not supported");
+    if (o->precision == FRPCA_PREC_FP32_SPLITGRAM)
+        return fail(h, FRPCA_ERR_UNSUPPORTED, "FP32_SPLITGRAM is not available in this build");
+    if (o->precision != FRPCA_PREC_FP64 && o->precision != FRPCA_PREC_FP32)
+        return fail(h, FRPCA_ERR_INVALID_ARG, "unknown precision");
+    int alg = o->alg ? o->alg : (m >= n ? 6 : 5);
+    if ((alg != 5 && alg != 6) || (alg == 6 && m < n) || (alg == 5 && m > n))
+        return fail(h, FRPCA_ERR_INVALID_ARG, "Alg. 6 needs m >= n and Alg. 5 needs m <= n");
+    const frpca_dtype dt = o->precision == FRPCA_PREC_FP64 ? FRPCA_F64 : FRPCA_F32;
+    const int fwd_trans = (alg == 6) ? 0 : 1;  // F = A for Alg. 6, A^T for Alg. 5
+    const int bwd_trans = 1 - fwd_trans;
+    const int64_t rq = (alg == 6) ? n : m;      // rows of Q
+    const int64_t rw = (alg == 6) ? m : n;      // rows of the pass intermediate
+    const int64_t ld = round_up(l, 4);
+    const size_t es = dsize(dt);
+
+    frpca_status st = reset_status(h);
+    if (st != FRPCA_OK) return st;
+    const size_t qbytes = es * (size_t)rq * ld, wbytes = es * (size_t)rw * ld;
+    if (h->ws_q.bytes < qbytes) {
+        CK(h->ws_q.ensure(qbytes), "alloc Q");
+        CK(cudaMemsetAsync(h->ws_q.ptr, 0, h->ws_q.bytes, h->stream), "clear Q");
+    }
+    if (h->ws_w.bytes < wbytes) {
+        CK(h->ws_w.ensure(wbytes), "alloc W");
+        CK(cudaMemsetAsync(h->ws_w.ptr, 0, h->ws_w.bytes, h->stream), "clear W");
+    }
+    void *Q = h->ws_q.ptr, *W = h->ws_w.ptr;
+    Small sm;
+    if ((st = small_bufs(h, l, sm)) != FRPCA_OK) return st;
+
+    // Alg. 6 (Alg. 5 with A and A^T exchanged): the first sketch.  Even q:
+    // Q = (Omega A)^T with Omega = randn(k+s, m), then lu() or, for q = 2,
+    // eigSVD.  Odd q (modified power iteration, Sec. 3.2): Q = randn(n, k+s).
+    {
+        PhaseTimer t(h, PH_GAUSS);
+        CK(launch_gaussian(q % 2 == 0 ? rw : rq, l, ld, o->seed, dt, q % 2 == 0 ? W : Q, h->stream), "gaussian");
+    }
+    if (q % 2 == 0) {
+        if ((st = spmm_pass(h, bwd_trans, l, W, ld, Q, ld, dt)) != FRPCA_OK) return st;
+        st = (q == 2) ? eigsvd_inplace(h, rq, l, Q, ld, dt, sm, nullptr) : lu_step(h, rq, l, Q, ld, dt, nullptr);
+        if (st != FRPCA_OK) return st;
+    }
+    // The power iteration: one orthonormalization per A, A^T pair (Sec. 3.1),
+    // lu() except for the last, which is eigSVD.
+    const int loops = (q - 1) / 2;
+    for (int i = 1; i <= loops; ++i) {
+        if ((st = spmm_pass(h, fwd_trans, l, Q, ld, W, ld, dt)) != FRPCA_OK) return st;
+        if ((st = spmm_pass(h, bwd_trans, l, W, ld, Q, ld, dt)) != FRPCA_OK) return st;
+        st = (i == loops) ? eigsvd_inplace(h, rq, l, Q, ld, dt, sm, nullptr) : lu_step(h, rq, l, Q, ld, dt, nullptr);
+        if (st != FRPCA_OK) return st;
+    }
+    // Final pass: [U^, S^, V^] = eigSVD(A Q); ind = k+s : -1 : s+1 keeps the k
+    // largest in descending order; U = U^(:, ind), V = Q V^(:, ind).
+    if ((st = spmm_pass(h, fwd_trans, l, Q, ld, W, ld, dt)) != FRPCA_OK) return st;
+    if ((st = gram_eig(h, rw, l, W, ld, dt, sm.B, sm.w, sm.V)) != FRPCA_OK) return st;
+    PhaseTimer fin(h, PH_FINISH);
+    void *thin = (alg == 6) ? V : U;  // Q V^(:, ind), rq x k
+    void *wide = (alg == 6) ? U : V;  // U^(:, ind),   rw x k
+    // Signs follow the factor of length min(m, n): v when m >= n, else u.
+    const bool sign_on_thin = (alg == 6) || (m < n);
+    CK(h->ws_sign.ensure(sign_workspace_bytes(k, h->num_sms)), "alloc sign workspace");
+    CK(launch_make_w(l, k, sm.w, sm.V, 1, 0, nullptr, dt, sm.W1, S, h->d_status, h->stream), "make_w thin");
+    CK(launch_apply(rq, l, Q, ld, sm.W1, k, thin, k, dt, h->stream), "apply thin");
+    if (sign_on_thin) {
+        CK(launch_column_signs(rq, k, thin, k, dt, sm.sign, h->ws_sign.ptr, h->num_sms, h->stream), "signs");
+        CK(launch_scale_columns(rq, k, thin, k, dt, sm.sign, h->stream), "flip thin");
+        CK(launch_make_w(l, k, sm.w, sm.V, 1, 1, sm.sign, dt, sm.W2, nullptr, h->d_status, h->stream), "make_w wide");
+        CK(launch_apply(rw, l, W, ld, sm.W2, k, wide, k, dt, h->stream), "apply wide");
+    } else {
+        CK(launch_make_w(l, k, sm.w, sm.V, 1, 1, nullptr, dt, sm.W2, nullptr, h->d_status, h->stream), "make_w wide");
+        CK(launch_apply(rw, l, W, ld, sm.W2, k, wide, k, dt, h->stream), "apply wide");
+        CK(launch_column_signs(rw, k, wide, k, dt, sm.sign, h->ws_sign.ptr, h->num_sms, h->stream), "signs");
+        CK(launch_scale_columns(rw, k, wide, k, dt, sm.sign, h->stream), "flip wide");
+        CK(launch_scale_columns(rq, k, thin, k, dt, sm.sign, h->stream), "flip thin");
+    }
+    h->acc.runs += 1;
+    return FRPCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, frpca_handle *out) {
+    frpca_ctx *h = nullptr;
+    if (!out) return fail(nullptr, FRPCA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    h = new (std::nothrow) frpca_ctx();
+    if (!h) return fail(nullptr, FRPCA_ERR_OOM, "host allocation failed");
+    auto bail = [&](frpca_status st) {
+        g_create_error = h->err;
+        frpca_destroy(h);
+        return st;
+    };
+    h->stream = opts ? (cudaStream_t)opts->stream : nullptr;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "device attribute"));
+    e = cudaMalloc(&h->d_status, 256);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "alloc status"));
+    e = cudaMemsetAsync(h->d_status, 0, 256, h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "clear status"));
+    if (!csr) {
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return bail(cuda_fail(h, e, "synchronize"));
+        *out = h;
+        return FRPCA_OK;
+    }
+    const int64_t m = csr->m, n = csr->n, nnz = csr->nnz;
+    if (m < 1 || n < 1 || m >= (1LL << 31) || n >= (1LL << 31) || nnz < 0 || nnz >= (1LL << 31))
+        return bail(fail(h, FRPCA_ERR_INVALID_ARG, "need 1 <= m, n < 2^31 and 0 <= nnz < 2^31"));
+    if (csr->dtype != FRPCA_F32 && csr->dtype != FRPCA_F64)
+        return bail(fail(h, FRPCA_ERR_INVALID_ARG, "unknown dtype"));
+    if (!csr->rowptr || (nnz > 0 && (!csr->colidx || !csr->values)))
+        return bail(fail(h, FRPCA_ERR_INVALID_ARG, "null CSR array"));
+    const int validate = opts ? opts->validate : 1;
+    const size_t vs = dsize(csr->dtype);
+    if (!csr->on_device && validate) {
+        // Host arrays: check before anything reaches the device.
+        const int64_t *rp = csr->rowptr;
+        bool bad = rp[0] != 0 || rp[m] != nnz;
+        for (int64_t i = 0; i < m && !bad; ++i) {
+            if (rp[i + 1] < rp[i] || rp[i + 1] > nnz) { bad = true; break; }
+            for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+                const int32_t c = csr->colidx[p];
+                if (c < 0 || c >= n || (p > rp[i] && csr->colidx[p - 1] >= c)) { bad = true; break; }
+            }
+        }
+        if (bad) return bail(fail(h, FRPCA_ERR_INVALID_CSR, "invalid CSR structure"));
+    }
+    h->A.rows = m;
+    h->A.cols = n;
+    h->A.nnz = nnz;
+    h->A.dtype = csr->dtype;
+    const bool borrow = csr->on_device && opts && opts->borrow;
+    if (borrow) {
+        h->A.rowptr = (int64_t *)csr->rowptr;
+        h->A.colidx = (int32_t *)csr->colidx;
+        h->A.vals = (void *)csr->values;
+    } else {
+        const cudaMemcpyKind kind = csr->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if ((e = h->own_rowptr.ensure(8 * (size_t)(m + 1))) != cudaSuccess ||
+            (e = h->own_colidx.ensure(4 * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess ||
+            (e = h->own_vals.ensure(vs * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess)
+            return bail(cuda_fail(h, e, "alloc CSR copy"));
+        if ((e = cudaMemcpyAsync(h->own_rowptr.ptr, csr->rowptr, 8 * (size_t)(m + 1), kind, h->stream)) != cudaSuccess ||
+            (nnz > 0 && (e = cudaMemcpyAsync(h->own_colidx.ptr, csr->colidx, 4 * (size_t)nnz, kind, h->stream)) != cudaSuccess) ||
+            (nnz > 0 && (e = cudaMemcpyAsync(h->own_vals.ptr, csr->values, vs * (size_t)nnz, kind, h->stream)) != cudaSuccess))
+            return bail(cuda_fail(h, e, "copy CSR"));
+        h->A.rowptr = (int64_t *)h->own_rowptr.ptr;
+        h->A.colidx = (int32_t *)h->own_colidx.ptr;
+        h->A.vals = h->own_vals.ptr;
+    }
+    if (csr->on_device && validate) {
+        if ((e = launch_validate_csr(h->A, h->d_status, h->stream)) != cudaSuccess)
+            return bail(cuda_fail(h, e, "validate"));
+        frpca_status st = read_status(h);
+        if (st != FRPCA_OK) return bail(st);
+    }
+    // A^T on the device.
+    h->AT.rows = n;
+    h->AT.cols = m;
+    h->AT.nnz = nnz;
+    h->AT.dtype = csr->dtype;
+    if ((e = h->t_rowptr.ensure(8 * (size_t)(n + 1))) != cudaSuccess ||
+        (e = h->t_colidx.ensure(4 * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess ||
+        (e = h->t_vals.ensure(vs * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess)
+        return bail(cuda_fail(h, e, "alloc transpose"));
+    h->AT.rowptr = (int64_t *)h->t_rowptr.ptr;
+    h->AT.colidx = (int32_t *)h->t_colidx.ptr;
+    h->AT.vals = h->t_vals.ptr;
+    if ((e = csr_transpose(h->A, h->AT, h->ws_scratch, h->ws_scan, h->stream)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "transpose"));
+    std::string perr;
+    if ((e = build_spmm_plan(h->A, h->planA, h->stream, perr)) != cudaSuccess ||
+        (e = build_spmm_plan(h->AT, h->planAT, h->stream, perr)) != cudaSuccess)
+        return bail(cuda_fail(h, e, perr.c_str()));
+    h->has_matrix = true;
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "synchronize"));
+    *out = h;
+    return FRPCA_OK;
+}
+
+frpca_status frpca_destroy(frpca_handle h) {
+    if (!h) return FRPCA_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    h->planA.free_all();
+    h->planAT.free_all();
+    for (DevBuf *b : {&h->own_rowptr, &h->own_colidx, &h->own_vals, &h->t_rowptr, &h->t_colidx, &h->t_vals,
+                      &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
+                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan})
+        b->release();
+    for (auto &mk : h->marks) {
+        cudaEventDestroy(mk.a);
+        cudaEventDestroy(mk.b);
+    }
+    for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
+    if (h->d_status) cudaFree(h->d_status);
+    delete h;
+    return FRPCA_OK;
+}
+
+const char *frpca_last_error(frpca_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+frpca_status frpca_refresh(frpca_handle h) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    if (!h->has_matrix) return fail(h, FRPCA_ERR_INVALID_ARG, "handle has no matrix");
+    PhaseTimer t(h, PH_TRANSPOSE);
+    CK(csr_transpose(h->A, h->AT, h->ws_scratch, h->ws_scan, h->stream), "transpose");
+    t.done();
+    h->alt_ready = false;
+    return FRPCA_OK;
+}
+
+frpca_status frpca_set_timing(frpca_handle h, int enable) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    h->timing = enable != 0;
+    return FRPCA_OK;
+}
+
+frpca_status frpca_reset_stats(frpca_handle h) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    CK(h->stream ? cudaStreamSynchronize(h->stream) : cudaDeviceSynchronize(), "synchronize");
+    for (auto &mk : h->marks) {
+        h->pool.push_back(mk.a);
+        h->pool.push_back(mk.b);
+    }
+    h->marks.clear();
+    h->acc = frpca_stats{};
+    h->launch_base = launches_total();
+    return FRPCA_OK;
+}
+
+frpca_status frpca_get_stats(frpca_handle h, frpca_stats *out) {
+    if (!h || !out) return FRPCA_ERR_INVALID_ARG;
+    CK(h->stream ? cudaStreamSynchronize(h->stream) : cudaDeviceSynchronize(), "synchronize");
+    double ms_by_phase[PH_COUNT] = {0};
+    for (auto &mk : h->marks) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, mk.a, mk.b), "event time");
+        ms_by_phase[mk.phase] += ms;
+        h->pool.push_back(mk.a);
+        h->pool.push_back(mk.b);
+    }
+    h->marks.clear();
+    h->acc.spmm_ms += ms_by_phase[PH_SPMM];
+    h->acc.lu_ms += ms_by_phase[PH_LU];
+    h->acc.gram_ms += ms_by_phase[PH_GRAM];
+    h->acc.eig_ms += ms_by_phase[PH_EIG];
+    h->acc.apply_ms += ms_by_phase[PH_APPLY];
+    h->acc.gaussian_ms += ms_by_phase[PH_GAUSS];
+    h->acc.transpose_ms += ms_by_phase[PH_TRANSPOSE];
+    h->acc.finish_ms += ms_by_phase[PH_FINISH];
+    h->acc.kernel_launches = launches_total() - h->launch_base;
+    *out = h->acc;
+    return FRPCA_OK;
+}
+
+frpca_status frpca_run_async(frpca_handle h, const frpca_run_opts *opts, void *U, double *S, void *V) {
+    return run_impl(h, opts, U, S, V);
+}
+
+frpca_status frpca_sync(frpca_handle h) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    return read_status(h);
+}
+
+frpca_status frpca_run(frpca_handle h, const frpca_run_opts *opts, void *U, double *S, void *V) {
+    frpca_status st = run_impl(h, opts, U, S, V);
+    if (st != FRPCA_OK) return st;
+    return read_status(h);
+}
+
+frpca_status frpca_gaussian(frpca_handle h, int64_t R, int l, int64_t ld, uint64_t seed, frpca_dtype dt, void *out) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    if (R < 0 || l < 1 || ld < l || (R > 0 && !out)) return fail(h, FRPCA_ERR_INVALID_ARG, "bad gaussian arguments");
+    CK(launch_gaussian(R, l, ld, seed, dt, out, h->stream), "gaussian");
+    return FRPCA_OK;
+}
+
+frpca_status frpca_spmm(frpca_handle h, int trans, int l, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                        frpca_dtype dt) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    if (!h->has_matrix) return fail(h, FRPCA_ERR_INVALID_ARG, "handle has no matrix");
+    if (l < 1 || l > 4 * 32 * (dt == FRPCA_F32 ? 4 : 2) || !X || !Y || !ld_ok(ldx, l, dt) || !ld_ok(ldy, l, dt) ||
+        !aligned16(X) || !aligned16(Y))
+        return fail(h, FRPCA_ERR_INVALID_ARG, "bad spmm arguments (l range, ld multiple of 16 bytes, alignment)");
+    return spmm_pass(h, trans, l, X, ldx, Y, ldy, dt);
+}
+
+frpca_status frpca_get_transpose(frpca_handle h, int64_t *rowptrT, int32_t *colidxT, void *valuesT) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    if (!h->has_matrix) return fail(h, FRPCA_ERR_INVALID_ARG, "handle has no matrix");
+    CK(cudaMemcpyAsync(rowptrT, h->AT.rowptr, 8 * (size_t)(h->AT.rows + 1), cudaMemcpyDeviceToDevice, h->stream),
+       "copy rowptr");
+    if (h->A.nnz > 0) {
+        CK(cudaMemcpyAsync(colidxT, h->AT.colidx, 4 * (size_t)h->A.nnz, cudaMemcpyDeviceToDevice, h->stream),
+           "copy colidx");
+        CK(cudaMemcpyAsync(valuesT, h->AT.vals, dsize(h->AT.dtype) * (size_t)h->A.nnz, cudaMemcpyDeviceToDevice,
+                           h->stream),
+           "copy values");
+    }
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    return FRPCA_OK;
+}
+
+frpca_status frpca_lu(frpca_handle h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    if (l < 1 || R < l || ld < l || !M) return fail(h, FRPCA_ERR_INVALID_ARG, "need R >= l >= 1 and ld >= l");
+    if (l > FRPCA_MAX_L) return fail(h, FRPCA_ERR_UNSUPPORTED, "l > 160 is not supported");
+    frpca_status st = reset_status(h);
+    if (st != FRPCA_OK) return st;
+    if ((st = lu_step(h, R, l, M, ld, dt, piv)) != FRPCA_OK) return st;
+    return read_status(h);
+}
+
+frpca_status frpca_gram(frpca_handle h, int64_t R, int l, const void *M, int64_t ld, frpca_dtype dt, double *B) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    if (l < 1 || R < 0 || ld < l || !B || (R > 0 && !M)) return fail(h, FRPCA_ERR_INVALID_ARG, "bad gram arguments");
+    if (l > FRPCA_MAX_L) return fail(h, FRPCA_ERR_UNSUPPORTED, "l > 160 is not supported");
+    CK(h->ws_gram.ensure(gram_workspace_bytes(R, l, h->num_sms)), "alloc gram workspace");
+    CK(launch_gram(R, l, M, ld, dt, B, h->ws_gram.ptr, h->num_sms, h->stream), "gram launch");
+    CK(cudaStreamSynchronize(h->stream), "synchronize");
+    return FRPCA_OK;
+}
+
+frpca_status frpca_eig(frpca_handle h, int n, const double *B, double *w, double *V) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    if (n < 1 || !B || !w || !V) return fail(h, FRPCA_ERR_INVALID_ARG, "bad eig arguments");
+    if (n > FRPCA_MAX_L) return fail(h, FRPCA_ERR_UNSUPPORTED, "n > 160 is not supported");
+    frpca_status st = reset_status(h);
+    if (st != FRPCA_OK) return st;
+    CK(h->ws_eig.ensure(eig_workspace_bytes(n)), "alloc eig workspace");
+    CK(launch_eig(n, B, w, V, h->ws_eig.ptr, h->d_status, h->stream), "eig launch");
+    return read_status(h);
+}
+
+frpca_status frpca_eigsvd(frpca_handle h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, double *S,
+                          double *V) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    if (l < 1 || R < l || !ld_ok(ld, l, dt) || !M || !S || !V || !aligned16(M))
+        return fail(h, FRPCA_ERR_INVALID_ARG, "bad eigsvd arguments");
+    if (l > FRPCA_MAX_L) return fail(h, FRPCA_ERR_UNSUPPORTED, "l > 160 is not supported");
+    frpca_status st = reset_status(h);
+    if (st != FRPCA_OK) return st;
+    Small sm;
+    if ((st = small_bufs(h, l, sm)) != FRPCA_OK) return st;
+    if ((st = gram_eig(h, R, l, M, ld, dt, sm.B, sm.w, sm.V)) != FRPCA_OK) return st;
+    // S = sqrt(w) ascending, W = V diag(1./S), then U = M W over M.
+    CK(launch_make_w(l, l, sm.w, sm.V, 0, 1, nullptr, dt, sm.W1, S, h->d_status, h->stream), "make_w");
+    CK(launch_apply(R, l, M, ld, sm.W1, l, M, ld, dt, h->stream), "apply");
+    CK(cudaMemcpyAsync(V, sm.V, sizeof(double) * (size_t)l * l, cudaMemcpyDeviceToDevice, h->stream), "copy V");
+    return read_status(h);
+}
+
+}  // extern "C"

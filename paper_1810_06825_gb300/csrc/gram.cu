@@ -1,0 +1,123 @@
+// gram.cu -- step 1 of eigSVD (Alg. 2): B = M^T M for a tall R x l block.
+//
+// Blocks take contiguous row ranges; rows are staged through shared memory in
+// chunks and every thread accumulates one 8x8 tile of the upper triangle of
+// B in registers (float for FP32 input, double for FP64).  Each block writes
+// its partial Gram in double; a second kernel sums the partials in block
+// order in double, so the result is deterministic.  The float-inside-a-tile,
+// double-across-tiles split keeps the FP32 path's Gram error at the level of
+// one tile's length instead of R.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace frpca {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTile = 8;
+constexpr int kChunk = 32;  // rows per shared-memory chunk
+
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(kThreads)
+gram_partial_kernel(int64_t R, int l, const T *__restrict__ M, int64_t ld, double *__restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Ms = reinterpret_cast<T *>(smem_raw);
+    const int lp = (int)round_up(l, kTile);  // padded row length in shared memory
+    const int nt = lp / kTile;
+    const int ntiles = nt * (nt + 1) / 2;
+    // Map thread -> upper tile (ti <= tj).
+    int ti = -1, tj = -1;
+    if ((int)threadIdx.x < ntiles) {
+        int t = threadIdx.x, r = 0;
+        while (t >= nt - r) { t -= nt - r; ++r; }
+        ti = r;
+        tj = r + t;
+    }
+    Acc acc[kTile][kTile];
+#pragma unroll
+    for (int a = 0; a < kTile; ++a)
+#pragma unroll
+        for (int b = 0; b < kTile; ++b) acc[a][b] = Acc(0);
+
+    const int64_t G = gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * R / G, r1 = (int64_t)(blockIdx.x + 1) * R / G;
+    for (int64_t c0 = r0; c0 < r1; c0 += kChunk) {
+        const int rows = (int)std::min<int64_t>(kChunk, r1 - c0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kChunk * lp; idx += kThreads) {
+            const int rr = idx / lp, cc = idx - rr * lp;
+            Ms[idx] = (rr < rows && cc < l) ? M[(c0 + rr) * ld + cc] : T(0);
+        }
+        __syncthreads();
+        if (ti >= 0) {
+            for (int rr = 0; rr < rows; ++rr) {
+                const T *row = Ms + rr * lp;
+                Acc x[kTile], y[kTile];
+#pragma unroll
+                for (int a = 0; a < kTile; ++a) {
+                    x[a] = (Acc)row[ti * kTile + a];
+                    y[a] = (Acc)row[tj * kTile + a];
+                }
+#pragma unroll
+                for (int a = 0; a < kTile; ++a)
+#pragma unroll
+                    for (int b = 0; b < kTile; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
+            }
+        }
+    }
+    if (ti >= 0) {
+        double *P = partial + (int64_t)blockIdx.x * l * l;
+#pragma unroll
+        for (int a = 0; a < kTile; ++a)
+#pragma unroll
+            for (int b = 0; b < kTile; ++b) {
+                const int ra = ti * kTile + a, cb = tj * kTile + b;
+                if (ra < l && cb < l) {
+                    P[ra * l + cb] = (double)acc[a][b];
+                    P[cb * l + ra] = (double)acc[a][b];
+                }
+            }
+    }
+}
+
+__global__ void gram_reduce_kernel(int l, int nparts, const double *__restrict__ partial, double *__restrict__ B) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= l * l) return;
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += partial[(int64_t)b * l * l + idx];
+    B[idx] = s;
+}
+
+int gram_blocks(int64_t R, int num_sms) {
+    const int64_t want = std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)num_sms, ceil_div(R, 256)));
+    return (int)want;
+}
+
+}  // namespace
+
+size_t gram_workspace_bytes(int64_t R, int l, int num_sms) {
+    return sizeof(double) * (size_t)gram_blocks(R, num_sms) * l * l;
+}
+
+cudaError_t launch_gram(int64_t R, int l, const void *M, int64_t ld, frpca_dtype dt, double *B, void *ws, int num_sms,
+                        cudaStream_t s) {
+    if (l < 1 || l > FRPCA_MAX_L) return cudaErrorInvalidValue;
+    const int G = gram_blocks(R, num_sms);
+    const int lp = (int)round_up(l, kTile);
+    double *partial = (double *)ws;
+    cudaError_t e;
+    if (dt == FRPCA_F32) {
+        const size_t sm = sizeof(float) * kChunk * lp;
+        gram_partial_kernel<float, float><<<G, kThreads, sm, s>>>(R, l, (const float *)M, ld, partial); count_launch();
+    } else {
+        const size_t sm = sizeof(double) * kChunk * lp;
+        gram_partial_kernel<double, double><<<G, kThreads, sm, s>>>(R, l, (const double *)M, ld, partial); count_launch();
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    gram_reduce_kernel<<<(l * l + 255) / 256, 256, 0, s>>>(l, G, partial, B); count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace frpca

@@ -1,0 +1,109 @@
+// internal.h -- host-side interface between the frPCA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "frpca.h"
+
+namespace frpca {
+
+struct GridBarrier;
+
+// Process-wide count of kernels this library has launched (instrumentation).
+void count_launch(int n = 1);
+int64_t launches_total();
+
+// A CSR matrix resident on the device (int64 row pointers, int32 columns).
+struct DeviceCSR {
+    int64_t rows = 0, cols = 0, nnz = 0;
+    int64_t *rowptr = nullptr;
+    int32_t *colidx = nullptr;
+    void *vals = nullptr;
+    frpca_dtype dtype = FRPCA_F32;
+};
+
+// Work split of one SpMM over a CSR.  Rows with at most `seg` entries are
+// handled whole by one warp (list `short_rows`); longer rows are cut into
+// segments of `seg` entries whose partial rows go to scratch and are summed
+// in segment order by a fix-up pass.
+struct SpmmPlan {
+    int seg = 0;
+    int64_t n_short = 0;          // rows handled whole
+    int64_t n_segs = 0;           // segments of long rows
+    int64_t n_long = 0;           // long rows
+    int32_t *short_rows = nullptr;
+    int64_t *seg_start = nullptr; // first entry of each segment
+    int32_t *seg_len = nullptr;
+    int32_t *long_rows = nullptr; // row of each long row
+    int64_t *long_first = nullptr;// first segment of each long row (n_long + 1 entries)
+    void free_all();
+};
+
+// Grow-only device buffer.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t need);
+    void release();
+};
+
+// ---- gaussian.cu
+cudaError_t launch_gaussian(int64_t R, int l, int64_t ld, uint64_t seed, frpca_dtype dt, void *out,
+                            cudaStream_t s);
+
+// ---- transpose.cu
+cudaError_t launch_validate_csr(const DeviceCSR &A, int *d_status, cudaStream_t s);
+// Stable transpose; AT arrays must be allocated by the caller (cols+1, nnz, nnz).
+// Asynchronous on s; scratch buffers grow on first use and are reused.
+cudaError_t csr_transpose(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, DevBuf &scan_scratch,
+                          cudaStream_t s);
+cudaError_t launch_convert(const void *in, frpca_dtype din, void *out, frpca_dtype dout, int64_t n,
+                           cudaStream_t s);
+// Exclusive scan of n int32 counts into n (+1 total) int64 offsets.
+cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, DevBuf &scratch,
+                                      cudaStream_t s);
+
+// ---- spmm.cu
+cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, std::string &err);
+size_t spmm_scratch_bytes(const SpmmPlan &plan, int l, frpca_dtype dt);
+cudaError_t launch_spmm(const DeviceCSR &A, const void *vals, const SpmmPlan &plan, int l, const void *X,
+                        int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *scratch, cudaStream_t s);
+
+// ---- lu.cu
+size_t lu_workspace_bytes(int64_t R, int l);
+cudaError_t launch_lu(int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv, void *ws,
+                      int *d_status, int num_sms, cudaStream_t s);
+
+// ---- gram.cu
+size_t gram_workspace_bytes(int64_t R, int l, int num_sms);
+cudaError_t launch_gram(int64_t R, int l, const void *M, int64_t ld, frpca_dtype dt, double *B, void *ws,
+                        int num_sms, cudaStream_t s);
+
+// ---- eig.cu
+size_t eig_workspace_bytes(int n);
+cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, int *d_status,
+                       cudaStream_t s);
+
+// ---- apply.cu
+// W (l x kout, dtype dt, ld kout) from the eigenpairs: column j takes
+// eigenvector column cols[j] = (descending ? l-1-j : j), scaled by 1/sqrt(w)
+// when `scale`, times sign[j] when sign != nullptr.  Also S_out[j] = sqrt(w[col])
+// when S_out != nullptr, and flags rank deficiency in d_status.
+cudaError_t launch_make_w(int l, int kout, const double *w, const double *V, int descending, int scale,
+                          const double *sign, frpca_dtype dt, void *W, double *S_out, int *d_status,
+                          cudaStream_t s);
+// Y (R x kout, ldy) = M (R x l, ldm) W; Y may equal M when kout <= ldm.
+cudaError_t launch_apply(int64_t R, int l, const void *M, int64_t ldm, const void *W, int kout, void *Y,
+                         int64_t ldy, frpca_dtype dt, cudaStream_t s);
+// sign[j] = +1/-1 so that the largest-magnitude entry (smallest row on ties) of
+// column j of X (R x k, ld) is positive; partial results in ws.
+size_t sign_workspace_bytes(int k, int num_sms);
+cudaError_t launch_column_signs(int64_t R, int k, const void *X, int64_t ld, frpca_dtype dt, double *sign,
+                                void *ws, int num_sms, cudaStream_t s);
+cudaError_t launch_scale_columns(int64_t R, int k, void *X, int64_t ld, frpca_dtype dt, const double *sign,
+                                 cudaStream_t s);
+
+}  // namespace frpca

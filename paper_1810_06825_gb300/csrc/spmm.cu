@@ -1,0 +1,235 @@
+// spmm.cu -- sparse times tall-skinny dense, the "passes over A" of Alg. 5/6
+// (A*Q and A^T*G; Sec. 3.3 counts the method's cost in these passes, q of
+// them, each C_mul * nnz(A) * l flops).
+//
+// Y(rows x l) = A X with A in CSR and X, Y row-major.  A warp owns one output
+// row (or one segment of a long row): each lane owns 16-byte vectors of the
+// l-wide row (lane, lane + 32, ...), the warp reads 32 (column, value) pairs
+// coalesced, broadcasts them with shuffles and gathers the X rows as 16-byte
+// loads through the read-only path, accumulating in registers in CSR order.
+// Rows longer than `seg` entries are cut into segments whose partial rows are
+// summed in segment order by a fix-up kernel, so the result is deterministic
+// and no float atomics are used.
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace frpca {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kDefaultSeg = 1024;
+
+template <typename T, int NV>
+__global__ void __launch_bounds__(kThreads)
+spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, const T *__restrict__ vals,
+            const int32_t *__restrict__ short_rows, int64_t n_short, const int64_t *__restrict__ seg_start,
+            const int32_t *__restrict__ seg_len, int64_t n_segs, int nvec, const T *__restrict__ X, int64_t ldx,
+            T *__restrict__ Y, int64_t ldy, T *__restrict__ partial) {
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::width;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+    int64_t start;
+    int len;
+    V *out;
+    if (w < n_short) {
+        const int32_t row = short_rows[w];
+        start = rowptr[row];
+        len = (int)(rowptr[row + 1] - start);
+        out = reinterpret_cast<V *>(Y + (int64_t)row * ldy);
+    } else if (w - n_short < n_segs) {
+        const int64_t sidx = w - n_short;
+        start = seg_start[sidx];
+        len = seg_len[sidx];
+        out = reinterpret_cast<V *>(partial + sidx * (int64_t)nvec * W);
+    } else {
+        return;
+    }
+    const V *Xv = reinterpret_cast<const V *>(X);
+    const int64_t ldxv = ldx / W;
+    V acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = Vec<T>::zero();
+
+    for (int base = 0; base < len; base += 32) {
+        const int cnt = min(32, len - base);
+        int32_t my_col = 0;
+        T my_val = T(0);
+        if (lane < cnt) {
+            my_col = __ldg(colidx + start + base + lane);
+            my_val = __ldg(vals + start + base + lane);
+        }
+        if (cnt == 32) {
+#pragma unroll
+            for (int t0 = 0; t0 < 32; t0 += 8) {
+                int32_t c[8];
+                T v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    c[u] = __shfl_sync(0xffffffffu, my_col, t0 + u);
+                    v[u] = __shfl_sync(0xffffffffu, my_val, t0 + u);
+                }
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const int vi = lane + 32 * k;
+                    if (vi < nvec) {
+                        V x[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) x[u] = __ldg(Xv + (int64_t)c[u] * ldxv + vi);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) Vec<T>::fma(acc[k], v[u], x[u]);
+                    }
+                }
+            }
+        } else {
+            for (int t = 0; t < cnt; ++t) {
+                const int32_t c = __shfl_sync(0xffffffffu, my_col, t);
+                const T v = __shfl_sync(0xffffffffu, my_val, t);
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const int vi = lane + 32 * k;
+                    if (vi < nvec) Vec<T>::fma(acc[k], v, __ldg(Xv + (int64_t)c * ldxv + vi));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int vi = lane + 32 * k;
+        if (vi < nvec) out[vi] = acc[k];
+    }
+}
+
+template <typename T>
+__global__ void spmm_fixup_kernel(int64_t n_long, const int32_t *__restrict__ long_rows,
+                                  const int64_t *__restrict__ long_first, int nvec, const T *__restrict__ partial,
+                                  T *__restrict__ Y, int64_t ldy) {
+    using V = typename Vec<T>::type;
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= n_long) return;
+    const int64_t s0 = long_first[r], s1 = long_first[r + 1];
+    const V *P = reinterpret_cast<const V *>(partial);
+    V *out = reinterpret_cast<V *>(Y + (int64_t)long_rows[r] * ldy);
+    for (int vi = lane; vi < nvec; vi += 32) {
+        V acc = P[s0 * nvec + vi];
+        for (int64_t s = s0 + 1; s < s1; ++s) Vec<T>::add(acc, P[s * nvec + vi]);
+        out[vi] = acc;
+    }
+}
+
+template <typename T>
+cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmPlan &p, int l, const T *X, int64_t ldx, T *Y,
+                         int64_t ldy, T *partial, cudaStream_t s) {
+    constexpr int W = Vec<T>::width;
+    const int nvec = (int)ceil_div(l, W);
+    const int nv = (int)ceil_div(nvec, 32);
+    const int64_t warps = p.n_short + p.n_segs;
+    if (warps > 0) {
+        const int64_t blocks = ceil_div(warps * 32, kThreads);
+#define FRPCA_SPMM_CASE(NVV)                                                                                  \
+    case NVV:                                                                                                 \
+        spmm_kernel<T, NVV><<<(unsigned)blocks, kThreads, 0, s>>>(A.rowptr, A.colidx, vals, p.short_rows,     \
+                                                                  p.n_short, p.seg_start, p.seg_len,          \
+                                                                  p.n_segs, nvec, X, ldx, Y, ldy, partial); count_launch();   \
+        break;
+        switch (nv) {
+            FRPCA_SPMM_CASE(1)
+            FRPCA_SPMM_CASE(2)
+            FRPCA_SPMM_CASE(3)
+            FRPCA_SPMM_CASE(4)
+            default: return cudaErrorInvalidValue;
+        }
+#undef FRPCA_SPMM_CASE
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (p.n_long > 0) {
+        spmm_fixup_kernel<T><<<(unsigned)ceil_div(p.n_long * 32, 256), 256, 0, s>>>(p.n_long, p.long_rows,
+                                                                                   p.long_first, nvec, partial,
+                                                                                   Y, ldy); count_launch();
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+void SpmmPlan::free_all() {
+    cudaFree(short_rows);
+    cudaFree(seg_start);
+    cudaFree(seg_len);
+    cudaFree(long_rows);
+    cudaFree(long_first);
+    short_rows = nullptr;
+    seg_start = nullptr;
+    seg_len = nullptr;
+    long_rows = nullptr;
+    long_first = nullptr;
+    n_short = n_segs = n_long = 0;
+}
+
+cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, std::string &err) {
+    plan.free_all();
+    plan.seg = kDefaultSeg;
+    std::vector<int64_t> rp((size_t)A.rows + 1);
+    cudaError_t e = cudaMemcpyAsync(rp.data(), A.rowptr, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        err = "spmm plan: reading row pointers failed";
+        return e;
+    }
+    std::vector<int32_t> shorts, lrows, slen;
+    std::vector<int64_t> sstart, lfirst;
+    shorts.reserve((size_t)A.rows);
+    for (int64_t i = 0; i < A.rows; ++i) {
+        const int64_t len = rp[i + 1] - rp[i];
+        if (len <= plan.seg) {
+            shorts.push_back((int32_t)i);
+        } else {
+            lrows.push_back((int32_t)i);
+            lfirst.push_back((int64_t)sstart.size());
+            for (int64_t p = rp[i]; p < rp[i + 1]; p += plan.seg) {
+                sstart.push_back(p);
+                slen.push_back((int32_t)std::min<int64_t>(plan.seg, rp[i + 1] - p));
+            }
+        }
+    }
+    lfirst.push_back((int64_t)sstart.size());
+    plan.n_short = (int64_t)shorts.size();
+    plan.n_long = (int64_t)lrows.size();
+    plan.n_segs = (int64_t)sstart.size();
+    auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
+        if (bytes == 0) return cudaSuccess;
+        cudaError_t r = cudaMalloc(dst, bytes);
+        if (r != cudaSuccess) return r;
+        return cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    if ((e = up((void **)&plan.short_rows, shorts.data(), 4 * shorts.size())) != cudaSuccess ||
+        (e = up((void **)&plan.long_rows, lrows.data(), 4 * lrows.size())) != cudaSuccess ||
+        (e = up((void **)&plan.long_first, lfirst.data(), 8 * lfirst.size())) != cudaSuccess ||
+        (e = up((void **)&plan.seg_start, sstart.data(), 8 * sstart.size())) != cudaSuccess ||
+        (e = up((void **)&plan.seg_len, slen.data(), 4 * slen.size())) != cudaSuccess) {
+        err = "spmm plan: device allocation failed";
+        return e;
+    }
+    return cudaStreamSynchronize(s);
+}
+
+size_t spmm_scratch_bytes(const SpmmPlan &plan, int l, frpca_dtype dt) {
+    const int W = dt == FRPCA_F32 ? 4 : 2;
+    return (size_t)plan.n_segs * (size_t)ceil_div(l, W) * 16;
+}
+
+cudaError_t launch_spmm(const DeviceCSR &A, const void *vals, const SpmmPlan &plan, int l, const void *X,
+                        int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *scratch, cudaStream_t s) {
+    if (dt == FRPCA_F32)
+        return launch_typed<float>(A, (const float *)vals, plan, l, (const float *)X, ldx, (float *)Y, ldy,
+                                   (float *)scratch, s);
+    return launch_typed<double>(A, (const double *)vals, plan, l, (const double *)X, ldx, (double *)Y, ldy,
+                                (double *)scratch, s);
+}
+
+}  // namespace frpca

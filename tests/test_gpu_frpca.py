@@ -1,0 +1,156 @@
+"""End-to-end GPU frPCA (Alg. 5 / Alg. 6) against the FP64 CPU oracle on the same
+Philox Gaussian test matrix.
+
+Gates: singular values rel. error <= 1e-10 (FP64 path) / 1e-4 (FP32 path);
+largest principal-angle sine between GPU and oracle U_k and V_k subspaces <=
+1e-8 (FP64) / 1e-3 (FP32); the sign convention agrees wherever it is decided
+by a clear margin.
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from tests.helpers import max_principal_sine
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_1810_06825_gb300 as frpca  # noqa: E402
+
+DEV = "cuda:0"
+TOL = {"fp64": (1e-10, 1e-8), "fp32": (1e-4, 1e-3)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1810_06825_gb300 import build
+    build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def _cpu(t):
+    return t.detach().double().cpu().numpy()
+
+
+def _compare(A, k, l, q, seed, prec, alg=None, mat=None):
+    Uo, So, Vo = oracle.frpca(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64), k, l, q, seed, alg=alg)
+    own = mat is None
+    if own:
+        mat = frpca.FrPCA.from_csr(A, device=DEV)
+    U, S, V = mat.run(k, l, q, seed=seed, precision=prec, alg=alg or 0)
+    U, S, V = _cpu(U), _cpu(S), _cpu(V)
+    if own:
+        mat.close()
+    stol, atol = TOL[prec]
+    assert np.all(np.diff(S) <= 0)
+    assert np.max(np.abs(S - So) / So) <= stol, np.max(np.abs(S - So) / So)
+    assert max_principal_sine(U, Uo) <= atol
+    assert max_principal_sine(V, Vo) <= atol
+    # Sign convention: the min(m, n)-length factor's largest entry is positive.
+    X, Xo = (V, Vo) if A.m >= A.n else (U, Uo)
+    srt = np.sort(np.abs(Xo), axis=0)
+    clear = (srt[-1] - srt[-2]) > 1e-3 * srt[-1]
+    gaps = np.abs(np.diff(So))
+    sep = np.ones(k, dtype=bool)
+    sep[:-1] &= gaps > 1e-3 * So[0]
+    sep[1:] &= gaps > 1e-3 * So[0]
+    cos = np.sum(X * Xo, axis=0)
+    assert np.all(cos[clear & sep] > 0)
+    return S, So
+
+
+SMALL_TALL = synthetic.powerlaw_csr(3000, 800, 12, 1.1, "tfidf", seed=1, dtype=np.float64)
+
+
+def _transposed(A):
+    pT, cT, vT = oracle.csr_transpose(A.m, A.n, A.indptr, A.indices, A.data)
+    return synthetic.CSR(A.n, A.m, pT, cT, vT)
+
+
+SMALL_WIDE = _transposed(SMALL_TALL)
+
+
+@pytest.mark.parametrize("q", [2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", ["tall", "wide"])
+def test_frpca_small(q, prec, shape):
+    A = SMALL_TALL if shape == "tall" else SMALL_WIDE
+    _compare(A.astype(np.float64 if prec == "fp64" else np.float32), 10, 24, q, 7, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_frpca_uniform_2000x1000(prec):
+    """The uniform 2,000 x 1,000 workload, k = 10, l = 20, 3 passes, seed 0."""
+    w = synthetic.WORKLOADS["uniform_2000x1000_nnz20000"]
+    A = synthetic.make_workload("uniform_2000x1000_nnz20000")
+    _compare(A if prec == "fp64" else A.astype(np.float32), w["k"], w["l"], w["q"], 0, prec)
+
+
+def test_frpca_square_alg5_forced():
+    """m == n with Alg. 5 forced: the sign is decided on V, the apply side."""
+    A = synthetic.powerlaw_csr(900, 900, 10, 1.1, "tfidf", seed=4, dtype=np.float64)
+    _compare(A, 6, 12, 4, 3, "fp64", alg=5)
+    _compare(A, 6, 12, 4, 3, "fp64", alg=6)
+
+
+def test_frpca_exact_rank():
+    """rank(A) = l exactly: every q returns the exact top-k SVD (closed form)."""
+    from tests.test_oracle import block_rank_csr
+    A, sig, _, _ = block_rank_csr(600, 300, 16, seed=3)
+    mat = frpca.FrPCA.from_csr(A, device=DEV)
+    for q in (2, 3, 4):
+        U, S, V = mat.run(10, 16, q, seed=1, precision="fp64")
+        assert np.max(np.abs(_cpu(S) - sig[:10]) / sig[:10]) <= 1e-10
+    mat.close()
+
+
+def test_frpca_deterministic():
+    A = SMALL_TALL.astype(np.float32)
+    mat = frpca.FrPCA.from_csr(A, device=DEV)
+    r1 = [t.clone() for t in mat.run(10, 24, 5, seed=3)]
+    r2 = [t.clone() for t in mat.run(10, 24, 5, seed=3)]
+    for a, b in zip(r1, r2):
+        assert torch.equal(a, b)
+    mat.close()
+
+
+def test_frpca_invalid_args():
+    mat = frpca.FrPCA.from_csr(SMALL_TALL, device=DEV)
+    for k, l, q in [(0, 5, 3), (6, 5, 3), (3, 5, 1), (3, 900, 3)]:
+        with pytest.raises(frpca.FrpcaError) as ei:
+            mat.run(k, l, q, precision="fp64")
+        assert ei.value.status == 1
+    with pytest.raises(frpca.FrpcaError) as ei:
+        mat.run(3, 5, 3, alg=5)  # Alg. 5 needs m <= n
+    assert ei.value.status == 1
+    mat.close()
+
+
+def test_frpca_rank_deficient_reports():
+    """Fewer than l nonzero rows: range(A Q) has dimension < l and eigSVD refuses it."""
+    A = synthetic.from_dense(np.vstack([np.random.default_rng(0).standard_normal((5, 40)), np.zeros((95, 40))]))
+    mat = frpca.FrPCA.from_csr(A, device=DEV)
+    with pytest.raises(frpca.FrpcaError) as ei:
+        mat.run(4, 8, 3, precision="fp64")
+    assert ei.value.status in (5, 6)
+    mat.close()
+
+
+# -------------------------------------------------------------- full-size workload
+@pytest.fixture(scope="module")
+def powerlaw_200k():
+    return synthetic.make_workload("powerlaw_200000x50000_deg100")
+
+
+@pytest.mark.parametrize("q", [4, 5])
+def test_frpca_powerlaw_200000x50000_fp32(powerlaw_200k, q):
+    """The 200,000 x 50,000 (~20M nnz) power-law workload, k=100, l=120, FP32
+    path, against the FP64 oracle on the same Gaussian test matrix."""
+    A = powerlaw_200k
+    S, So = _compare(A, 100, 120, q, 0, "fp32")
+    print(f"q={q} max sigma rel err {np.max(np.abs(S - So) / So):.3e}")

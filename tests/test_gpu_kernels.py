@@ -1,0 +1,249 @@
+"""GPU parity of each step of the path against the FP64 CPU oracle, through the C ABI.
+
+Tolerances: integer/index work bit-exact; the Gaussian generator's words
+bit-exact (checked through the normals to within libm/CUDA rounding); FP64
+SpMM within the summation bound d * eps * (|A||X|); FP32 SpMM within
+(d + 2) * eps32 * (|A||X|); FP64 LU bit-exact (same operations, no fused
+multiply-add); eigensolver within a few eps * ||B||.
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from tests.helpers import max_principal_sine
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_1810_06825_gb300 as frpca  # noqa: E402
+
+EPS64 = np.finfo(np.float64).eps
+EPS32 = np.finfo(np.float32).eps
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1810_06825_gb300 import build
+    build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def _cpu(t):
+    return t.detach().double().cpu().numpy()
+
+
+# ---------------------------------------------------------------- Gaussian
+@pytest.mark.parametrize("R,l", [(1, 1), (7, 5), (33, 20), (1000, 120), (50_000, 120), (4097, 13)])
+@pytest.mark.parametrize("seed", [0, 12345])
+def test_gaussian_matches_oracle(R, l, seed):
+    ref = oracle.gaussian(R, l, seed)
+    g64 = _cpu(frpca.gaussian(R, l, seed, dtype=torch.float64, device=DEV))
+    # Same words; libm vs CUDA log/cos differ by a few ulps of r <= 8.6.
+    assert np.max(np.abs(g64 - ref)) <= 200 * EPS64
+    g32 = _cpu(frpca.gaussian(R, l, seed, dtype=torch.float32, device=DEV))
+    # Float evaluation of the same formula: uniform rounding moves the angle by
+    # at most 2 pi 2^-24, and ln(u) keeps relative accuracy at both ends.
+    assert np.max(np.abs(g32 - ref)) <= 8e-6 + 4 * EPS32 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------- transpose
+def _mats():
+    rng = np.random.default_rng(0)
+    out = []
+    # empty rows and columns, a dense row longer than one SpMM segment, a hot column
+    m, n = 3000, 1500
+    rows, cols = [], []
+    for i in range(m):
+        if i % 97 == 0:
+            continue
+        c = rng.choice(n, size=rng.integers(1, 12), replace=False)
+        rows.append(np.full(c.size, i)); cols.append(c)
+    rows.append(np.full(1400, 5)); cols.append(rng.choice(n, 1400, replace=False))
+    hot = np.setdiff1d(np.arange(m), [5])
+    rows.append(hot); cols.append(np.full(hot.size, 7))
+    r = np.concatenate(rows); c = np.concatenate(cols)
+    key = np.unique(r * n + c)
+    r, c = key // n, key % n
+    out.append(synthetic.from_coo(m, n, r, c, rng.standard_normal(r.size)))
+    out.append(synthetic.powerlaw_csr(20_000, 3_000, 20, 1.1, "tfidf", seed=2, dtype=np.float64))
+    out.append(synthetic.uniform_csr(2000, 1000, 20000, seed=1))
+    return out
+
+
+MATS = _mats()
+
+
+@pytest.mark.parametrize("idx", range(len(MATS)))
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_transpose_bit_exact(idx, dtype):
+    A = MATS[idx].astype(dtype)
+    mat = frpca.FrPCA.from_csr(A, device=DEV)
+    pT, cT, vT = mat.transpose()
+    rp, ci, va = oracle.csr_transpose(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64))
+    assert np.array_equal(pT.cpu().numpy(), rp)
+    assert np.array_equal(cT.cpu().numpy(), ci)
+    assert np.array_equal(vT.cpu().numpy(), va.astype(dtype))
+    mat.close()
+
+
+# ---------------------------------------------------------------- SpMM
+def _spmm_bound(A, X, trans, eps):
+    Aabs = synthetic.CSR(A.m, A.n, A.indptr, A.indices, np.abs(A.data.astype(np.float64)))
+    f = oracle.spmm_t if trans else oracle.spmm
+    mag = f(Aabs.m, Aabs.n, Aabs.indptr, Aabs.indices, Aabs.data, np.abs(X))
+    deg = np.diff(A.indptr) if not trans else np.bincount(A.indices, minlength=A.n)
+    return (deg[:, None] + 2) * eps * mag + 1e-300
+
+
+@pytest.mark.parametrize("idx", range(len(MATS)))
+@pytest.mark.parametrize("l", [1, 5, 20, 48, 120, 160])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_spmm_matches_oracle(idx, l, dtype, trans):
+    A = MATS[idx].astype(dtype)
+    mat = frpca.FrPCA.from_csr(A, device=DEV)
+    rng = np.random.default_rng(l)
+    X = rng.standard_normal((A.m if trans else A.n, l)).astype(dtype)
+    Xg = frpca.empty_block(X.shape[0], l, torch.float64 if dtype == np.float64 else torch.float32, DEV)
+    Xg.copy_(torch.from_numpy(X))
+    Y = _cpu(mat.spmm(Xg, trans=bool(trans)))
+    f = oracle.spmm_t if trans else oracle.spmm
+    ref = f(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64), X.astype(np.float64))
+    eps = EPS64 if dtype == np.float64 else EPS32
+    bound = _spmm_bound(A, X.astype(np.float64), trans, eps)
+    assert np.all(np.abs(Y - ref) <= bound)
+    mat.close()
+
+
+def test_spmm_is_deterministic():
+    A = MATS[1].astype(np.float32)
+    mat = frpca.FrPCA.from_csr(A, device=DEV)
+    X = frpca.empty_block(A.m, 120, torch.float32, DEV)
+    X.copy_(torch.randn(A.m, 120, generator=torch.Generator().manual_seed(0)))
+    Y1 = mat.spmm(X, trans=True).clone()
+    Y2 = mat.spmm(X, trans=True).clone()
+    assert torch.equal(Y1, Y2)
+    mat.close()
+
+
+# ---------------------------------------------------------------- LU
+@pytest.mark.parametrize("R,l", [(1, 1), (7, 7), (50, 8), (1000, 33), (20_000, 120), (5000, 160), (333, 17)])
+def test_lu_fp64_bit_exact(R, l):
+    M = np.random.default_rng(R + l).standard_normal((R, l))
+    ref, piv_ref = oracle.lu_ptl(M)
+    Mg = torch.from_numpy(M).to(DEV)
+    PL, piv = frpca.lu(Mg)
+    assert np.array_equal(piv.cpu().numpy(), piv_ref)
+    assert np.array_equal(_cpu(PL), ref)
+
+
+@pytest.mark.parametrize("R,l", [(50, 8), (20_000, 120), (4099, 48)])
+def test_lu_fp32_spans_same_range(R, l):
+    M = np.random.default_rng(R).standard_normal((R, l)).astype(np.float32)
+    PL, piv = frpca.lu(torch.from_numpy(M).to(DEV))
+    P = _cpu(PL)
+    piv = piv.cpu().numpy()
+    assert len(set(piv.tolist())) == l
+    assert np.max(np.abs(P)) <= 1.0 + 1e-6
+    for j, p in enumerate(piv):
+        assert P[p, j] == 1.0 and np.all(P[p, j + 1:] == 0.0)
+    assert max_principal_sine(P, M.astype(np.float64)) < 1e-4
+
+
+def test_lu_singular_pivot_reports():
+    M = np.random.default_rng(0).standard_normal((100, 6))
+    M[:, 3] = 0.0
+    with pytest.raises(frpca.FrpcaError) as ei:
+        frpca.lu(torch.from_numpy(M).to(DEV))
+    assert ei.value.status == 5
+
+
+# ---------------------------------------------------------------- Gram / eig / eigSVD
+@pytest.mark.parametrize("R,l", [(1, 1), (100, 20), (5000, 120), (200_000, 120), (777, 160)])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_gram_matches_oracle(R, l, dtype):
+    M = np.random.default_rng(R).standard_normal((R, l)).astype(dtype)
+    B = _cpu(frpca.gram(torch.from_numpy(M).to(DEV)))
+    ref = oracle.gram(M.astype(np.float64))
+    scale = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+    eps = EPS64 if dtype == np.float64 else EPS32
+    chunk = R if dtype == np.float64 else min(R, 4096)
+    assert np.all(np.abs(B - ref) <= (chunk + 2) * eps * scale + 1e-300)
+    assert np.array_equal(B, B.T)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 20, 64, 120, 121, 160])
+def test_eig_matches_oracle(n):
+    rng = np.random.default_rng(n)
+    X = rng.standard_normal((3 * n, n))
+    B = X.T @ X
+    w, V = frpca.eig(torch.from_numpy(B).to(DEV))
+    w, V = _cpu(w), _cpu(V)
+    wr, Vr = oracle.eig_sym(B)
+    nb = np.linalg.norm(B, 2)
+    assert np.max(np.abs(w - wr)) <= 64 * EPS64 * nb
+    assert np.allclose(V.T @ V, np.eye(n), atol=1e-12)
+    assert np.max(np.abs(B @ V - V * w)) <= 256 * EPS64 * nb
+    gaps = np.diff(wr)
+    for j in range(n):
+        gap = min(gaps[j - 1] if j > 0 else np.inf, gaps[j] if j < n - 1 else np.inf)
+        if gap > 1e-6 * nb:
+            assert abs(abs(V[:, j] @ Vr[:, j]) - 1) <= 1e-9
+
+
+def test_eig_clustered_and_indefinite():
+    Q, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((40, 40)))
+    d = np.concatenate([np.full(10, 2.0), np.linspace(-1, 1, 20), np.full(10, 5.0 + 1e-9)])
+    B = (Q * d) @ Q.T
+    B = (B + B.T) / 2
+    w, V = frpca.eig(torch.from_numpy(B).to(DEV))
+    w, V = _cpu(w), _cpu(V)
+    assert np.allclose(np.sort(d), w, atol=1e-12)
+    assert np.allclose(V.T @ V, np.eye(40), atol=1e-12)
+    assert np.allclose(B @ V, V * w, atol=1e-11)
+
+
+@pytest.mark.parametrize("R,l,cond", [(500, 20, 10.0), (20_000, 120, 100.0), (3000, 160, 30.0)])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_eigsvd_matches_oracle(R, l, cond, dtype):
+    rng = np.random.default_rng(R)
+    Uq, _ = np.linalg.qr(rng.standard_normal((R, l)))
+    Vq, _ = np.linalg.qr(rng.standard_normal((l, l)))
+    M = ((Uq * np.geomspace(1, 1 / cond, l)) @ Vq.T).astype(dtype)
+    U, S, V = frpca.eigsvd(torch.from_numpy(M).to(DEV))
+    Uo, So, Vo = oracle.eigsvd(M.astype(np.float64))
+    S, U = _cpu(S), _cpu(U)
+    tol = 1e-10 if dtype == np.float64 else 1e-4
+    assert np.max(np.abs(S - So) / So) <= tol
+    assert np.allclose(U.T @ U, np.eye(l), atol=(1e-10 if dtype == np.float64 else 1e-3))
+    assert max_principal_sine(U, Uo) <= (1e-10 if dtype == np.float64 else 1e-3)
+
+
+def test_eigsvd_rank_deficient_reports():
+    M = np.random.default_rng(0).standard_normal((300, 8))
+    M[:, 7] = M[:, 0] - M[:, 2]
+    with pytest.raises(frpca.FrpcaError) as ei:
+        frpca.eigsvd(torch.from_numpy(M).to(DEV))
+    assert ei.value.status == 6
+
+
+def test_invalid_csr_rejected_on_device():
+    A = synthetic.uniform_csr(50, 40, 300, seed=3)
+    bad = A.indices.copy()
+    s = A.indptr[7]
+    bad[s], bad[s + 1] = bad[s + 1], bad[s]  # unsorted row
+    with pytest.raises(frpca.FrpcaError) as ei:
+        frpca.FrPCA(torch.from_numpy(A.indptr).to(DEV), torch.from_numpy(bad).to(DEV),
+                    torch.from_numpy(A.data).to(DEV), (A.m, A.n))
+    assert ei.value.status == 2
+    bad = A.indices.copy()
+    bad[3] = 40  # column out of range
+    with pytest.raises(frpca.FrpcaError):
+        frpca.FrPCA(torch.from_numpy(A.indptr).to(DEV), torch.from_numpy(bad).to(DEV),
+                    torch.from_numpy(A.data).to(DEV), (A.m, A.n))
