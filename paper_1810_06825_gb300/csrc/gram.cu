@@ -2,11 +2,18 @@
 //
 // Blocks take contiguous row ranges; rows are staged through shared memory in
 // chunks and every thread accumulates one 8x8 tile of the upper triangle of
-// B in registers (float for FP32 input, double for FP64).  Each block writes
-// its partial Gram in double; a second kernel sums the partials in block
-// order in double, so the result is deterministic.  The float-inside-a-tile,
-// double-across-tiles split keeps the FP32 path's Gram error at the level of
-// one tile's length instead of R.
+// B in registers.  Each block writes its partial Gram in double; a second
+// kernel sums the partials in block order in double, so the result is
+// deterministic.
+//
+// eigSVD squares the condition number of its input (Sec. 3.1), and the blocks
+// that reach it after a power-iteration step have condition numbers near 1e4,
+// so their Gram matrix must be accurate to far more than float's 24 bits.
+// FP32 input is therefore accumulated as an unevaluated sum of two floats: the
+// product x*y is split exactly into p + e (p = fl(x y), e = fma(x, y, -p)) and
+// added to (hi, lo) with Knuth's TwoSum, which keeps about 48 significant
+// bits with float arithmetic only (GB300's double-precision rate is a small
+// fraction of its float rate).  FP64 input is accumulated with double FMA.
 #include <algorithm>
 
 #include "common.cuh"
@@ -18,6 +25,78 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kTile = 8;
 constexpr int kChunk = 32;  // rows per shared-memory chunk
+
+// (hi, lo) += x * y exactly rounded to about 48 bits, float operations only.
+__device__ inline void df_fma(float x, float y, float &hi, float &lo) {
+    const float p = __fmul_rn(x, y);
+    const float e = __fmaf_rn(x, y, -p);      // x y = p + e exactly
+    const float t = __fadd_rn(hi, p);         // TwoSum(hi, p) = t + err exactly
+    const float z = __fadd_rn(t, -hi);
+    const float err = __fadd_rn(__fadd_rn(hi, -__fadd_rn(t, -z)), __fadd_rn(p, -z));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+__global__ void __launch_bounds__(kThreads)
+gram_partial_df_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, double *__restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *Ms = reinterpret_cast<float *>(smem_raw);
+    const int lp = (int)round_up(l, kTile);
+    const int nt = lp / kTile;
+    const int ntiles = nt * (nt + 1) / 2;
+    int ti = -1, tj = -1;
+    if ((int)threadIdx.x < ntiles) {
+        int t = threadIdx.x, r = 0;
+        while (t >= nt - r) { t -= nt - r; ++r; }
+        ti = r;
+        tj = r + t;
+    }
+    float hi[kTile][kTile], lo[kTile][kTile];
+#pragma unroll
+    for (int a = 0; a < kTile; ++a)
+#pragma unroll
+        for (int b = 0; b < kTile; ++b) hi[a][b] = lo[a][b] = 0.0f;
+    const int64_t G = gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * R / G, r1 = (int64_t)(blockIdx.x + 1) * R / G;
+    for (int64_t c0 = r0; c0 < r1; c0 += kChunk) {
+        const int rows = (int)std::min<int64_t>(kChunk, r1 - c0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kChunk * lp; idx += kThreads) {
+            const int rr = idx / lp, cc = idx - rr * lp;
+            Ms[idx] = (rr < rows && cc < l) ? M[(c0 + rr) * ld + cc] : 0.0f;
+        }
+        __syncthreads();
+        if (ti >= 0) {
+            for (int rr = 0; rr < rows; ++rr) {
+                const float *row = Ms + rr * lp;
+                float x[kTile], y[kTile];
+#pragma unroll
+                for (int a = 0; a < kTile; ++a) {
+                    x[a] = row[ti * kTile + a];
+                    y[a] = row[tj * kTile + a];
+                }
+#pragma unroll
+                for (int a = 0; a < kTile; ++a)
+#pragma unroll
+                    for (int b = 0; b < kTile; ++b) df_fma(x[a], y[b], hi[a][b], lo[a][b]);
+            }
+        }
+    }
+    if (ti >= 0) {
+        double *P = partial + (int64_t)blockIdx.x * l * l;
+#pragma unroll
+        for (int a = 0; a < kTile; ++a)
+#pragma unroll
+            for (int b = 0; b < kTile; ++b) {
+                const int ra = ti * kTile + a, cb = tj * kTile + b;
+                if (ra < l && cb < l) {
+                    const double v = (double)hi[a][b] + (double)lo[a][b];
+                    P[ra * l + cb] = v;
+                    P[cb * l + ra] = v;
+                }
+            }
+    }
+}
 
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(kThreads)
@@ -110,7 +189,7 @@ cudaError_t launch_gram(int64_t R, int l, const void *M, int64_t ld, frpca_dtype
     cudaError_t e;
     if (dt == FRPCA_F32) {
         const size_t sm = sizeof(float) * kChunk * lp;
-        gram_partial_kernel<float, float><<<G, kThreads, sm, s>>>(R, l, (const float *)M, ld, partial); count_launch();
+        gram_partial_df_kernel<<<G, kThreads, sm, s>>>(R, l, (const float *)M, ld, partial); count_launch();
     } else {
         const size_t sm = sizeof(double) * kChunk * lp;
         gram_partial_kernel<double, double><<<G, kThreads, sm, s>>>(R, l, (const double *)M, ld, partial); count_launch();

@@ -2,17 +2,19 @@
 // returning P^T L in the block's original row order (Lemma 3, Eq. 8: P M = L U,
 // so range(P^T L) = range(M); its entries are bounded by 1).
 //
-// One cooperative launch.  Block b owns a contiguous range of rows.  Column j
-// is processed as: (1) every block reduces the per-block pivot candidates of
-// column j (largest |M(i,j)| among not-yet-pivoted rows, smallest row index on
-// equal magnitudes) to the same pivot row p; (2) every block reads row p and
-// updates its own unpivoted rows, M(i,j) <- M(i,j)/M(p,j) and
-// M(i,c) <- M(i,c) - M(i,j) M(p,c) for c > j, while finding its candidate for
-// column j+1; (3) a grid barrier.  The pivot row keeps its U entries until
-// every block has used them; its owner rewrites it to 1 at j and 0 to the right
-// one step later.  In double precision the update is done without fused
-// multiply-add, in the same operation order as a textbook right-looking
-// elimination, so the result is reproducible bit for bit.
+// One cooperative launch.  Block b owns a contiguous range of rows and keeps
+// as many of them as fit in shared memory for the whole factorization (the
+// rest stay in global memory).  Column j is processed as: (1) every block
+// reduces the per-block pivot candidates of column j (largest |M(i,j)| among
+// not-yet-pivoted rows, smallest row index on equal magnitudes) to the same
+// pivot row p and reads row p; (2) every block updates its own unpivoted rows,
+// M(i,j) <- M(i,j) / M(p,j) and M(i,c) <- M(i,c) - M(i,j) M(p,c) for c > j,
+// and finds its candidate for column j+1; (3) a bounded grid barrier.  The
+// pivot row keeps its U entries until every block has used them; its owner
+// rewrites it to 1 at j and 0 to the right one step later.  In double
+// precision the update is done without fused multiply-add, in the operation
+// order of textbook right-looking elimination, so it is reproducible bit for
+// bit against a plain CPU implementation.
 #include <algorithm>
 
 #include "common.cuh"
@@ -21,9 +23,10 @@
 namespace frpca {
 namespace {
 
-constexpr int kLuThreads = 512;
+constexpr int kLuThreads = 1024;
 constexpr int kLuWarps = kLuThreads / 32;
 constexpr int kMaxBlocks = 1024;
+constexpr int kMaxRowsPerBlock = 8192;
 
 struct Cand {
     double absval;  // |M(i,j)| (exact in double for either input type)
@@ -45,9 +48,10 @@ template <> __device__ inline double sub_mul<double>(double x, double m, double 
 template <> __device__ inline float sub_mul<float>(float x, float m, float u) { return fmaf(-m, u, x); }
 
 template <typename T>
-__global__ void __launch_bounds__(kLuThreads)
+__global__ void __launch_bounds__(kLuThreads, 1)
 lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__ piv_out, Cand *cand,
-          GridBarrier *bar, unsigned char *pivflag, int *status) {
+          GridBarrier *bar, int cache_rows, int *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T urow[FRPCA_MAX_L];
     __shared__ int64_t pivots[FRPCA_MAX_L];
     __shared__ double wbest[kLuWarps];
@@ -58,15 +62,27 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned G = gridDim.x;
     const int64_t r0 = (int64_t)blockIdx.x * R / G, r1 = (int64_t)(blockIdx.x + 1) * R / G;
+    const int nrows = (int)(r1 - r0);
+    const int ncache = min(nrows, cache_rows);
+    T *cache = reinterpret_cast<T *>(smem_raw);                                   // ncache x l
+    unsigned char *pivd = reinterpret_cast<unsigned char *>(cache + (size_t)cache_rows * l);  // nrows flags
+    // Row i of the block: shared memory for the first ncache rows, global after.
+    auto rowp = [&](int li) -> T * { return li < ncache ? cache + (size_t)li * l : M + (r0 + li) * ld; };
+
+    for (int li = threadIdx.x; li < nrows; li += kLuThreads) pivd[li] = 0;
+    for (int idx = threadIdx.x; idx < ncache * l; idx += kLuThreads) {
+        const int li = idx / l, c = idx - li * l;
+        cache[idx] = M[(r0 + li) * ld + c];
+    }
+    __syncthreads();
 
     // Candidate for column 0.
     double best = 0.0;
     int64_t brow = -1;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += kLuThreads) {
-        const double a = fabs((double)M[i * ld]);
-        if (better(a, i, best, brow)) { best = a; brow = i; }
+    for (int li = threadIdx.x; li < nrows; li += kLuThreads) {
+        const double a = fabs((double)rowp(li)[0]);
+        if (better(a, r0 + li, best, brow)) { best = a; brow = r0 + li; }
     }
-    // Block reduction of (best, brow).
     auto block_reduce_write = [&](int slot) {
         for (int o = 16; o > 0; o >>= 1) {
             const double ob = __shfl_down_sync(0xffffffffu, best, o);
@@ -85,9 +101,9 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
         }
     };
     block_reduce_write(0);
-    if (!grid_barrier(bar, G, status, kBarrierLimitCycles)) return;
+    bool ok = grid_barrier(bar, G, status, kBarrierLimitCycles);
 
-    for (int j = 0; j < l; ++j) {
+    for (int j = 0; j < l && ok; ++j) {
         // (1) the pivot of column j, identical in every block.
         if (threadIdx.x == 0) {
             double b = 0.0;
@@ -108,54 +124,85 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
             }
         }
         __syncthreads();
-        if (s_stop) return;
+        if (s_stop) { ok = false; break; }
         const int64_t p = s_p;
         // Finish the previous pivot row (no block reads it any more).
         if (j > 0) {
             const int64_t pp = pivots[j - 1];
-            if (pp >= r0 && pp < r1)
-                for (int c = j - 1 + threadIdx.x; c < l; c += kLuThreads) M[pp * ld + c] = (c == j - 1) ? T(1) : T(0);
+            if (pp >= r0 && pp < r1) {
+                T *row = rowp((int)(pp - r0));
+                for (int c = j - 1 + threadIdx.x; c < l; c += kLuThreads) row[c] = (c == j - 1) ? T(1) : T(0);
+            }
         }
-        for (int c = j + threadIdx.x; c < l; c += kLuThreads) urow[c] = __ldcg(M + p * ld + c);
-        if (p >= r0 && p < r1 && threadIdx.x == 0) pivflag[p] = 1;
+        // Row p: from this block's shared memory if it owns it, else from
+        // global memory, where its owner wrote it back before the barrier.
+        if (p >= r0 && p < r1) {
+            const T *row = rowp((int)(p - r0));
+            for (int c = j + threadIdx.x; c < l; c += kLuThreads) urow[c] = row[c];
+            if (threadIdx.x == 0) pivd[p - r0] = 1;
+        } else {
+            for (int c = j + threadIdx.x; c < l; c += kLuThreads) urow[c] = __ldcg(M + p * ld + c);
+        }
         __syncthreads();
 
         // (2) eliminate column j from the own unpivoted rows; candidate of j+1.
         const T ujj = urow[j];
         best = 0.0;
         brow = -1;
-        for (int64_t i = r0 + warp; i < r1; i += kLuWarps) {
-            if (pivflag[i]) continue;
-            T *row = M + i * ld;
+        for (int li = warp; li < nrows; li += kLuWarps) {
+            if (pivd[li]) continue;
+            T *row = rowp(li);
             const T mult = row[j] / ujj;
             for (int c = j + 1 + lane; c < l; c += 32) {
                 const T v = sub_mul<T>(row[c], mult, urow[c]);
                 row[c] = v;
                 if (c == j + 1) {
                     const double a = fabs((double)v);
-                    if (better(a, i, best, brow)) { best = a; brow = i; }
+                    if (better(a, r0 + li, best, brow)) { best = a; brow = r0 + li; }
                 }
             }
             __syncwarp();
             if (lane == 0) row[j] = mult;
         }
         if (j + 1 < l) {
+            // The next pivot row may be read by other blocks from global memory:
+            // each block writes its candidate row back before the barrier.
+            __syncthreads();
             block_reduce_write((j + 1) & 1);
-            if (!grid_barrier(bar, G, status, kBarrierLimitCycles)) return;
+            __syncthreads();
+            const int64_t mine = cand[((j + 1) & 1) * G + blockIdx.x].row;
+            if (mine >= r0 && mine < r0 + ncache) {
+                const T *row = cache + (size_t)(mine - r0) * l;
+                for (int c = j + 1 + threadIdx.x; c < l; c += kLuThreads) M[mine * ld + c] = row[c];
+            }
+            ok = grid_barrier(bar, G, status, kBarrierLimitCycles);
         }
     }
-    // The last pivot row: wait until every block has read it.
-    if (!grid_barrier(bar, G, status, kBarrierLimitCycles)) return;
-    const int64_t pl = pivots[l - 1];
-    if (pl >= r0 && pl < r1)
-        for (int c = l - 1 + threadIdx.x; c < l; c += kLuThreads) M[pl * ld + c] = T(1);
+    if (ok) {
+        // The last pivot row: wait until every block has read it.
+        ok = grid_barrier(bar, G, status, kBarrierLimitCycles);
+        if (ok) {
+            const int64_t pl = pivots[l - 1];
+            if (pl >= r0 && pl < r1) {
+                T *row = rowp((int)(pl - r0));
+                if (threadIdx.x == 0) row[l - 1] = T(1);
+            }
+        }
+    }
+    __syncthreads();
+    // Write the cached rows back (also after a failure, so M stays consistent).
+    for (int idx = threadIdx.x; idx < ncache * l; idx += kLuThreads) {
+        const int li = idx / l, c = idx - li * l;
+        M[(r0 + li) * ld + c] = cache[idx];
+    }
 }
 
 }  // namespace
 
 size_t lu_workspace_bytes(int64_t R, int l) {
+    (void)R;
     (void)l;
-    return 256 + sizeof(Cand) * 2 * kMaxBlocks + (size_t)round_up(R, 256);
+    return 256 + sizeof(Cand) * 2 * kMaxBlocks;
 }
 
 cudaError_t launch_lu(int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv, void *ws, int *d_status,
@@ -164,22 +211,36 @@ cudaError_t launch_lu(int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int
     char *p = (char *)ws;
     GridBarrier *bar = (GridBarrier *)p;
     Cand *cand = (Cand *)(p + 256);
-    unsigned char *pivflag = (unsigned char *)(p + 256 + sizeof(Cand) * 2 * kMaxBlocks);
     cudaError_t e = cudaMemsetAsync(ws, 0, lu_workspace_bytes(R, l), s);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
+    const size_t es = dt == FRPCA_F32 ? 4 : 8;
     const void *fn = (dt == FRPCA_F32) ? (const void *)lu_kernel<float> : (const void *)lu_kernel<double>;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLuThreads, 0);
-    if (e != cudaSuccess) return e;
+    int dev = 0, max_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes attr;
+    if ((e = cudaFuncGetAttributes(&attr, fn)) != cudaSuccess) return e;
+    // One block per SM; rows split evenly; cache as many rows as fit.
+    int64_t G = std::max<int64_t>(1, std::min<int64_t>({(int64_t)num_sms, ceil_div(R, 32), (int64_t)kMaxBlocks}));
+    const int64_t rows_per = ceil_div(R, G);
+    if (rows_per > kMaxRowsPerBlock) return cudaErrorInvalidValue;
+    const size_t flags = (size_t)round_up(rows_per, 16);
+    const size_t avail = (size_t)max_optin - attr.sharedSizeBytes - flags - 1024;
+    int cache_rows = (int)std::min<int64_t>(rows_per, (int64_t)(avail / (es * l)));
+    if (cache_rows < 0) cache_rows = 0;
+    const size_t smem = es * (size_t)cache_rows * l + flags;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kLuThreads, smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    int64_t G = std::min<int64_t>((int64_t)num_sms, ceil_div(R, 64));
-    G = std::max<int64_t>(1, std::min<int64_t>(G, std::min<int64_t>(kMaxBlocks, (int64_t)per_sm * num_sms)));
+    G = std::min<int64_t>(G, (int64_t)per_sm * num_sms);
     void *Mp = M;
     int64_t Rv = R, ldv = ld;
-    int lv = l;
-    void *args[] = {&Rv, &lv, &Mp, &ldv, &piv, &cand, &bar, &pivflag, &d_status};
+    int lv = l, cr = cache_rows;
+    void *args[] = {&Rv, &lv, &Mp, &ldv, &piv, &cand, &bar, &cr, &d_status};
     count_launch();
-    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kLuThreads), args, 0, s);
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kLuThreads), args, smem, s);
 }
 
 }  // namespace frpca
