@@ -54,8 +54,10 @@ __device__ inline int dim_of(const int *dn, int n_static) { return dn ? *dn : n_
 
 // Float Jacobi on the n x n block of B (leading dimension ld), scaled by its
 // largest diagonal magnitude.  Writes the eigenvectors (columns) into X (ld).
-// A pair is rotated while |a_pq| > 2^-22 max|a_ii|; the sweep loop stops at
-// the first sweep without rotations.
+// A pair is rotated while |a_pq| > 2^-23 sqrt(|a_pp a_qq|) (the relative test
+// that lets Jacobi resolve small eigenvalues of a definite matrix to float
+// accuracy); the sweep loop stops at the first sweep without rotations or
+// after kJacobiMaxSweeps.
 __global__ void __launch_bounds__(kJacobiThreads)
 jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int ld, double *__restrict__ X) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -88,7 +90,6 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
         if (a <= b) blk[a * nb - a * (a - 1) / 2 + (b - a)] = make_ushort2((unsigned short)a, (unsigned short)b);
     }
     __syncthreads();
-    const float tol = 0x1p-22f;  // relative to max |a_ii| = 1 after scaling
 
     for (int sweep = 0; sweep < kJacobiMaxSweeps; ++sweep) {
         if (threadIdx.x == 0) rotations = 0;
@@ -100,7 +101,7 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
                 float c = 1.0f, s = 0.0f;
                 if (q < n) {
                     const float apq = A[p * np + q], app = A[p * np + p], aqq = A[q * np + q];
-                    if (fabsf(apq) > tol) {
+                    if (apq != 0.0f && fabsf(apq) > 0x1p-23f * sqrtf(fabsf(app) * fabsf(aqq))) {
                         const float tau = (aqq - app) / (2.0f * apq);
                         const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
                         c = 1.0f / sqrtf(1.0f + t * t);
@@ -210,6 +211,10 @@ __device__ inline double block_sum(double v, double *red) {
 }
 
 // One CTA: lambda, delta and E from G = X^T X and S = X^T C X (n x n, ld).
+// Pairs whose eigenvalues both lie below kTau * max|lambda| are treated as one
+// cluster (orthogonalized only): float cannot separate them at this level, a
+// first-order rotation between them would be unreliable, and the next
+// deflation level resolves them.
 __global__ void oa_update_kernel(const int *dn, int n_static, int ld, const double *__restrict__ Cm,
                                  const double *__restrict__ Gm, const double *__restrict__ S, double *__restrict__ E,
                                  double *__restrict__ lam) {
@@ -217,8 +222,16 @@ __global__ void oa_update_kernel(const int *dn, int n_static, int ld, const doub
     if (n < 1) return;
     __shared__ double red[32];
     __shared__ double lam_s[FRPCA_MAX_L];
+    __shared__ double lam_top;
     for (int i = threadIdx.x; i < n; i += blockDim.x) lam_s[i] = S[i * ld + i] / Gm[i * ld + i];
     __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) t = fmax(t, fabs(lam_s[i]));
+        lam_top = t;
+    }
+    __syncthreads();
+    const double low = kTau * lam_top;
     double sS = 0.0, sB = 0.0, sR = 0.0;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const int i = idx / n, j = idx - i * n;
@@ -237,7 +250,8 @@ __global__ void oa_update_kernel(const int *dn, int n_static, int ld, const doub
         const int i = idx / n, j = idx - i * n;
         const double rij = (i == j ? 1.0 : 0.0) - Gm[i * ld + j];
         const double gap = lam_s[j] - lam_s[i];
-        E[i * ld + j] = (fabs(gap) > delta) ? (S[i * ld + j] + lam_s[j] * rij) / gap : 0.5 * rij;
+        const bool both_low = fabs(lam_s[i]) < low && fabs(lam_s[j]) < low;
+        E[i * ld + j] = (fabs(gap) > delta && !both_low) ? (S[i * ld + j] + lam_s[j] * rij) / gap : 0.5 * rij;
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = lam_s[i];
 }

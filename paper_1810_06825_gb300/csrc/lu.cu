@@ -104,16 +104,30 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
     bool ok = grid_barrier(bar, G, status, kBarrierLimitCycles);
 
     for (int j = 0; j < l && ok; ++j) {
-        // (1) the pivot of column j, identical in every block.
-        if (threadIdx.x == 0) {
+        // (1) the pivot of column j, identical in every block: thread k reads
+        // block k's candidate, then a block-wide (max, smallest row) reduction.
+        {
             double b = 0.0;
             int64_t r = -1;
             const Cand *cs = cand + (j & 1) * G;
-            for (unsigned k = 0; k < G; ++k) {
+            for (unsigned k = threadIdx.x; k < G; k += kLuThreads) {
                 const double cb = __ldcg(&cs[k].absval);
                 const int64_t cr = __ldcg(&cs[k].row);
                 if (better(cb, cr, b, r)) { b = cb; r = cr; }
             }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_down_sync(0xffffffffu, b, o);
+                const int64_t orr = __shfl_down_sync(0xffffffffu, r, o);
+                if (better(ob, orr, b, r)) { b = ob; r = orr; }
+            }
+            if (lane == 0) { wbest[warp] = b; wrow[warp] = r; }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            double b = 0.0;
+            int64_t r = -1;
+            for (int w = 0; w < kLuWarps; ++w)
+                if (better(wbest[w], wrow[w], b, r)) { b = wbest[w]; r = wrow[w]; }
             s_p = r;
             s_stop = (r < 0);
             pivots[j] = r;

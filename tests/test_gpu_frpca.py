@@ -148,9 +148,10 @@ def powerlaw_200k():
 
 
 @pytest.mark.parametrize("q", [4, 5])
-def test_frpca_powerlaw_200000x50000_fp32(powerlaw_200k, q):
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_frpca_powerlaw_200000x50000(powerlaw_200k, q, prec):
     """The 200,000 x 50,000 (~20M nnz) power-law workload, k=100, l=120, FP32
-    path, against the FP64 oracle on the same Gaussian test matrix."""
-    A = powerlaw_200k
-    S, So = _compare(A, 100, 120, q, 0, "fp32")
-    print(f"q={q} max sigma rel err {np.max(np.abs(S - So) / So):.3e}")
+    and FP64 paths, against the FP64 oracle on the same Gaussian test matrix."""
+    A = powerlaw_200k if prec == "fp32" else powerlaw_200k.astype(np.float64)
+    S, So = _compare(A, 100, 120, q, 0, prec)
+    print(f"{prec} q={q} max sigma rel err {np.max(np.abs(S - So) / So):.3e}")
