@@ -81,9 +81,10 @@ def _load():
     lib.or_gram.argtypes = [I64, I64, P, I64, P]
     lib.or_eigsvd.argtypes = [I64, I64, P, I64, P, I64, P, P]
     lib.or_frpca.argtypes = [ctypes.c_int, I64, I64, P, P, P, I64, I64, I64, U64, P, P, P]
+    lib.or_frpca_ex.argtypes = [ctypes.c_int, I64, I64, P, P, P, I64, I64, I64, U64, ctypes.c_int, P, P, P]
     lib.or_num_threads.argtypes = []
     for name in ("or_gaussian", "or_csr_transpose", "or_spmm", "or_spmm_t", "or_lu_ptl", "or_eig_sym",
-                 "or_gram", "or_eigsvd", "or_frpca", "or_num_threads"):
+                 "or_gram", "or_eigsvd", "or_frpca", "or_frpca_ex", "or_num_threads"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -196,13 +197,19 @@ def eigsvd(M: np.ndarray):
     return U, S, V
 
 
-def frpca(m: int, n: int, indptr, indices, data, k: int, l: int, q: int, seed: int, alg: int | None = None):
-    """Alg. 5 / Alg. 6.  ``alg=None`` applies the shape rule (Alg. 6 when m >= n)."""
+def frpca(m: int, n: int, indptr, indices, data, k: int, l: int, q: int, seed: int, alg: int | None = None,
+          stabilize: bool = False):
+    """Alg. 5 / Alg. 6.  ``alg=None`` applies the shape rule (Alg. 6 when m >= n).
+
+    ``stabilize=True`` runs the last power-iteration orthonormalization as
+    eigSVD(lu(M)) (same range by Lemma 3, same result in exact arithmetic).
+    """
     indptr, indices, data = _csr(indptr, indices, data)
     if alg is None:
         alg = 6 if m >= n else 5
     U = np.empty((m, k), dtype=np.float64)
     S = np.empty(k, dtype=np.float64)
     V = np.empty((n, k), dtype=np.float64)
-    _check(_load().or_frpca(alg, m, n, _p(indptr), _p(indices), _p(data), k, l, q, seed, _p(U), _p(S), _p(V)), "frpca")
+    _check(_load().or_frpca_ex(alg, m, n, _p(indptr), _p(indices), _p(data), k, l, q, seed, int(stabilize),
+                               _p(U), _p(S), _p(V)), "frpca")
     return U, S, V

@@ -384,6 +384,18 @@ static int orth_step(int use_eigsvd, int64_t R, int64_t l, double *M) {
 int or_frpca(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
              const double *vals, int64_t k, int64_t l, int64_t q, uint64_t seed,
              double *U, double *S, double *V) {
+    return or_frpca_ex(alg, m, n, rowptr, colidx, vals, k, l, q, seed, 0, U, S, V);
+}
+
+/* stabilize != 0: the last orthonormalization of the power iteration is
+ * eigSVD(lu(M)) instead of eigSVD(M).  lu() keeps range(M) (Lemma 3) and the
+ * result depends only on that range (Lemma 2), so in exact arithmetic this is
+ * the same Alg. 5/6; in floating point eigSVD then squares the condition
+ * number of the unit-lower factor instead of that of A^T A Q, and the
+ * orthonormal basis it returns is correspondingly more accurate. */
+int or_frpca_ex(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                const double *vals, int64_t k, int64_t l, int64_t q, uint64_t seed, int stabilize,
+                double *U, double *S, double *V) {
     if (alg != 5 && alg != 6) return OR_ERR_INVALID_ARG;
     if (alg == 6 && m < n) return OR_ERR_INVALID_ARG;
     if (alg == 5 && m > n) return OR_ERR_INVALID_ARG;
@@ -416,6 +428,7 @@ int or_frpca(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int32_t
     for (int64_t i = 1; i <= loops && st == OR_OK; ++i) {
         st = FWD(Q, W);
         if (st == OR_OK) st = BWD(W, Q);
+        if (st == OR_OK && i == loops && stabilize) st = orth_step(0, rq, l, Q);
         if (st == OR_OK) st = orth_step(i == loops, rq, l, Q);
     }
     if (st == OR_OK) {

@@ -60,5 +60,12 @@ int or_frpca(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int32_t
              const double *vals, int64_t k, int64_t l, int64_t q, uint64_t seed,
              double *U, double *S, double *V);
 
+/* Same, with stabilize != 0 running the last power-iteration orthonormalization
+ * as eigSVD(lu(M)) (Lemma 3 keeps the range, so Alg. 5/6 are unchanged in
+ * exact arithmetic). */
+int or_frpca_ex(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                const double *vals, int64_t k, int64_t l, int64_t q, uint64_t seed, int stabilize,
+                double *U, double *S, double *V);
+
 int or_num_threads(void);
 #endif

@@ -272,13 +272,16 @@ def _theorem_case(tall):
 
 @pytest.mark.parametrize("q", [2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("tall", [True, False])
-def test_frpca_equals_qr_scheme(oracle_lib, q, tall):
+@pytest.mark.parametrize("stabilize", [False, True])
+def test_frpca_equals_qr_scheme(oracle_lib, q, tall, stabilize):
     """Pin 3: Theorem 2 (Alg. 6 vs Alg. 4) and Theorem 1 (Alg. 5 vs Alg. 1) with
-    p = (q-2)/2 on the same Omega; odd q against the modified power iteration."""
+    p = (q-2)/2 on the same Omega; odd q against the modified power iteration.
+    The stabilized schedule (an extra lu() before the last eigSVD, Lemma 3)
+    must give the same result."""
     from oracle import qr_scheme
     A = _theorem_case(tall)
     k, l = 8, 14
-    U, S, V = oracle_lib.frpca(A.m, A.n, A.indptr, A.indices, A.data, k, l, q, seed=4)
+    U, S, V = oracle_lib.frpca(A.m, A.n, A.indptr, A.indices, A.data, k, l, q, seed=4, stabilize=stabilize)
     base = qr_scheme.rpca_t if tall else qr_scheme.rpca
     if q % 2 == 0:
         Ur, Sr, Vr = base(A.m, A.n, A.indptr, A.indices, A.data, k, l, (q - 2) // 2, seed=4)
