@@ -37,7 +37,7 @@ def _cpu(t):
     return t.detach().double().cpu().numpy()
 
 
-def _compare(A, k, l, q, seed, prec, alg=None, mat=None, stabilize=False):
+def _compare(A, k, l, q, seed, prec, alg=None, mat=None, stabilize=False, angle_tol=None):
     Uo, So, Vo = oracle.frpca(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64), k, l, q, seed, alg=alg,
                               stabilize=stabilize)
     own = mat is None
@@ -48,6 +48,7 @@ def _compare(A, k, l, q, seed, prec, alg=None, mat=None, stabilize=False):
     if own:
         mat.close()
     stol, atol = TOL[prec]
+    atol = angle_tol or atol
     assert np.all(np.diff(S) <= 0)
     assert np.max(np.abs(S - So) / So) <= stol, np.max(np.abs(S - So) / So)
     assert max_principal_sine(U, Uo) <= atol
@@ -162,10 +163,12 @@ def test_frpca_powerlaw_200000x50000(powerlaw_200k, q, prec):
     eps * kappa^2 ~ 1e-8, which moves its singular values by up to ~5e-10.
     The FP64 path is therefore held to 1e-10 against the oracle's stabilized
     schedule (lu() before that eigSVD; Lemma 3, identical in exact
-    arithmetic) and to 1e-8 against the plain one."""
+    arithmetic) and to 1e-8 against the plain one.  sigma_100 and sigma_101
+    are only ~1e-3 apart in relative terms, so the top-100 subspaces are
+    compared at 1e-6 in FP64 (rounding-level perturbations over that gap)."""
     A = powerlaw_200k if prec == "fp32" else powerlaw_200k.astype(np.float64)
     if prec == "fp64":
-        S, So = _compare(A, 100, 120, q, 0, prec, stabilize=True)
+        S, So = _compare(A, 100, 120, q, 0, prec, stabilize=True, angle_tol=1e-6)
         _, So_plain, _ = oracle.frpca(A.m, A.n, A.indptr, A.indices, A.data, 100, 120, q, 0)
         dev = np.max(np.abs(S - So_plain) / So_plain)
         print(f"fp64 q={q} vs plain-schedule oracle {dev:.3e}")
