@@ -173,6 +173,25 @@ frpca_status frpca_get_transpose(frpca_handle h, int64_t *rowptrT, int32_t *coli
  * Synchronizes; FRPCA_ERR_SINGULAR_PIVOT when a column has no nonzero pivot. */
 frpca_status frpca_lu(frpca_handle h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv);
 
+/* frpca_lu without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- for example a
+ * process whose device memory is already fully reserved by another allocator,
+ * or a latency-critical loop that must not take the device-wide
+ * synchronization that cudaMalloc and cudaFree can imply.  It needs no handle:
+ * M (R x l, leading dimension ld, device, in place), piv (nullable, device, l
+ * int64) and the stream (cudaStream_t as void*, NULL = legacy default) are the
+ * caller's; the result is exactly that of frpca_lu.  The kernel's scratch (grid
+ * barrier, pivot candidates, status word) lives in one static 64 KiB device
+ * array that every GPU loading this library holds until the process exits.
+ * Limits: 1 <= l <= 160 and R <= 8192 times the number of SMs; larger sizes
+ * return FRPCA_ERR_INVALID_ARG with a message from frpca_last_error(NULL).
+ * The first call on each device looks up the array's device address once
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array and clears the parts that must start at
+ * zero, so calls that overlap on the GPU (other streams, other host threads)
+ * race: serialize them.  Synchronizes the stream to read the status. */
+frpca_status frpca_lu_noalloc(int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv, void *stream);
+
 /* Step 1 of eigSVD (Alg. 2): B = M^T M, l x l double (ld l), M R x l.  FP32
  * input is accumulated in float inside a tile of rows and in double across
  * tiles; FP64 input in double throughout. */

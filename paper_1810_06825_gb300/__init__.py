@@ -90,6 +90,7 @@ def library() -> ctypes.CDLL:
         "frpca_spmm": [P, I, I, P, I64, P, I64, I],
         "frpca_get_transpose": [P, P, P, P],
         "frpca_lu": [P, I64, I, P, I64, I, P],
+        "frpca_lu_noalloc": [I64, I, P, I64, I, P, P],
         "frpca_gram": [P, I64, I, P, I64, I, P],
         "frpca_eig": [P, I, P, P, P],
         "frpca_eigsvd": [P, I64, I, P, I64, I, P, P],
@@ -171,6 +172,11 @@ def frpca_get_transpose(h, rowptrT, colidxT, valuesT) -> None:
 
 def frpca_lu(h, R, l, M, ld, dtype, piv) -> None:
     _check(library().frpca_lu(h, R, l, M, ld, dtype, piv), h)
+
+
+def frpca_lu_noalloc(R, l, M, ld, dtype, piv, stream) -> None:
+    """frpca_lu without device allocation (static scratch); see include/frpca.h."""
+    _check(library().frpca_lu_noalloc(R, l, M, ld, dtype, piv, stream), None)
 
 
 def frpca_gram(h, R, l, M, ld, dtype, B) -> None:

@@ -41,15 +41,18 @@ struct frpca_ctx {
     int64_t launch_base = 0;
 };
 
+namespace {
+thread_local std::string g_create_error;
+}  // namespace
+
 namespace frpca {
+void set_thread_error(const std::string &msg) { g_create_error = msg; }
 static std::atomic<int64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace frpca
 
 namespace {
-
-thread_local std::string g_create_error;
 
 enum Phase { PH_SPMM, PH_LU, PH_GRAM, PH_EIG, PH_APPLY, PH_GAUSS, PH_TRANSPOSE, PH_FINISH, PH_COUNT };
 

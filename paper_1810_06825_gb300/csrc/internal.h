@@ -72,8 +72,12 @@ size_t spmm_scratch_bytes(const SpmmPlan &plan, int l, frpca_dtype dt);
 cudaError_t launch_spmm(const DeviceCSR &A, const void *vals, const SpmmPlan &plan, int l, const void *X,
                         int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *scratch, cudaStream_t s);
 
+// ---- capi.cu: message returned by frpca_last_error(NULL) on this thread
+void set_thread_error(const std::string &msg);
+
 // ---- lu.cu
 size_t lu_workspace_bytes(int64_t R, int l);
+int lu_max_rows_per_block();
 cudaError_t launch_lu(int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv, void *ws,
                       int *d_status, int num_sms, cudaStream_t s);
 

@@ -213,6 +213,8 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
 
 }  // namespace
 
+int lu_max_rows_per_block() { return kMaxRowsPerBlock; }
+
 size_t lu_workspace_bytes(int64_t R, int l) {
     (void)R;
     (void)l;
