@@ -4,11 +4,11 @@
 //
 // GB300 has little double-precision throughput, so the result is reached in
 // stages that keep double-precision work in GEMMs spread over many SMs.
-//  (1) One CTA runs cyclic Jacobi in float on the (scaled, rounded) matrix, the
-//      matrix and the eigenvector accumulator resident in shared memory; each
-//      sweep visits all pairs in the round-robin order, so every round applies
-//      n/2 disjoint rotations at once (Golub and Van Loan, Matrix Computations,
-//      Sec. 8.5, parallel Jacobi).
+//  (1) Cyclic Jacobi in float on the (scaled, rounded) matrix, resident in
+//      shared memory; each sweep visits all pairs in the round-robin order, so
+//      every round applies n/2 disjoint rotations at once (Golub and Van Loan,
+//      Matrix Computations, Sec. 8.5, parallel Jacobi).  A few CTAs repeat the
+//      same rotations and split the rows of the eigenvector accumulator.
 //  (2) The float eigenvectors X are refined in double by the iteration of
 //      Ogita and Aishima ("Iterative refinement for symmetric eigenvalue
 //      decomposition", Japan J. Indust. Appl. Math. 35, 2018): with
@@ -32,6 +32,7 @@ namespace frpca {
 namespace {
 
 constexpr int kJacobiThreads = 1024;
+constexpr int kJacobiCtas = 8;  // CTAs sharing the rows of V (each holds all of A)
 constexpr int kJacobiMaxSweeps = 24;
 constexpr int kRefineSteps = 5;
 constexpr int kLevels = 3;
@@ -58,6 +59,11 @@ __device__ inline int dim_of(const int *dn, int n_static) { return dn ? *dn : n_
 // that lets Jacobi resolve small eigenvalues of a definite matrix to float
 // accuracy); the sweep loop stops at the first sweep without rotations or
 // after kJacobiMaxSweeps.
+//
+// The round is bound by shared-memory traffic, so the work is split over
+// gridDim.x CTAs without any communication: every CTA runs the same
+// deterministic sequence of rotations on its own copy of A (only the upper
+// triangle is updated) and accumulates only its own slice of the rows of V.
 __global__ void __launch_bounds__(kJacobiThreads)
 jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int ld, double *__restrict__ X) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -66,9 +72,13 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
     const int np = n + (n & 1);
     const int nb = np / 2;
     const int nblk = nb * (nb + 1) / 2;
+    const int vrows = (np + gridDim.x - 1) / gridDim.x;
+    const int v0 = blockIdx.x * vrows;
+    const int vcnt = max(0, min(vrows, np - v0));
     float *A = reinterpret_cast<float *>(smem_raw);
-    float *V = A + np * np;
-    ushort2 *blk = reinterpret_cast<ushort2 *>(V + np * np);
+    float *V = A + np * np;  // rows v0 .. v0 + vcnt - 1 of V
+    ushort2 *blk = reinterpret_cast<ushort2 *>(V + (size_t)vrows * np);
+    auto up = [np](int r, int c) { return r <= c ? r * np + c : c * np + r; };
     __shared__ float cs_c[FRPCA_MAX_L / 2], cs_s[FRPCA_MAX_L / 2];
     __shared__ int pp[FRPCA_MAX_L / 2], qq[FRPCA_MAX_L / 2];
     __shared__ int rotations;
@@ -83,6 +93,9 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
     for (int idx = threadIdx.x; idx < np * np; idx += kJacobiThreads) {
         const int i = idx / np, j = idx - i * np;
         A[idx] = (i < n && j < n) ? (float)(B[i * ld + j] * scale) : 0.0f;
+    }
+    for (int idx = threadIdx.x; idx < vcnt * np; idx += kJacobiThreads) {
+        const int i = v0 + idx / np, j = idx % np;
         V[idx] = (i == j) ? 1.0f : 0.0f;
     }
     for (int idx = threadIdx.x; idx < nb * nb; idx += kJacobiThreads) {
@@ -115,37 +128,32 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
                 qq[threadIdx.x] = q;
             }
             __syncthreads();
-            const int total = nblk + np * nb;
+            const int total = nblk + vcnt * nb;
             for (int idx = threadIdx.x; idx < total; idx += kJacobiThreads) {
                 if (idx < nblk) {
-                    // A <- J^T A J on the 2x2 block of pairs (ka, kb) and its mirror.
+                    // A <- J^T A J on the 2x2 block of pairs (ka, kb), upper triangle.
                     const ushort2 ab = blk[idx];
                     const int ka = ab.x, kb = ab.y;
                     const float ca = cs_c[ka], sa = cs_s[ka], cb = cs_c[kb], sb = cs_s[kb];
                     if (sa == 0.0f && sb == 0.0f) continue;
                     const int pa = pp[ka], qa = qq[ka], pb = pp[kb], qb = qq[kb];
-                    const float a11 = A[pa * np + pb], a12 = A[pa * np + qb];
-                    const float a21 = A[qa * np + pb], a22 = A[qa * np + qb];
+                    const int i11 = up(pa, pb), i12 = up(pa, qb), i21 = up(qa, pb), i22 = up(qa, qb);
+                    const float a11 = A[i11], a12 = A[i12], a21 = A[i21], a22 = A[i22];
                     const float t11 = ca * a11 - sa * a21, t12 = ca * a12 - sa * a22;
                     const float t21 = sa * a11 + ca * a21, t22 = sa * a12 + ca * a22;
-                    float n11 = t11 * cb - t12 * sb, n12 = t11 * sb + t12 * cb;
-                    float n21 = t21 * cb - t22 * sb, n22 = t21 * sb + t22 * cb;
+                    const float n11 = t11 * cb - t12 * sb, n22 = t21 * sb + t22 * cb;
                     if (ka == kb) {
-                        n12 = 0.0f;
-                        n21 = 0.0f;
-                    }
-                    A[pa * np + pb] = n11;
-                    A[pa * np + qb] = n12;
-                    A[qa * np + pb] = n21;
-                    A[qa * np + qb] = n22;
-                    if (ka != kb) {
-                        A[pb * np + pa] = n11;
-                        A[qb * np + pa] = n12;
-                        A[pb * np + qa] = n21;
-                        A[qb * np + qa] = n22;
+                        A[i11] = n11;
+                        A[i12] = 0.0f;  // (pa, qa): the rotation annihilates it
+                        A[i22] = n22;
+                    } else {
+                        A[i11] = n11;
+                        A[i12] = t11 * sb + t12 * cb;
+                        A[i21] = t21 * cb - t22 * sb;
+                        A[i22] = n22;
                     }
                 } else {
-                    // V <- V J, one row and one pair.
+                    // V <- V J, one row of this CTA's slice and one pair.
                     const int v = idx - nblk;
                     const int row = v / nb, k = v - row * nb;
                     const float c = cs_c[k], s = cs_s[k];
@@ -161,9 +169,9 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
         if (rotations == 0) break;
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < n * n; idx += kJacobiThreads) {
-        const int i = idx / n, j = idx - i * n;
-        X[i * ld + j] = (double)V[i * np + j];
+    for (int idx = threadIdx.x; idx < vcnt * n; idx += kJacobiThreads) {
+        const int r = idx / n, j = idx - r * n;
+        if (v0 + r < n) X[(v0 + r) * ld + j] = (double)V[r * np + j];
     }
 }
 
@@ -210,33 +218,26 @@ __device__ inline double block_sum(double v, double *red) {
     return red[0];
 }
 
-// One CTA: lambda, delta and E from G = X^T X and S = X^T C X (n x n, ld).
-// Pairs whose eigenvalues both lie below kTau * max|lambda| are treated as one
-// cluster (orthogonalized only): float cannot separate them at this level, a
-// first-order rotation between them would be unreliable, and the next
-// deflation level resolves them.
-__global__ void oa_update_kernel(const int *dn, int n_static, int ld, const double *__restrict__ Cm,
-                                 const double *__restrict__ Gm, const double *__restrict__ S, double *__restrict__ E,
-                                 double *__restrict__ lam) {
-    const int n = dim_of(dn, n_static);
-    if (n < 1) return;
+// lambda_i = S_ii / (1 - R_ii) = S_ii / G_ii.
+__device__ inline double oa_lambda(const double *S, const double *Gm, int ld, int i) {
+    return S[i * ld + i] / Gm[i * ld + i];
+}
+
+constexpr int kOaRows = 4;  // rows of E per CTA
+
+// Partial sums of |S - diag(lambda)|_F^2, |C|_F^2 and |R|_F^2 over kOaRows rows.
+__global__ void oa_norms_kernel(const int *dn, int ld, const double *__restrict__ Cm, const double *__restrict__ Gm,
+                                const double *__restrict__ S, double *__restrict__ part) {
+    const int n = *dn;
+    const int r0 = blockIdx.x * kOaRows;
+    if (n < 1 || r0 >= n) return;
     __shared__ double red[32];
-    __shared__ double lam_s[FRPCA_MAX_L];
-    __shared__ double lam_top;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) lam_s[i] = S[i * ld + i] / Gm[i * ld + i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < n; ++i) t = fmax(t, fabs(lam_s[i]));
-        lam_top = t;
-    }
-    __syncthreads();
-    const double low = kTau * lam_top;
     double sS = 0.0, sB = 0.0, sR = 0.0;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int i = idx / n, j = idx - i * n;
+    const int r1 = min(n, r0 + kOaRows);
+    for (int idx = threadIdx.x; idx < (r1 - r0) * n; idx += blockDim.x) {
+        const int i = r0 + idx / n, j = idx % n;
         const double rij = (i == j ? 1.0 : 0.0) - Gm[i * ld + j];
-        const double d = (i == j) ? S[i * ld + j] - lam_s[i] : S[i * ld + j];
+        const double d = (i == j) ? S[i * ld + j] - oa_lambda(S, Gm, ld, i) : S[i * ld + j];
         const double b = Cm[i * ld + j];
         sS += d * d;
         sB += b * b;
@@ -245,15 +246,60 @@ __global__ void oa_update_kernel(const int *dn, int n_static, int ld, const doub
     sS = block_sum(sS, red);
     sB = block_sum(sB, red);
     sR = block_sum(sR, red);
-    const double delta = 2.0 * (sqrt(sS) + sqrt(sB) * sqrt(sR));
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int i = idx / n, j = idx - i * n;
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x + 0] = sS;
+        part[3 * blockIdx.x + 1] = sB;
+        part[3 * blockIdx.x + 2] = sR;
+    }
+}
+
+// 1/g to double accuracy: float reciprocal, one Newton step in double.
+__device__ inline double recip(double g) {
+    const double ag = fabs(g);
+    if (!(ag > 1e-30 && ag < 1e30)) return 1.0 / g;
+    const double r0 = (double)__frcp_rn((float)g);
+    const double e = fma(-g, r0, 1.0);
+    return fma(r0, e, r0);
+}
+
+// E for kOaRows rows (see the header): pairs separated by more than delta are
+// rotated to first order; pairs closer than delta, and pairs whose eigenvalues
+// both lie below kTau * max|lambda|, are only orthogonalized (E_ij = R_ij / 2):
+// float cannot separate the latter at this level, a first-order rotation
+// between them would be unreliable, and the next deflation level resolves them.
+__global__ void oa_e_kernel(const int *dn, int ld, const double *__restrict__ Gm, const double *__restrict__ S,
+                            const double *__restrict__ part, double *__restrict__ E, double *__restrict__ lam) {
+    const int n = *dn;
+    const int r0 = blockIdx.x * kOaRows;
+    if (n < 1 || r0 >= n) return;
+    __shared__ double lam_s[FRPCA_MAX_L];
+    __shared__ double s_delta, s_low;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lam_s[i] = oa_lambda(S, Gm, ld, i);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sS = 0.0, sB = 0.0, sR = 0.0, top = 0.0;
+        const int nparts = (n + kOaRows - 1) / kOaRows;
+        for (int p = 0; p < nparts; ++p) {
+            sS += part[3 * p];
+            sB += part[3 * p + 1];
+            sR += part[3 * p + 2];
+        }
+        for (int i = 0; i < n; ++i) top = fmax(top, fabs(lam_s[i]));
+        s_delta = 2.0 * (sqrt(sS) + sqrt(sB) * sqrt(sR));
+        s_low = kTau * top;
+    }
+    __syncthreads();
+    const double delta = s_delta, low = s_low;
+    const int r1 = min(n, r0 + kOaRows);
+    for (int idx = threadIdx.x; idx < (r1 - r0) * n; idx += blockDim.x) {
+        const int i = r0 + idx / n, j = idx % n;
         const double rij = (i == j ? 1.0 : 0.0) - Gm[i * ld + j];
         const double gap = lam_s[j] - lam_s[i];
         const bool both_low = fabs(lam_s[i]) < low && fabs(lam_s[j]) < low;
-        E[i * ld + j] = (fabs(gap) > delta && !both_low) ? (S[i * ld + j] + lam_s[j] * rij) / gap : 0.5 * rij;
+        E[i * ld + j] = (fabs(gap) > delta && !both_low) ? fma(lam_s[j], rij, S[i * ld + j]) * recip(gap) : 0.5 * rij;
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = lam_s[i];
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = lam_s[i];
 }
 
 // After a level: sort the active block ascending by lambda (its columns of X,
@@ -318,7 +364,7 @@ __global__ void copy_out_kernel(int n, int ld, const double *__restrict__ lam_al
 
 size_t eig_workspace_bytes(int n) {
     const size_t ld = FRPCA_MAX_L;
-    return sizeof(double) * (10 * ld * ld + 2 * ld) + 64 * sizeof(int) + 256;
+    return sizeof(double) * (10 * ld * ld + 5 * ld) + 64 * sizeof(int) + 256;
 }
 
 cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, int *d_status, cudaStream_t s) {
@@ -328,7 +374,8 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
     double *base = (double *)ws;
     double *X = base, *Xn = X + nn, *Cm = Xn + nn, *Z = Cm + nn, *Z2 = Z + nn, *G = Z2 + nn, *T = G + nn,
            *S = T + nn, *E = S + nn, *Bl = E + nn, *lam_b = Bl + nn, *lam_all = lam_b + ld;
-    int *dims = (int *)(lam_all + ld);
+    double *Pn = lam_all + ld;  // norm partials, 3 per row group
+    int *dims = (int *)(Pn + 3 * ld);
     cudaError_t e;
     // B copied to leading dimension ld.
     e = cudaMemcpy2DAsync(Bl, sizeof(double) * ld, B, sizeof(double) * n, sizeof(double) * n, n,
@@ -336,7 +383,9 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
     if (e != cudaSuccess) return e;
     const int np = n + (n & 1);
     const int nb = np / 2;
-    const size_t smem = sizeof(float) * 2 * np * np + sizeof(ushort2) * (size_t)nb * (nb + 1) / 2;
+    const int vrows = (np + kJacobiCtas - 1) / kJacobiCtas;
+    const size_t smem = sizeof(float) * ((size_t)np * np + (size_t)vrows * np) +
+                        sizeof(ushort2) * (size_t)nb * (nb + 1) / 2;
     if ((e = cudaFuncSetAttribute(jacobi_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
@@ -348,15 +397,16 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
         // C = Xa^T B Xa on the active columns (the first b columns of X).
         gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, nullptr, n, 0, n, ld, Bl, X, nullptr, T);
         gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, nullptr, 0, 0, n, ld, X, T, nullptr, Cm);
-        jacobi_f32_kernel<<<1, kJacobiThreads, smem, s>>>(db, 0, Cm, ld, Z);
+        jacobi_f32_kernel<<<kJacobiCtas, kJacobiThreads, smem, s>>>(db, 0, Cm, ld, Z);
         count_launch(3);
         for (int it = 0; it < kRefineSteps; ++it) {
             gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Z, Z, nullptr, G);   // Z^T Z
             gemm64_kernel<false><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Cm, Z, nullptr, T); // C Z
             gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Z, T, nullptr, S);   // Z^T C Z
-            oa_update_kernel<<<1, 1024, 0, s>>>(db, 0, ld, Cm, G, S, E, lam_b);
+            oa_norms_kernel<<<(n + kOaRows - 1) / kOaRows, 256, 0, s>>>(db, ld, Cm, G, S, Pn);
+            oa_e_kernel<<<(n + kOaRows - 1) / kOaRows, 256, 0, s>>>(db, ld, G, S, Pn, E, lam_b);
             gemm64_kernel<false><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Z, E, Z, Z2);       // Z + Z E
-            count_launch(5);
+            count_launch(6);
             std::swap(Z, Z2);
         }
         // Xa <- Xa Z, then sort the active block and choose the next one.
