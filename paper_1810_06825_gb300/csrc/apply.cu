@@ -115,13 +115,23 @@ __global__ void col_best_kernel(int64_t R, int k, const T *__restrict__ X, int64
     }
 }
 
+// One warp per column: lanes stride over the partials, then a warp reduction
+// with the same (magnitude, smallest row) order.
 __global__ void col_sign_kernel(int k, int nparts, const ColBest *__restrict__ part, double *__restrict__ sign) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
-        ColBest b{-1.0, -1, 1.0};
-        for (int p = 0; p < nparts; ++p)
-            if (col_better(part[(int64_t)p * k + j], b)) b = part[(int64_t)p * k + j];
-        sign[j] = b.sgn;
+    const int lane = threadIdx.x & 31;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= k) return;
+    ColBest b{-1.0, -1, 1.0};
+    for (int p = lane; p < nparts; p += 32)
+        if (col_better(part[(int64_t)p * k + j], b)) b = part[(int64_t)p * k + j];
+    for (int o = 16; o > 0; o >>= 1) {
+        ColBest c;
+        c.absval = __shfl_down_sync(0xffffffffu, b.absval, o);
+        c.row = __shfl_down_sync(0xffffffffu, b.row, o);
+        c.sgn = __shfl_down_sync(0xffffffffu, b.sgn, o);
+        if (col_better(c, b)) b = c;
     }
+    if (lane == 0) sign[j] = b.sgn;
 }
 
 template <typename T>
@@ -198,7 +208,7 @@ cudaError_t launch_column_signs(int64_t R, int k, const void *X, int64_t ld, frp
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    col_sign_kernel<<<(k + 127) / 128, 128, 0, s>>>(k, G, part, sign); count_launch();
+    col_sign_kernel<<<(k * 32 + 127) / 128, 128, 0, s>>>(k, G, part, sign); count_launch();
     return cudaGetLastError();
 }
 

@@ -170,7 +170,7 @@ __global__ void gram_reduce_kernel(int l, int nparts, const double *__restrict__
 }
 
 int gram_blocks(int64_t R, int num_sms) {
-    const int64_t want = std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)num_sms, ceil_div(R, 256)));
+    const int64_t want = std::max<int64_t>(1, std::min<int64_t>(4 * (int64_t)num_sms, ceil_div(R, 128)));
     return (int)want;
 }
 

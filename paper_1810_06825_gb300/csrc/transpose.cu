@@ -199,9 +199,18 @@ __global__ void radix_scatter_kernel(const uint32_t *__restrict__ keys, const in
     }
 }
 
+// Column histogram.  Hot columns (a power-law matrix can put ~m entries in one
+// column) would serialize plain atomics, so equal columns within a warp are
+// combined first and one lane adds their count.
 __global__ void column_count_kernel(const int32_t *__restrict__ colidx, int64_t nnz, int32_t *__restrict__ cnt) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&cnt[colidx[e]], 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < nnz; base += stride) {
+        const int64_t e = base + lane;
+        const int c = e < nnz ? colidx[e] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        if (c >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[c], __popc(peers));
+    }
 }
 
 __global__ void row_of_entry_kernel(int64_t m, const int64_t *__restrict__ rowptr, int32_t *__restrict__ row_of) {
