@@ -257,7 +257,9 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
     const int bwd_trans = 1 - fwd_trans;
     const int64_t rq = (alg == 6) ? n : m;      // rows of Q
     const int64_t rw = (alg == 6) ? m : n;      // rows of the pass intermediate
-    const int64_t ld = round_up(l, 4);
+    // Rows of the dense blocks start on 128-byte boundaries, so the gather of
+    // one row in the SpMM touches the fewest L1 lines.
+    const int64_t ld = round_up(l, dt == FRPCA_F32 ? 32 : 16);
     const size_t es = dsize(dt);
 
     frpca_status st = reset_status(h);

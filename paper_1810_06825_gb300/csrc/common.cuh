@@ -70,14 +70,18 @@ __device__ inline bool grid_barrier(GridBarrier *bar, unsigned int nblocks, int 
             __threadfence();
             atomicAdd(&bar->gen, 1u);
         } else {
+            // Poll without sleeping first (a barrier normally completes within
+            // a few microseconds and __nanosleep's granularity is coarse), then
+            // back off; give up after limit_cycles.
             const long long t0 = clock64();
+            int polls = 0;
             while (*vgen == g) {
                 if (clock64() - t0 > limit_cycles) {
                     set_status(status, FRPCA_ERR_TIMEOUT);
                     ok = 0;
                     break;
                 }
-                __nanosleep(40);
+                if (++polls > 4096) __nanosleep(200);
             }
         }
         __threadfence();
