@@ -79,8 +79,7 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
     float *V = A + np * np;  // rows v0 .. v0 + vcnt - 1 of V
     ushort2 *blk = reinterpret_cast<ushort2 *>(V + (size_t)vrows * np);
     auto up = [np](int r, int c) { return r <= c ? r * np + c : c * np + r; };
-    __shared__ float cs_c[FRPCA_MAX_L / 2], cs_s[FRPCA_MAX_L / 2];
-    __shared__ int pp[FRPCA_MAX_L / 2], qq[FRPCA_MAX_L / 2];
+    __shared__ float4 rot[FRPCA_MAX_L / 2];  // (c, s, p, q) of each pair, one 16-byte load
     __shared__ int rotations;
     __shared__ double scale;
 
@@ -122,10 +121,7 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
                         atomicAdd(&rotations, 1);
                     }
                 }
-                cs_c[threadIdx.x] = c;
-                cs_s[threadIdx.x] = s;
-                pp[threadIdx.x] = p;
-                qq[threadIdx.x] = q;
+                rot[threadIdx.x] = make_float4(c, s, __int_as_float(p), __int_as_float(q));
             }
             __syncthreads();
             const int total = nblk + vcnt * nb;
@@ -134,9 +130,11 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
                     // A <- J^T A J on the 2x2 block of pairs (ka, kb), upper triangle.
                     const ushort2 ab = blk[idx];
                     const int ka = ab.x, kb = ab.y;
-                    const float ca = cs_c[ka], sa = cs_s[ka], cb = cs_c[kb], sb = cs_s[kb];
+                    const float4 ra = rot[ka], rb = rot[kb];
+                    const float ca = ra.x, sa = ra.y, cb = rb.x, sb = rb.y;
                     if (sa == 0.0f && sb == 0.0f) continue;
-                    const int pa = pp[ka], qa = qq[ka], pb = pp[kb], qb = qq[kb];
+                    const int pa = __float_as_int(ra.z), qa = __float_as_int(ra.w);
+                    const int pb = __float_as_int(rb.z), qb = __float_as_int(rb.w);
                     const int i11 = up(pa, pb), i12 = up(pa, qb), i21 = up(qa, pb), i22 = up(qa, qb);
                     const float a11 = A[i11], a12 = A[i12], a21 = A[i21], a22 = A[i22];
                     const float t11 = ca * a11 - sa * a21, t12 = ca * a12 - sa * a22;
@@ -156,12 +154,14 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
                     // V <- V J, one row of this CTA's slice and one pair.
                     const int v = idx - nblk;
                     const int row = v / nb, k = v - row * nb;
-                    const float c = cs_c[k], s = cs_s[k];
+                    const float4 rk = rot[k];
+                    const float c = rk.x, s = rk.y;
                     if (s == 0.0f) continue;
+                    const int p = __float_as_int(rk.z), q = __float_as_int(rk.w);
                     float *vr = V + row * np;
-                    const float x = vr[pp[k]], y = vr[qq[k]];
-                    vr[pp[k]] = c * x - s * y;
-                    vr[qq[k]] = s * x + c * y;
+                    const float x = vr[p], y = vr[q];
+                    vr[p] = c * x - s * y;
+                    vr[q] = s * x + c * y;
                 }
             }
             __syncthreads();

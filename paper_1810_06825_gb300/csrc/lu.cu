@@ -47,6 +47,12 @@ template <> __device__ inline double sub_mul<double>(double x, double m, double 
 }
 template <> __device__ inline float sub_mul<float>(float x, float m, float u) { return fmaf(-m, u, x); }
 
+// The multiplier M(i,j) / M(p,j): a true division in double (the textbook
+// operation, reproducible bit for bit), the precomputed reciprocal in float.
+template <typename T> __device__ inline T lu_mult(T x, T piv, T rinv);
+template <> __device__ inline double lu_mult<double>(double x, double piv, double) { return x / piv; }
+template <> __device__ inline float lu_mult<float>(float x, float, float rinv) { return x * rinv; }
+
 template <typename T>
 __global__ void __launch_bounds__(kLuThreads, 1)
 lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__ piv_out, Cand *cand,
@@ -65,7 +71,11 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
     const int nrows = (int)(r1 - r0);
     const int ncache = min(nrows, cache_rows);
     T *cache = reinterpret_cast<T *>(smem_raw);                                   // ncache x l
-    unsigned char *pivd = reinterpret_cast<unsigned char *>(cache + (size_t)cache_rows * l);  // nrows flags
+    // After the cached rows: one multiplier per row, then one pivoted flag per
+    // row (sized for the largest block, ceil(R / G) rows, identically in all).
+    const int64_t rows_max = (R + G - 1) / G;
+    T *mults = cache + (size_t)cache_rows * l;
+    unsigned char *pivd = reinterpret_cast<unsigned char *>(mults + round_up(rows_max, 2));
     // Row i of the block: shared memory for the first ncache rows, global after.
     auto rowp = [&](int li) -> T * { return li < ncache ? cache + (size_t)li * l : M + (r0 + li) * ld; };
 
@@ -159,24 +169,47 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
         }
         __syncthreads();
 
-        // (2) eliminate column j from the own unpivoted rows; candidate of j+1.
+        // (2a) the multipliers of column j for the own unpivoted rows.
         const T ujj = urow[j];
+        const T rinv = T(1) / ujj;
+        for (int li = threadIdx.x; li < nrows; li += kLuThreads) {
+            T mu = T(0);
+            if (!pivd[li]) {
+                T *row = rowp(li);
+                mu = lu_mult<T>(row[j], ujj, rinv);
+                row[j] = mu;
+            }
+            mults[li] = mu;
+        }
+        __syncthreads();
+        // (2b) eliminate column j from the trailing columns, four rows per warp
+        // at a time so their updates overlap; candidate of column j+1.
         best = 0.0;
         brow = -1;
-        for (int li = warp; li < nrows; li += kLuWarps) {
-            if (pivd[li]) continue;
-            T *row = rowp(li);
-            const T mult = row[j] / ujj;
+        for (int li0 = 4 * warp; li0 < nrows; li0 += 4 * kLuWarps) {
+            T *rows[4];
+            T mu[4];
+            bool act[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int li = li0 + u;
+                act[u] = li < nrows && !pivd[li];
+                rows[u] = act[u] ? rowp(li) : nullptr;
+                mu[u] = act[u] ? mults[li] : T(0);
+            }
             for (int c = j + 1 + lane; c < l; c += 32) {
-                const T v = sub_mul<T>(row[c], mult, urow[c]);
-                row[c] = v;
-                if (c == j + 1) {
-                    const double a = fabs((double)v);
-                    if (better(a, r0 + li, best, brow)) { best = a; brow = r0 + li; }
+                const T uc = urow[c];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (!act[u]) continue;
+                    const T v = sub_mul<T>(rows[u][c], mu[u], uc);
+                    rows[u][c] = v;
+                    if (c == j + 1) {
+                        const double a = fabs((double)v);
+                        if (better(a, r0 + li0 + u, best, brow)) { best = a; brow = r0 + li0 + u; }
+                    }
                 }
             }
-            __syncwarp();
-            if (lane == 0) row[j] = mult;
         }
         if (j + 1 < l) {
             // The next pivot row may be read by other blocks from global memory:
@@ -240,7 +273,7 @@ cudaError_t launch_lu(int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int
     int64_t G = std::max<int64_t>(1, std::min<int64_t>({(int64_t)num_sms, ceil_div(R, 32), (int64_t)kMaxBlocks}));
     const int64_t rows_per = ceil_div(R, G);
     if (rows_per > kMaxRowsPerBlock) return cudaErrorInvalidValue;
-    const size_t flags = (size_t)round_up(rows_per, 16);
+    const size_t flags = (size_t)round_up(rows_per, 16) + es * (size_t)round_up(rows_per, 2);
     const size_t avail = (size_t)max_optin - attr.sharedSizeBytes - flags - 1024;
     int cache_rows = (int)std::min<int64_t>(rows_per, (int64_t)(avail / (es * l)));
     if (cache_rows < 0) cache_rows = 0;
