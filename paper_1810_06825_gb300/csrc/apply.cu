@@ -20,10 +20,10 @@ constexpr int kApplyThreads = 256;
 __global__ void make_w_kernel(int l, int kout, const double *__restrict__ w, const double *__restrict__ V,
                               int descending, int scale, const double *__restrict__ sign, frpca_dtype dt, void *W,
                               double *__restrict__ S_out, int *status) {
-    if (scale && threadIdx.x == 0 && blockIdx.x == 0) {
+    if (scale && blockIdx.x == 0) {
         // Sec. 3.1: eigSVD needs full column rank; refuse tiny or non-finite eigenvalues.
         const double lmax = w[l - 1];
-        for (int c = 0; c < l; ++c)
+        for (int c = threadIdx.x; c < l; c += blockDim.x)
             if (!isfinite(w[c]) || !(w[c] > (double)l * 2.220446049250313e-16 * lmax))
                 set_status(status, FRPCA_ERR_RANK_DEFICIENT);
     }
@@ -87,9 +87,11 @@ apply_kernel(int64_t R, int l, const T *M, int64_t ldm, const T *__restrict__ W,
 }
 
 // Per block: for every column j, the largest |X(i,j)| over the block's rows,
-// ties to the smaller i; partial (absval, row, value sign) per block.
+// ties to the smaller i; partial (magnitude key, row, value sign) per block.
+// Magnitudes are compared through their IEEE bit patterns (monotone for
+// non-negative values) so the search stays on the integer pipes.
 struct ColBest {
-    double absval;
+    unsigned long long key;
     int64_t row;
     double sgn;
 };
@@ -97,18 +99,25 @@ struct ColBest {
 __device__ inline bool col_better(const ColBest &a, const ColBest &b) {
     if (a.row < 0) return false;
     if (b.row < 0) return true;
-    return a.absval > b.absval || (a.absval == b.absval && a.row < b.row);
+    return a.key > b.key || (a.key == b.key && a.row < b.row);
 }
+
+__device__ inline unsigned long long abs_key(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+__device__ inline unsigned long long abs_key(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+__device__ inline bool negative(float v) { return v < 0.0f; }
+__device__ inline bool negative(double v) { return v < 0.0; }
 
 template <typename T>
 __global__ void col_best_kernel(int64_t R, int k, const T *__restrict__ X, int64_t ld, ColBest *__restrict__ part) {
     const int64_t G = gridDim.x;
     const int64_t r0 = (int64_t)blockIdx.x * R / G, r1 = (int64_t)(blockIdx.x + 1) * R / G;
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
-        ColBest b{-1.0, -1, 1.0};
+        ColBest b{0ull, -1, 1.0};
         for (int64_t i = r0; i < r1; ++i) {
-            const double v = (double)X[i * ld + j];
-            ColBest c{fabs(v), i, v < 0 ? -1.0 : 1.0};
+            const T v = X[i * ld + j];
+            const ColBest c{abs_key(v), i, negative(v) ? -1.0 : 1.0};
             if (col_better(c, b)) b = c;
         }
         part[(int64_t)blockIdx.x * k + j] = b;
@@ -121,12 +130,12 @@ __global__ void col_sign_kernel(int k, int nparts, const ColBest *__restrict__ p
     const int lane = threadIdx.x & 31;
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= k) return;
-    ColBest b{-1.0, -1, 1.0};
+    ColBest b{0ull, -1, 1.0};
     for (int p = lane; p < nparts; p += 32)
         if (col_better(part[(int64_t)p * k + j], b)) b = part[(int64_t)p * k + j];
     for (int o = 16; o > 0; o >>= 1) {
         ColBest c;
-        c.absval = __shfl_down_sync(0xffffffffu, b.absval, o);
+        c.key = __shfl_down_sync(0xffffffffu, b.key, o);
         c.row = __shfl_down_sync(0xffffffffu, b.row, o);
         c.sgn = __shfl_down_sync(0xffffffffu, b.sgn, o);
         if (col_better(c, b)) b = c;

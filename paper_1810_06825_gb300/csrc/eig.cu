@@ -81,11 +81,16 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
     auto up = [np](int r, int c) { return r <= c ? r * np + c : c * np + r; };
     __shared__ float4 rot[FRPCA_MAX_L / 2];  // (c, s, p, q) of each pair, one 16-byte load
     __shared__ int rotations;
+    __shared__ unsigned long long maxdiag;  // bit pattern of max |B_ii| (monotone)
     __shared__ double scale;
 
+    if (threadIdx.x == 0) maxdiag = 0ull;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kJacobiThreads)
+        atomicMax(&maxdiag, (unsigned long long)__double_as_longlong(B[i * ld + i]) & 0x7fffffffffffffffull);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int i = 0; i < n; ++i) m = fmax(m, fabs(B[i * ld + i]));
+        const double m = __longlong_as_double((long long)maxdiag);
         scale = (m > 0.0 && isfinite(m)) ? 1.0 / m : 1.0;
     }
     __syncthreads();
@@ -315,29 +320,41 @@ __global__ void level_split_kernel(int n, int ld, const int *db, const double *_
         if (threadIdx.x == 0) *db_next = 0;
         return;
     }
+    // Ranks by comparing order-preserving integer images of the doubles
+    // (sign-magnitude flipped to two's-complement order), ties by index.
+    __shared__ unsigned long long key_s[FRPCA_MAX_L];
+    __shared__ int first_big;
     for (int i = threadIdx.x; i < b; i += blockDim.x) {
         const double li = lam_b[i];
         if (!isfinite(li)) set_status(status, FRPCA_ERR_NOT_CONVERGED);
+        const unsigned long long u = (unsigned long long)__double_as_longlong(li);
+        key_s[i] = (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+    }
+    if (threadIdx.x == 0) first_big = b;
+    __syncthreads();
+    for (int i = threadIdx.x; i < b; i += blockDim.x) {
+        const unsigned long long ki = key_s[i];
         int r = 0;
         for (int j = 0; j < b; ++j) {
-            const double lj = lam_b[j];
-            r += (lj < li) || (lj == li && j < i);
+            const unsigned long long kj = key_s[j];
+            r += (kj < ki) || (kj == ki && j < i);
         }
         rank_s[i] = r;
-        sorted[r] = li;
+        sorted[r] = lam_b[i];
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < n * b; idx += blockDim.x) {
         const int row = idx / b, j = idx - row * b;
         X[row * ld + rank_s[j]] = Xnew[row * ld + j];
     }
-    for (int i = threadIdx.x; i < b; i += blockDim.x) lam_all[i] = sorted[i];
-    if (threadIdx.x == 0) {
-        const double top = fmax(fabs(sorted[b - 1]), fabs(sorted[0]));
-        int cnt = 0;
-        while (cnt < b && fabs(sorted[cnt]) < kTau * top) ++cnt;
-        *db_next = (cnt >= 2) ? cnt : 0;
+    // The next block: the ascending prefix with |lambda| < kTau * max|lambda|.
+    const double top = fmax(fabs(sorted[b - 1]), fabs(sorted[0]));
+    for (int i = threadIdx.x; i < b; i += blockDim.x) {
+        lam_all[i] = sorted[i];
+        if (!(fabs(sorted[i]) < kTau * top)) atomicMin(&first_big, i);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) *db_next = (first_big >= 2) ? first_big : 0;
 }
 
 __global__ void set_identity_kernel(int n, int ld, double *X, int *dims, int levels) {

@@ -29,16 +29,30 @@ constexpr int kMaxBlocks = 1024;
 constexpr int kMaxRowsPerBlock = 8192;
 
 struct Cand {
-    double absval;  // |M(i,j)| (exact in double for either input type)
+    unsigned long long key;  // bit pattern of |M(i,j)| (order-preserving; 0: none)
     int64_t row;    // -1: none
 };
 
-__device__ inline bool better(double a, int64_t ra, double b, int64_t rb) {
+__device__ inline bool better(unsigned long long a, int64_t ra, unsigned long long b, int64_t rb) {
     // Larger magnitude wins; equal magnitudes go to the smaller row.  A
     // candidate must be > 0 (zeros and NaNs never pivot).
     if (ra < 0) return false;
-    if (rb < 0) return a > 0.0;
+    if (rb < 0) return a > 0ull;
     return a > b || (a == b && ra < rb);
+}
+
+// |v| as an integer key that orders like the magnitude (IEEE bit patterns of
+// non-negative values are monotone); NaN maps to 0 so it never pivots, as in
+// a floating-point comparison.  Integer compares keep the pivot search off the
+// double-precision pipe.
+template <typename T> __device__ inline unsigned long long mag_key(T v);
+template <> __device__ inline unsigned long long mag_key<float>(float v) {
+    const unsigned int b = __float_as_uint(v) & 0x7fffffffu;
+    return b > 0x7f800000u ? 0ull : (unsigned long long)b;
+}
+template <> __device__ inline unsigned long long mag_key<double>(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    return b > 0x7ff0000000000000ull ? 0ull : b;
 }
 
 template <typename T> __device__ inline T sub_mul(T x, T m, T u);
@@ -60,7 +74,7 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T urow[FRPCA_MAX_L];
     __shared__ int64_t pivots[FRPCA_MAX_L];
-    __shared__ double wbest[kLuWarps];
+    __shared__ unsigned long long wbest[kLuWarps];
     __shared__ int64_t wrow[kLuWarps];
     __shared__ int64_t s_p;
     __shared__ int s_stop;
@@ -87,26 +101,26 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
     __syncthreads();
 
     // Candidate for column 0.
-    double best = 0.0;
+    unsigned long long best = 0;
     int64_t brow = -1;
     for (int li = threadIdx.x; li < nrows; li += kLuThreads) {
-        const double a = fabs((double)rowp(li)[0]);
+        const unsigned long long a = mag_key<T>(rowp(li)[0]);
         if (better(a, r0 + li, best, brow)) { best = a; brow = r0 + li; }
     }
     auto block_reduce_write = [&](int slot) {
         for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_down_sync(0xffffffffu, best, o);
+            const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
             const int64_t orr = __shfl_down_sync(0xffffffffu, brow, o);
             if (better(ob, orr, best, brow)) { best = ob; brow = orr; }
         }
         if (lane == 0) { wbest[warp] = best; wrow[warp] = brow; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double b = 0.0;
+            unsigned long long b = 0;
             int64_t r = -1;
             for (int w = 0; w < kLuWarps; ++w)
                 if (better(wbest[w], wrow[w], b, r)) { b = wbest[w]; r = wrow[w]; }
-            cand[slot * G + blockIdx.x].absval = b;
+            cand[slot * G + blockIdx.x].key = b;
             cand[slot * G + blockIdx.x].row = r;
         }
     };
@@ -117,16 +131,16 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
         // (1) the pivot of column j, identical in every block: thread k reads
         // block k's candidate, then a block-wide (max, smallest row) reduction.
         {
-            double b = 0.0;
+            unsigned long long b = 0;
             int64_t r = -1;
             const Cand *cs = cand + (j & 1) * G;
             for (unsigned k = threadIdx.x; k < G; k += kLuThreads) {
-                const double cb = __ldcg(&cs[k].absval);
+                const unsigned long long cb = __ldcg(&cs[k].key);
                 const int64_t cr = __ldcg(&cs[k].row);
                 if (better(cb, cr, b, r)) { b = cb; r = cr; }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_down_sync(0xffffffffu, b, o);
+                const unsigned long long ob = __shfl_down_sync(0xffffffffu, b, o);
                 const int64_t orr = __shfl_down_sync(0xffffffffu, r, o);
                 if (better(ob, orr, b, r)) { b = ob; r = orr; }
             }
@@ -134,7 +148,7 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
             __syncthreads();
         }
         if (threadIdx.x == 0) {
-            double b = 0.0;
+            unsigned long long b = 0;
             int64_t r = -1;
             for (int w = 0; w < kLuWarps; ++w)
                 if (better(wbest[w], wrow[w], b, r)) { b = wbest[w]; r = wrow[w]; }
@@ -184,7 +198,7 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
         __syncthreads();
         // (2b) eliminate column j from the trailing columns, four rows per warp
         // at a time so their updates overlap; candidate of column j+1.
-        best = 0.0;
+        best = 0;
         brow = -1;
         for (int li0 = 4 * warp; li0 < nrows; li0 += 4 * kLuWarps) {
             T *rows[4];
@@ -205,7 +219,7 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
                     const T v = sub_mul<T>(rows[u][c], mu[u], uc);
                     rows[u][c] = v;
                     if (c == j + 1) {
-                        const double a = fabs((double)v);
+                        const unsigned long long a = mag_key<T>(v);
                         if (better(a, r0 + li0 + u, best, brow)) { best = a; brow = r0 + li0 + u; }
                     }
                 }
