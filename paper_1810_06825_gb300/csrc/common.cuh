@@ -55,34 +55,31 @@ struct GridBarrier {
     unsigned int gen;
 };
 
+// One atomic per block: block 0 adds 2^31 - (nblocks - 1) and every other
+// block adds 1, so the counter's top bit flips exactly when the last block
+// arrives and no reset is needed between barriers; each block polls until the
+// bit differs from the one it saw on arrival.
 __device__ inline bool grid_barrier(GridBarrier *bar, unsigned int nblocks, int *status,
                                     long long limit_cycles) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = &bar->gen;
-        const unsigned int g = *vgen;
+        const unsigned int add = (blockIdx.x == 0) ? (0x80000000u - (nblocks - 1u)) : 1u;
         __threadfence();
-        const unsigned int arrived = atomicAdd(&bar->count, 1u);
+        const unsigned int old = atomicAdd(&bar->count, add);
+        volatile unsigned int *vc = &bar->count;
         ok = 1;
-        if (arrived == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            // Poll without sleeping first (a barrier normally completes within
-            // a few microseconds and __nanosleep's granularity is coarse), then
-            // back off; give up after limit_cycles.
-            const long long t0 = clock64();
-            int polls = 0;
-            while (*vgen == g) {
-                if (clock64() - t0 > limit_cycles) {
-                    set_status(status, FRPCA_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                if (++polls > 4096) __nanosleep(200);
+        const long long t0 = clock64();
+        int polls = 0;
+        while (((*vc ^ old) & 0x80000000u) == 0u) {
+            if (clock64() - t0 > limit_cycles) {
+                set_status(status, FRPCA_ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
+            // Poll without sleeping first (a barrier normally completes within
+            // microseconds and __nanosleep is coarse), then back off.
+            if (++polls > 4096) __nanosleep(200);
         }
         __threadfence();
     }

@@ -75,10 +75,11 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
     const int vrows = (np + gridDim.x - 1) / gridDim.x;
     const int v0 = blockIdx.x * vrows;
     const int vcnt = max(0, min(vrows, np - v0));
+    const int lda = np + 1;  // odd row strides: fewer shared-memory bank conflicts
     float *A = reinterpret_cast<float *>(smem_raw);
-    float *V = A + np * np;  // rows v0 .. v0 + vcnt - 1 of V
-    ushort2 *blk = reinterpret_cast<ushort2 *>(V + (size_t)vrows * np);
-    auto up = [np](int r, int c) { return r <= c ? r * np + c : c * np + r; };
+    float *V = A + np * lda;  // rows v0 .. v0 + vcnt - 1 of V, stride lda
+    ushort2 *blk = reinterpret_cast<ushort2 *>(V + (size_t)vrows * lda);
+    auto up = [lda](int r, int c) { return r <= c ? r * lda + c : c * lda + r; };
     __shared__ float4 rot[FRPCA_MAX_L / 2];  // (c, s, p, q) of each pair, one 16-byte load
     __shared__ int rotations;
     __shared__ unsigned long long maxdiag;  // bit pattern of max |B_ii| (monotone)
@@ -96,11 +97,11 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
     __syncthreads();
     for (int idx = threadIdx.x; idx < np * np; idx += kJacobiThreads) {
         const int i = idx / np, j = idx - i * np;
-        A[idx] = (i < n && j < n) ? (float)(B[i * ld + j] * scale) : 0.0f;
+        A[i * lda + j] = (i < n && j < n) ? (float)(B[i * ld + j] * scale) : 0.0f;
     }
     for (int idx = threadIdx.x; idx < vcnt * np; idx += kJacobiThreads) {
         const int i = v0 + idx / np, j = idx % np;
-        V[idx] = (i == j) ? 1.0f : 0.0f;
+        V[(idx / np) * lda + j] = (i == j) ? 1.0f : 0.0f;
     }
     for (int idx = threadIdx.x; idx < nb * nb; idx += kJacobiThreads) {
         const int a = idx / nb, b = idx - a * nb;
@@ -117,7 +118,7 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
                 pair_of(r, threadIdx.x, np, p, q);
                 float c = 1.0f, s = 0.0f;
                 if (q < n) {
-                    const float apq = A[p * np + q], app = A[p * np + p], aqq = A[q * np + q];
+                    const float apq = A[p * lda + q], app = A[p * lda + p], aqq = A[q * lda + q];
                     if (apq != 0.0f && fabsf(apq) > 0x1p-23f * sqrtf(fabsf(app) * fabsf(aqq))) {
                         const float tau = (aqq - app) / (2.0f * apq);
                         const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
@@ -163,7 +164,7 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
                     const float c = rk.x, s = rk.y;
                     if (s == 0.0f) continue;
                     const int p = __float_as_int(rk.z), q = __float_as_int(rk.w);
-                    float *vr = V + row * np;
+                    float *vr = V + row * lda;
                     const float x = vr[p], y = vr[q];
                     vr[p] = c * x - s * y;
                     vr[q] = s * x + c * y;
@@ -176,7 +177,7 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
     }
     for (int idx = threadIdx.x; idx < vcnt * n; idx += kJacobiThreads) {
         const int r = idx / n, j = idx - r * n;
-        if (v0 + r < n) X[(v0 + r) * ld + j] = (double)V[r * np + j];
+        if (v0 + r < n) X[(v0 + r) * ld + j] = (double)V[r * lda + j];
     }
 }
 
@@ -401,7 +402,7 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
     const int np = n + (n & 1);
     const int nb = np / 2;
     const int vrows = (np + kJacobiCtas - 1) / kJacobiCtas;
-    const size_t smem = sizeof(float) * ((size_t)np * np + (size_t)vrows * np) +
+    const size_t smem = sizeof(float) * ((size_t)np * (np + 1) + (size_t)vrows * (np + 1)) +
                         sizeof(ushort2) * (size_t)nb * (nb + 1) / 2;
     if ((e = cudaFuncSetAttribute(jacobi_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)

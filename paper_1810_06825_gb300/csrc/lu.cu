@@ -76,7 +76,8 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
     __shared__ int64_t pivots[FRPCA_MAX_L];
     __shared__ unsigned long long wbest[kLuWarps];
     __shared__ int64_t wrow[kLuWarps];
-    __shared__ int64_t s_p;
+    __shared__ int64_t s_p, s_row;
+    __shared__ unsigned long long s_key;
     __shared__ int s_stop;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -84,19 +85,20 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
     const int64_t r0 = (int64_t)blockIdx.x * R / G, r1 = (int64_t)(blockIdx.x + 1) * R / G;
     const int nrows = (int)(r1 - r0);
     const int ncache = min(nrows, cache_rows);
-    T *cache = reinterpret_cast<T *>(smem_raw);                                   // ncache x l
+    const int cst = l + 1;  // odd row stride of the cached rows: no bank conflicts down a column
+    T *cache = reinterpret_cast<T *>(smem_raw);                                   // ncache x cst
     // After the cached rows: one multiplier per row, then one pivoted flag per
     // row (sized for the largest block, ceil(R / G) rows, identically in all).
     const int64_t rows_max = (R + G - 1) / G;
-    T *mults = cache + (size_t)cache_rows * l;
+    T *mults = cache + (size_t)cache_rows * cst;
     unsigned char *pivd = reinterpret_cast<unsigned char *>(mults + round_up(rows_max, 2));
     // Row i of the block: shared memory for the first ncache rows, global after.
-    auto rowp = [&](int li) -> T * { return li < ncache ? cache + (size_t)li * l : M + (r0 + li) * ld; };
+    auto rowp = [&](int li) -> T * { return li < ncache ? cache + (size_t)li * cst : M + (r0 + li) * ld; };
 
     for (int li = threadIdx.x; li < nrows; li += kLuThreads) pivd[li] = 0;
     for (int idx = threadIdx.x; idx < ncache * l; idx += kLuThreads) {
         const int li = idx / l, c = idx - li * l;
-        cache[idx] = M[(r0 + li) * ld + c];
+        cache[li * cst + c] = M[(r0 + li) * ld + c];
     }
     __syncthreads();
 
@@ -107,21 +109,33 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
         const unsigned long long a = mag_key<T>(rowp(li)[0]);
         if (better(a, r0 + li, best, brow)) { best = a; brow = r0 + li; }
     }
-    auto block_reduce_write = [&](int slot) {
+    // Block-wide (largest key, smallest row) reduction: warp shuffles, then
+    // warp 0 over the 32 warp results; the winner lands in s_key / s_row.
+    auto block_argmax = [&](unsigned long long b, int64_t r) {
         for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
-            const int64_t orr = __shfl_down_sync(0xffffffffu, brow, o);
-            if (better(ob, orr, best, brow)) { best = ob; brow = orr; }
+            const unsigned long long ob = __shfl_down_sync(0xffffffffu, b, o);
+            const int64_t orr = __shfl_down_sync(0xffffffffu, r, o);
+            if (better(ob, orr, b, r)) { b = ob; r = orr; }
         }
-        if (lane == 0) { wbest[warp] = best; wrow[warp] = brow; }
+        if (lane == 0) { wbest[warp] = b; wrow[warp] = r; }
         __syncthreads();
+        if (warp == 0) {
+            b = wbest[lane];
+            r = wrow[lane];
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_down_sync(0xffffffffu, b, o);
+                const int64_t orr = __shfl_down_sync(0xffffffffu, r, o);
+                if (better(ob, orr, b, r)) { b = ob; r = orr; }
+            }
+            if (lane == 0) { s_key = b; s_row = r; }
+        }
+        __syncthreads();
+    };
+    auto block_reduce_write = [&](int slot) {
+        block_argmax(best, brow);
         if (threadIdx.x == 0) {
-            unsigned long long b = 0;
-            int64_t r = -1;
-            for (int w = 0; w < kLuWarps; ++w)
-                if (better(wbest[w], wrow[w], b, r)) { b = wbest[w]; r = wrow[w]; }
-            cand[slot * G + blockIdx.x].key = b;
-            cand[slot * G + blockIdx.x].row = r;
+            cand[slot * G + blockIdx.x].key = s_key;
+            cand[slot * G + blockIdx.x].row = s_row;
         }
     };
     block_reduce_write(0);
@@ -139,19 +153,10 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
                 const int64_t cr = __ldcg(&cs[k].row);
                 if (better(cb, cr, b, r)) { b = cb; r = cr; }
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long ob = __shfl_down_sync(0xffffffffu, b, o);
-                const int64_t orr = __shfl_down_sync(0xffffffffu, r, o);
-                if (better(ob, orr, b, r)) { b = ob; r = orr; }
-            }
-            if (lane == 0) { wbest[warp] = b; wrow[warp] = r; }
-            __syncthreads();
+            block_argmax(b, r);
         }
         if (threadIdx.x == 0) {
-            unsigned long long b = 0;
-            int64_t r = -1;
-            for (int w = 0; w < kLuWarps; ++w)
-                if (better(wbest[w], wrow[w], b, r)) { b = wbest[w]; r = wrow[w]; }
+            const int64_t r = s_row;
             s_p = r;
             s_stop = (r < 0);
             pivots[j] = r;
@@ -183,47 +188,60 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
         }
         __syncthreads();
 
-        // (2a) the multipliers of column j for the own unpivoted rows.
+        // (2a) one thread per own unpivoted row: its multiplier for column j,
+        // its updated entry in column j+1 and the block's candidate for the
+        // next pivot (cached rows through shared memory, the rest global).
         const T ujj = urow[j];
         const T rinv = T(1) / ujj;
+        const T u1 = (j + 1 < l) ? urow[j + 1] : T(0);
+        best = 0;
+        brow = -1;
         for (int li = threadIdx.x; li < nrows; li += kLuThreads) {
             T mu = T(0);
             if (!pivd[li]) {
-                T *row = rowp(li);
+                T *row = li < ncache ? cache + (size_t)li * cst : M + (r0 + li) * ld;
                 mu = lu_mult<T>(row[j], ujj, rinv);
                 row[j] = mu;
+                if (j + 1 < l) {
+                    const T v = sub_mul<T>(row[j + 1], mu, u1);
+                    row[j + 1] = v;
+                    const unsigned long long a = mag_key<T>(v);
+                    if (better(a, r0 + li, best, brow)) { best = a; brow = r0 + li; }
+                }
             }
             mults[li] = mu;
         }
         __syncthreads();
-        // (2b) eliminate column j from the trailing columns, four rows per warp
-        // at a time so their updates overlap; candidate of column j+1.
-        best = 0;
-        brow = -1;
-        for (int li0 = 4 * warp; li0 < nrows; li0 += 4 * kLuWarps) {
-            T *rows[4];
+        // (2b) the remaining trailing columns j+2 .. l-1, four rows per warp at
+        // a time so their updates overlap.
+        auto update4 = [&](T *rows0, int64_t stride, int li0) {
             T mu[4];
             bool act[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int li = li0 + u;
                 act[u] = li < nrows && !pivd[li];
-                rows[u] = act[u] ? rowp(li) : nullptr;
                 mu[u] = act[u] ? mults[li] : T(0);
             }
-            for (int c = j + 1 + lane; c < l; c += 32) {
+            for (int c = j + 2 + lane; c < l; c += 32) {
                 const T uc = urow[c];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (!act[u]) continue;
-                    const T v = sub_mul<T>(rows[u][c], mu[u], uc);
-                    rows[u][c] = v;
-                    if (c == j + 1) {
-                        const unsigned long long a = mag_key<T>(v);
-                        if (better(a, r0 + li0 + u, best, brow)) { best = a; brow = r0 + li0 + u; }
-                    }
-                }
+                for (int u = 0; u < 4; ++u)
+                    if (act[u]) rows0[u * stride + c] = sub_mul<T>(rows0[u * stride + c], mu[u], uc);
             }
+        };
+        for (int li0 = 4 * warp; li0 < nrows; li0 += 4 * kLuWarps) {
+            if (li0 + 4 <= ncache)
+                update4(cache + (size_t)li0 * cst, cst, li0);      // shared memory
+            else if (li0 >= ncache)
+                update4(M + (r0 + li0) * ld, ld, li0);            // global memory
+            else
+                for (int u = 0; u < 4 && li0 + u < nrows; ++u) {  // straddles the boundary
+                    const int li = li0 + u;
+                    if (pivd[li]) continue;
+                    T *row = li < ncache ? cache + (size_t)li * cst : M + (r0 + li) * ld;
+                    for (int c = j + 2 + lane; c < l; c += 32) row[c] = sub_mul<T>(row[c], mults[li], urow[c]);
+                }
         }
         if (j + 1 < l) {
             // The next pivot row may be read by other blocks from global memory:
@@ -231,9 +249,9 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
             __syncthreads();
             block_reduce_write((j + 1) & 1);
             __syncthreads();
-            const int64_t mine = cand[((j + 1) & 1) * G + blockIdx.x].row;
+            const int64_t mine = s_row;
             if (mine >= r0 && mine < r0 + ncache) {
-                const T *row = cache + (size_t)(mine - r0) * l;
+                const T *row = cache + (size_t)(mine - r0) * cst;
                 for (int c = j + 1 + threadIdx.x; c < l; c += kLuThreads) M[mine * ld + c] = row[c];
             }
             ok = grid_barrier(bar, G, status, kBarrierLimitCycles);
@@ -254,7 +272,7 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
     // Write the cached rows back (also after a failure, so M stays consistent).
     for (int idx = threadIdx.x; idx < ncache * l; idx += kLuThreads) {
         const int li = idx / l, c = idx - li * l;
-        M[(r0 + li) * ld + c] = cache[idx];
+        M[(r0 + li) * ld + c] = cache[li * cst + c];
     }
 }
 
@@ -289,9 +307,9 @@ cudaError_t launch_lu(int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int
     if (rows_per > kMaxRowsPerBlock) return cudaErrorInvalidValue;
     const size_t flags = (size_t)round_up(rows_per, 16) + es * (size_t)round_up(rows_per, 2);
     const size_t avail = (size_t)max_optin - attr.sharedSizeBytes - flags - 1024;
-    int cache_rows = (int)std::min<int64_t>(rows_per, (int64_t)(avail / (es * l)));
+    int cache_rows = (int)std::min<int64_t>(rows_per, (int64_t)(avail / (es * (l + 1))));
     if (cache_rows < 0) cache_rows = 0;
-    const size_t smem = es * (size_t)cache_rows * l + flags;
+    const size_t smem = es * (size_t)cache_rows * (l + 1) + flags;
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     int per_sm = 0;
