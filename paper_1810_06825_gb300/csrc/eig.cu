@@ -36,7 +36,13 @@ constexpr int kJacobiCtas = 8;  // CTAs sharing the rows of V (each holds all of
 constexpr int kJacobiMaxSweeps = 24;
 constexpr int kRefineSteps = 5;
 constexpr int kLevels = 3;
-constexpr double kTau = 1.0e-3;  // bottom block: lambda < kTau * lambda_max of the block
+constexpr double kTau = 1.0e-5;  // bottom block: lambda < kTau * lambda_max of the block
+
+// A refinement step is skipped once the previous one moved X by less than
+// this (max |E_ij|): X is then converged to double precision.
+__device__ inline bool converged(const unsigned long long *emax) {
+    return emax && *emax <= (unsigned long long)__double_as_longlong(1.0e-15);
+}
 
 __device__ inline void pair_of(int r, int k, int np, int &p, int &q) {
     int a, b;
@@ -187,11 +193,16 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
 template <bool TA>
 __global__ void gemm64_kernel(const int *dM, const int *dN, const int *dK, int Ms, int Ns, int Ks, int ld,
                               const double *__restrict__ A, const double *__restrict__ Bm,
-                              const double *__restrict__ Cadd, double *__restrict__ C) {
+                              const double *__restrict__ Cadd, double *__restrict__ C,
+                              const unsigned long long *skip) {
     const int M = dim_of(dM, Ms), N = dim_of(dN, Ns), K = dim_of(dK, Ks);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
     if (blockIdx.y * 16 >= M || blockIdx.x * 16 >= N) return;
+    if (converged(skip)) {  // refinement converged: C = Cadd (a copy) or nothing
+        if (Cadd && i < M && j < N) C[i * ld + j] = Cadd[i * ld + j];
+        return;
+    }
     __shared__ double As[16][17], Bs[16][17];
     double acc = 0.0;
     for (int k0 = 0; k0 < K; k0 += 16) {
@@ -233,10 +244,11 @@ constexpr int kOaRows = 4;  // rows of E per CTA
 
 // Partial sums of |S - diag(lambda)|_F^2, |C|_F^2 and |R|_F^2 over kOaRows rows.
 __global__ void oa_norms_kernel(const int *dn, int ld, const double *__restrict__ Cm, const double *__restrict__ Gm,
-                                const double *__restrict__ S, double *__restrict__ part) {
+                                const double *__restrict__ S, double *__restrict__ part,
+                                const unsigned long long *skip) {
     const int n = *dn;
     const int r0 = blockIdx.x * kOaRows;
-    if (n < 1 || r0 >= n) return;
+    if (n < 1 || r0 >= n || converged(skip)) return;
     __shared__ double red[32];
     double sS = 0.0, sB = 0.0, sR = 0.0;
     const int r1 = min(n, r0 + kOaRows);
@@ -274,10 +286,17 @@ __device__ inline double recip(double g) {
 // float cannot separate the latter at this level, a first-order rotation
 // between them would be unreliable, and the next deflation level resolves them.
 __global__ void oa_e_kernel(const int *dn, int ld, const double *__restrict__ Gm, const double *__restrict__ S,
-                            const double *__restrict__ part, double *__restrict__ E, double *__restrict__ lam) {
+                            const double *__restrict__ part, double *__restrict__ E, double *__restrict__ lam,
+                            const unsigned long long *skip, unsigned long long *emax) {
     const int n = *dn;
     const int r0 = blockIdx.x * kOaRows;
     if (n < 1 || r0 >= n) return;
+    if (converged(skip)) {  // keep the converged mark for the following steps
+        if (blockIdx.x == 0 && threadIdx.x == 0) *emax = 0ull;
+        return;
+    }
+    __shared__ unsigned long long emax_s;
+    if (threadIdx.x == 0) emax_s = 0ull;
     __shared__ double lam_s[FRPCA_MAX_L];
     __shared__ double s_delta, s_low;
     for (int i = threadIdx.x; i < n; i += blockDim.x) lam_s[i] = oa_lambda(S, Gm, ld, i);
@@ -302,8 +321,12 @@ __global__ void oa_e_kernel(const int *dn, int ld, const double *__restrict__ Gm
         const double rij = (i == j ? 1.0 : 0.0) - Gm[i * ld + j];
         const double gap = lam_s[j] - lam_s[i];
         const bool both_low = fabs(lam_s[i]) < low && fabs(lam_s[j]) < low;
-        E[i * ld + j] = (fabs(gap) > delta && !both_low) ? fma(lam_s[j], rij, S[i * ld + j]) * recip(gap) : 0.5 * rij;
+        const double e = (fabs(gap) > delta && !both_low) ? fma(lam_s[j], rij, S[i * ld + j]) * recip(gap) : 0.5 * rij;
+        E[i * ld + j] = e;
+        atomicMax(&emax_s, (unsigned long long)__double_as_longlong(e) & 0x7fffffffffffffffull);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(emax, emax_s);
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = lam_s[i];
 }
@@ -358,7 +381,9 @@ __global__ void level_split_kernel(int n, int ld, const int *db, const double *_
     if (threadIdx.x == 0) *db_next = (first_big >= 2) ? first_big : 0;
 }
 
-__global__ void set_identity_kernel(int n, int ld, double *X, int *dims, int levels) {
+__global__ void set_identity_kernel(int n, int ld, double *X, int *dims, int levels, unsigned long long *emax,
+                                    int nemax) {
+    for (int i = threadIdx.x; i < nemax; i += blockDim.x) emax[i] = ~0ull;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
         const int i = idx / n, j = idx - i * n;
         X[i * ld + j] = (i == j) ? 1.0 : 0.0;
@@ -382,7 +407,7 @@ __global__ void copy_out_kernel(int n, int ld, const double *__restrict__ lam_al
 
 size_t eig_workspace_bytes(int n) {
     const size_t ld = FRPCA_MAX_L;
-    return sizeof(double) * (10 * ld * ld + 5 * ld) + 64 * sizeof(int) + 256;
+    return sizeof(double) * (10 * ld * ld + 5 * ld) + 64 * sizeof(int) + 8 * kLevels * kRefineSteps + 256;
 }
 
 cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, int *d_status, cudaStream_t s) {
@@ -394,6 +419,7 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
            *S = T + nn, *E = S + nn, *Bl = E + nn, *lam_b = Bl + nn, *lam_all = lam_b + ld;
     double *Pn = lam_all + ld;  // norm partials, 3 per row group
     int *dims = (int *)(Pn + 3 * ld);
+    unsigned long long *emax = (unsigned long long *)(dims + 64);  // max |E| per level and step
     cudaError_t e;
     // B copied to leading dimension ld.
     e = cudaMemcpy2DAsync(Bl, sizeof(double) * ld, B, sizeof(double) * n, sizeof(double) * n, n,
@@ -407,28 +433,30 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
     if ((e = cudaFuncSetAttribute(jacobi_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
-    set_identity_kernel<<<1, 256, 0, s>>>(n, ld, X, dims, kLevels);
+    set_identity_kernel<<<1, 256, 0, s>>>(n, ld, X, dims, kLevels, emax, kLevels * kRefineSteps);
     count_launch();
     const dim3 g2((n + 15) / 16, (n + 15) / 16);
     for (int lv = 0; lv < kLevels; ++lv) {
         const int *db = dims + lv;  // active block size (0: nothing left)
         // C = Xa^T B Xa on the active columns (the first b columns of X).
-        gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, nullptr, n, 0, n, ld, Bl, X, nullptr, T);
-        gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, nullptr, 0, 0, n, ld, X, T, nullptr, Cm);
+        gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, nullptr, n, 0, n, ld, Bl, X, nullptr, T, nullptr);
+        gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, nullptr, 0, 0, n, ld, X, T, nullptr, Cm, nullptr);
         jacobi_f32_kernel<<<kJacobiCtas, kJacobiThreads, smem, s>>>(db, 0, Cm, ld, Z);
         count_launch(3);
         for (int it = 0; it < kRefineSteps; ++it) {
-            gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Z, Z, nullptr, G);   // Z^T Z
-            gemm64_kernel<false><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Cm, Z, nullptr, T); // C Z
-            gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Z, T, nullptr, S);   // Z^T C Z
-            oa_norms_kernel<<<(n + kOaRows - 1) / kOaRows, 256, 0, s>>>(db, ld, Cm, G, S, Pn);
-            oa_e_kernel<<<(n + kOaRows - 1) / kOaRows, 256, 0, s>>>(db, ld, G, S, Pn, E, lam_b);
-            gemm64_kernel<false><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Z, E, Z, Z2);       // Z + Z E
+            const unsigned long long *skip = it ? emax + lv * kRefineSteps + it - 1 : nullptr;
+            unsigned long long *em = emax + lv * kRefineSteps + it;
+            gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Z, Z, nullptr, G, skip);   // Z^T Z
+            gemm64_kernel<false><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Cm, Z, nullptr, T, skip); // C Z
+            gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Z, T, nullptr, S, skip);   // Z^T C Z
+            oa_norms_kernel<<<(n + kOaRows - 1) / kOaRows, 256, 0, s>>>(db, ld, Cm, G, S, Pn, skip);
+            oa_e_kernel<<<(n + kOaRows - 1) / kOaRows, 256, 0, s>>>(db, ld, G, S, Pn, E, lam_b, skip, em);
+            gemm64_kernel<false><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Z, E, Z, Z2, skip);       // Z + Z E
             count_launch(6);
             std::swap(Z, Z2);
         }
         // Xa <- Xa Z, then sort the active block and choose the next one.
-        gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, db, n, 0, 0, ld, X, Z, nullptr, Xn);
+        gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, db, n, 0, 0, ld, X, Z, nullptr, Xn, nullptr);
         level_split_kernel<<<1, 256, 0, s>>>(n, ld, db, lam_b, Xn, X, lam_all, dims + lv + 1, d_status);
         count_launch(2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
