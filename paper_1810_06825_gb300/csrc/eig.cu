@@ -36,7 +36,7 @@ constexpr int kJacobiCtas = 8;  // CTAs sharing the rows of V (each holds all of
 constexpr int kJacobiMaxSweeps = 24;
 constexpr int kRefineSteps = 5;
 constexpr int kLevels = 3;
-constexpr double kTau = 1.0e-5;  // bottom block: lambda < kTau * lambda_max of the block
+constexpr double kTau = 1.0e-3;  // bottom block: lambda < kTau * lambda_max of the block
 
 // A refinement step is skipped once the previous one moved X by less than
 // this (max |E_ij|): X is then converged to double precision.
