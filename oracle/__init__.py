@@ -82,9 +82,10 @@ def _load():
     lib.or_eigsvd.argtypes = [I64, I64, P, I64, P, I64, P, P]
     lib.or_frpca.argtypes = [ctypes.c_int, I64, I64, P, P, P, I64, I64, I64, U64, P, P, P]
     lib.or_frpca_ex.argtypes = [ctypes.c_int, I64, I64, P, P, P, I64, I64, I64, U64, ctypes.c_int, P, P, P]
+    lib.or_svd_adjoint_sddmm.argtypes = [I64, I64, P, P, I64, P, P, P, P, P, P, P]
     lib.or_num_threads.argtypes = []
     for name in ("or_gaussian", "or_csr_transpose", "or_spmm", "or_spmm_t", "or_lu_ptl", "or_eig_sym",
-                 "or_gram", "or_eigsvd", "or_frpca", "or_frpca_ex", "or_num_threads"):
+                 "or_gram", "or_eigsvd", "or_frpca", "or_frpca_ex", "or_svd_adjoint_sddmm", "or_num_threads"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -213,3 +214,22 @@ def frpca(m: int, n: int, indptr, indices, data, k: int, l: int, q: int, seed: i
     _check(_load().or_frpca_ex(alg, m, n, _p(indptr), _p(indices), _p(data), k, l, q, seed, int(stabilize),
                                _p(U), _p(S), _p(V)), "frpca")
     return U, S, V
+
+
+def svd_adjoint_sddmm(m: int, n: int, indptr, indices, U, S, V, dU=None, dS=None, dV=None):
+    """Gradient with respect to the CSR values of a loss of the rank-k truncated
+    SVD (U, S, V) with cotangents (dU, dS, dV), each optional: the thin-SVD
+    adjoint (Townsend 2016) sampled at the nonzeros.  Not part of the paper."""
+    indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(indices, dtype=np.int32)
+    f64 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)  # noqa: E731
+    U, S, V, dU, dS, dV = map(f64, (U, S, V, dU, dS, dV))
+    k = S.shape[0]
+    assert U.shape == (m, k) and V.shape == (n, k)
+    assert dU is None or dU.shape == (m, k)
+    assert dV is None or dV.shape == (n, k)
+    out = np.empty(int(indptr[-1]), dtype=np.float64)
+    opt = lambda a: None if a is None else _p(a)  # noqa: E731
+    _check(_load().or_svd_adjoint_sddmm(m, n, _p(indptr), _p(indices), k, _p(U), _p(S), _p(V), opt(dU),
+                                        opt(dS), opt(dV), _p(out)), "svd_adjoint_sddmm")
+    return out

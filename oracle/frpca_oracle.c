@@ -462,3 +462,91 @@ int or_frpca_ex(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int3
     free(Q); free(W); free(Sh); free(Vh);
     return st;
 }
+
+/*
+ * Backward of the rank-k truncated SVD A ~ U diag(S) V^T, sampled at the
+ * nonzeros of A (the gradient with respect to the CSR values).  Not part of
+ * the paper: this is the real thin-SVD adjoint (Townsend 2016, "Differentiating
+ * the singular value decomposition"; Ionescu et al. 2015) written for the
+ * returned triplets.  With Ub = dU, Vb = dV, Sb = dS (each may be NULL = 0),
+ *   J = U^T Ub,  K = V^T Vb,  F_ab = 1 / (s_b^2 - s_a^2) (a != b), F_aa = 0,
+ *   C = (F o (J - J^T)) diag(s) + diag(Sb) + diag(s) (F o (K - K^T)),
+ *   Abar = U C V^T + (Ub - U J) diag(1/s) V^T + U diag(1/s) (Vb - V K)^T,
+ * and dvalues[e] = Abar[i_e, j_e].  A pair with s_a == s_b exactly gets
+ * F_ab = 0.  U is m x k, V is n x k, both row-major with ld = k.
+ */
+int or_svd_adjoint_sddmm(int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx, int64_t k,
+                         const double *U, const double *S, const double *V, const double *dU,
+                         const double *dS, const double *dV, double *dvalues) {
+    if (m < 1 || n < 1 || k < 1 || k > m || k > n) return OR_ERR_INVALID_ARG;
+    for (int64_t a = 0; a < k; ++a)
+        if (!(S[a] > 0.0)) return OR_ERR_INVALID_ARG;
+    double *J = (double *)calloc((size_t)(k * k), sizeof(double));
+    double *K = (double *)calloc((size_t)(k * k), sizeof(double));
+    double *C = (double *)calloc((size_t)(k * k), sizeof(double));
+    double *UC = (double *)malloc(sizeof(double) * (size_t)(m * k));   /* U C          */
+    double *P = (double *)malloc(sizeof(double) * (size_t)(m * k));    /* Ub - U J     */
+    double *Qv = (double *)malloc(sizeof(double) * (size_t)(n * k));   /* Vb - V K     */
+    if (!J || !K || !C || !UC || !P || !Qv) {
+        free(J); free(K); free(C); free(UC); free(P); free(Qv);
+        return OR_ERR_OOM;
+    }
+    /* J = U^T Ub, K = V^T Vb */
+    for (int64_t a = 0; a < k; ++a)
+        for (int64_t b = 0; b < k; ++b) {
+            double sj = 0.0, sk = 0.0;
+            if (dU)
+                for (int64_t i = 0; i < m; ++i) sj += U[i * k + a] * dU[i * k + b];
+            if (dV)
+                for (int64_t j = 0; j < n; ++j) sk += V[j * k + a] * dV[j * k + b];
+            J[a * k + b] = sj;
+            K[a * k + b] = sk;
+        }
+    /* C */
+    for (int64_t a = 0; a < k; ++a)
+        for (int64_t b = 0; b < k; ++b) {
+            double c = 0.0;
+            if (a == b) {
+                c = dS ? dS[a] : 0.0;
+            } else {
+                const double gap = S[b] * S[b] - S[a] * S[a];
+                const double F = gap != 0.0 ? 1.0 / gap : 0.0;
+                c = F * (J[a * k + b] - J[b * k + a]) * S[b] + S[a] * F * (K[a * k + b] - K[b * k + a]);
+            }
+            C[a * k + b] = c;
+        }
+    /* UC = U C, P = Ub - U J, Qv = Vb - V K */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t b = 0; b < k; ++b) {
+            double uc = 0.0, uj = 0.0;
+            for (int64_t a = 0; a < k; ++a) {
+                uc += U[i * k + a] * C[a * k + b];
+                uj += U[i * k + a] * J[a * k + b];
+            }
+            UC[i * k + b] = uc;
+            P[i * k + b] = (dU ? dU[i * k + b] : 0.0) - uj;
+        }
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t b = 0; b < k; ++b) {
+            double vk = 0.0;
+            for (int64_t a = 0; a < k; ++a) vk += V[j * k + a] * K[a * k + b];
+            Qv[j * k + b] = (dV ? dV[j * k + b] : 0.0) - vk;
+        }
+    /* Abar at the nonzeros */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const int64_t j = colidx[e];
+            double acc = 0.0;
+            for (int64_t b = 0; b < k; ++b) {
+                acc += UC[i * k + b] * V[j * k + b];
+                acc += P[i * k + b] * V[j * k + b] / S[b];
+                acc += U[i * k + b] * Qv[j * k + b] / S[b];
+            }
+            dvalues[e] = acc;
+        }
+    free(J); free(K); free(C); free(UC); free(P); free(Qv);
+    return OR_OK;
+}

@@ -67,5 +67,12 @@ int or_frpca_ex(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int3
                 const double *vals, int64_t k, int64_t l, int64_t q, uint64_t seed, int stabilize,
                 double *U, double *S, double *V);
 
+/* Gradient with respect to the CSR values of a loss of the rank-k truncated
+ * SVD (U m x k, S k, V n x k, ld = k; cotangents dU, dS, dV may be NULL):
+ * the real thin-SVD adjoint (Townsend 2016) sampled at the nonzeros of A.
+ * Not part of the paper; used to check the backward kernels. */
+int or_svd_adjoint_sddmm(int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx, int64_t k,
+                         const double *U, const double *S, const double *V, const double *dU,
+                         const double *dS, const double *dV, double *dvalues);
 int or_num_threads(void);
 #endif

@@ -105,7 +105,7 @@ def test_frpca_exact_rank():
     Block scales decay as 0.85^b, so that the power step's eigSVD input stays
     within double precision's reach (a faster decay makes kappa(M)^2 exceed
     1e13 at q = 3, where no FP64 evaluation of eigSVD holds 1e-10)."""
-    from tests.test_oracle import block_rank_csr
+    from tests.helpers import block_rank_csr
     A, sig, _, _ = block_rank_csr(600, 300, 16, seed=3, scales=0.85 ** np.arange(16))
     mat = frpca.FrPCA.from_csr(A, device=DEV)
     for q in (2, 3, 4):

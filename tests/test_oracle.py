@@ -13,7 +13,7 @@ import scipy.sparse as sp
 import scipy.stats
 
 import synthetic
-from tests.helpers import dense_svd_topk, max_principal_sine, rel_err
+from tests.helpers import block_rank_csr, dense_svd_topk, max_principal_sine, rel_err
 
 pytestmark = pytest.mark.usefixtures("oracle_lib")
 
@@ -203,29 +203,6 @@ def test_eigsvd_rank_deficient(oracle_lib):
 
 
 # ----------------------------------------------------------------- the method
-def block_rank_csr(m, n, blocks, seed, scales=None):
-    """Sum of `blocks` disjoint rank-1 blocks x_b y_b^T * scale_b: its SVD is
-    known in closed form (sigma_b = scale_b |x_b| |y_b|)."""
-    rng = np.random.default_rng(seed)
-    rperm, cperm = rng.permutation(m), rng.permutation(n)
-    rsplit = np.array_split(rperm, blocks)
-    csplit = np.array_split(cperm, blocks)
-    if scales is None:
-        scales = 2.0 ** (-0.5 * np.arange(blocks))
-    rows, cols, vals, sig, U, V = [], [], [], [], np.zeros((m, blocks)), np.zeros((n, blocks))
-    for b in range(blocks):
-        x = rng.uniform(0.5, 1.5, size=rsplit[b].size) * rng.choice([-1, 1], size=rsplit[b].size)
-        y = rng.uniform(0.5, 1.5, size=csplit[b].size) * rng.choice([-1, 1], size=csplit[b].size)
-        rr, cc = np.meshgrid(rsplit[b], csplit[b], indexing="ij")
-        rows.append(rr.ravel()); cols.append(cc.ravel()); vals.append((np.outer(x, y) * scales[b]).ravel())
-        sig.append(scales[b] * np.linalg.norm(x) * np.linalg.norm(y))
-        U[rsplit[b], b] = x / np.linalg.norm(x)
-        V[csplit[b], b] = y / np.linalg.norm(y)
-    A = synthetic.from_coo(m, n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
-    order = np.argsort(-np.array(sig), kind="stable")
-    return A, np.array(sig)[order], U[:, order], V[:, order]
-
-
 @pytest.mark.parametrize("q", [2, 3, 4, 5, 6])
 @pytest.mark.parametrize("tall", [True, False])
 def test_frpca_exact_rank_closed_form(oracle_lib, q, tall):
