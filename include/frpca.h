@@ -193,8 +193,9 @@ frpca_status frpca_lu(frpca_handle h, int64_t R, int l, void *M, int64_t ld, frp
 frpca_status frpca_lu_noalloc(int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv, void *stream);
 
 /* Step 1 of eigSVD (Alg. 2): B = M^T M, l x l double (ld l), M R x l.  FP32
- * input is accumulated in float inside a tile of rows and in double across
- * tiles; FP64 input in double throughout. */
+ * input is accumulated in double-float (exact products, compensated sums)
+ * inside a tile of rows and in double across tiles; FP64 input in double
+ * throughout.  Synchronizes. */
 frpca_status frpca_gram(frpca_handle h, int64_t R, int l, const void *M, int64_t ld, frpca_dtype dt, double *B);
 
 /* Step 2 of eigSVD (Alg. 2): eigenvalues w (ascending) and orthonormal
@@ -207,6 +208,28 @@ frpca_status frpca_eig(frpca_handle h, int n, const double *B, double *w, double
  * FRPCA_ERR_RANK_DEFICIENT as in Sec. 3.1. */
 frpca_status frpca_eigsvd(frpca_handle h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt,
                           double *S, double *V);
+
+/* Backward of frpca_run: the gradient of a scalar loss with respect to the
+ * nnz CSR values of the handle's matrix A, given the rank-k result (U, S, V)
+ * and the loss's cotangents (dU, dS, dV).  Not in the paper: it applies the
+ * real thin-SVD adjoint (Townsend 2016, "Differentiating the singular value
+ * decomposition") to the returned triplets,
+ *   J = U^T dU, K = V^T dV, F_ab = 1/(S_b^2 - S_a^2) (a != b), F_aa = 0,
+ *   C = (F o (J - J^T)) diag(S) + diag(dS) + diag(S) (F o (K - K^T)),
+ *   Abar = U C V^T + (dU - U J) diag(1/S) V^T + U diag(1/S) (dV - V K)^T,
+ * and writes dvalues[e] = Abar[i_e, j_e] for every stored entry e of A (CSR
+ * order).  It is the exact gradient of the top-k SVD when the discarded
+ * singular values are zero; otherwise the couplings with them are dropped.
+ * A pair with S_a == S_b exactly gets F_ab = 0.
+ *   U, dU:   m x k, V, dV: n x k, row-major, ld = k, element type dt (device).
+ *   S, dS:   k doubles (device); S as returned by frpca_run (all > 0).
+ *   dU, dS, dV may be NULL (a zero cotangent); dvalues: nnz elements of dt.
+ * Only A's structure is read.  Buffers are caller-owned; the scratch (the two
+ * rank-2k factors, (m + n) x round_up(2k, 128 B)) belongs to the handle.
+ * Enqueued on the handle's stream, then synchronizes to report
+ * FRPCA_ERR_INVALID_ARG for an S entry that is not positive and finite. */
+frpca_status frpca_backward(frpca_handle h, int k, const void *U, const double *S, const void *V,
+                            const void *dU, const double *dS, const void *dV, frpca_dtype dt, void *dvalues);
 
 #ifdef __cplusplus
 }

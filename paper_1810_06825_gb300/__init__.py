@@ -28,7 +28,7 @@ EXPORTED = [
     "frpca_create", "frpca_destroy", "frpca_last_error", "frpca_run", "frpca_run_async", "frpca_sync",
     "frpca_refresh", "frpca_set_timing", "frpca_get_stats", "frpca_reset_stats",
     "frpca_gaussian", "frpca_spmm", "frpca_get_transpose", "frpca_lu", "frpca_gram", "frpca_eig",
-    "frpca_eigsvd",
+    "frpca_eigsvd", "frpca_backward",
 ]
 
 
@@ -94,6 +94,7 @@ def library() -> ctypes.CDLL:
         "frpca_gram": [P, I64, I, P, I64, I, P],
         "frpca_eig": [P, I, P, P, P],
         "frpca_eigsvd": [P, I64, I, P, I64, I, P, P],
+        "frpca_backward": [P, I, P, P, P, P, P, P, I, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -192,6 +193,10 @@ def frpca_eigsvd(h, R, l, M, ld, dtype, S, V) -> None:
 
 
 # ---------------------------------------------------------------- torch helpers
+def frpca_backward(h, k, U, S, V, dU, dS, dV, dtype, dvalues) -> None:
+    _check(library().frpca_backward(h, k, U, S, V, dU, dS, dV, dtype, dvalues), h)
+
+
 def _torch():
     import torch
     return torch
@@ -334,6 +339,25 @@ class FrPCA:
     def reset_stats(self):
         frpca_reset_stats(self.handle)
 
+    def backward(self, U, S, V, dU=None, dS=None, dV=None, out=None):
+        """Gradient with respect to the nnz CSR values of a loss of the rank-k
+        result (U, S, V), given its cotangents (any may be None = zero): the
+        thin-SVD adjoint sampled at A's nonzeros (``frpca_backward``)."""
+        torch = _torch()
+        k = S.shape[0]
+        dt = U.dtype
+        for t, rows in ((U, self.m), (V, self.n), (dU, self.m), (dV, self.n)):
+            if t is not None and (t.shape != (rows, k) or t.dtype != dt or not t.is_contiguous()):
+                raise ValueError("U, V, dU, dV must be contiguous (rows x k) tensors of one dtype")
+        for t in (S, dS):
+            if t is not None and (t.shape != (k,) or t.dtype != torch.float64 or not t.is_contiguous()):
+                raise ValueError("S and dS must be contiguous float64 vectors of length k")
+        out = out if out is not None else torch.empty(self.nnz, dtype=dt, device=U.device)
+        ptr = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
+        frpca_backward(self.handle, k, U.data_ptr(), S.data_ptr(), V.data_ptr(), ptr(dU), ptr(dS), ptr(dV),
+                       _dtype_code(U), out.data_ptr() if self.nnz else None)
+        return out
+
     def transpose(self):
         torch = _torch()
         dev = self.values.device
@@ -397,3 +421,52 @@ def eigsvd(M):
     V = torch.empty((l, l), dtype=torch.float64, device=M.device)
     frpca_eigsvd(_Context.get(), R, l, U.data_ptr(), U.stride(0), _dtype_code(U), S.data_ptr(), V.data_ptr())
     return U, S, V
+
+
+def _make_svd_function():
+    torch = _torch()
+
+    class FrpcaSVD(torch.autograd.Function):
+        """(U, S, V) = frPCA of the CSR matrix whose values are the input.
+
+        The forward runs ``frpca_run`` on a handle that borrows ``values``
+        (A^T is rebuilt on every call, so in-place updates are seen); the
+        backward runs ``frpca_backward``.  Nothing from the q passes is kept:
+        the adjoint needs only U, S, V and the cotangents."""
+
+        @staticmethod
+        def forward(ctx, values, indptr, indices, shape, k, l, q, seed, mat):
+            precision = "fp64" if values.dtype == torch.float64 else "fp32"
+            if mat is None:
+                mat = FrPCA(indptr, indices, values.detach(), shape, borrow=True)
+            else:
+                if mat.values.data_ptr() != values.data_ptr() or mat.dtype != values.dtype:
+                    raise ValueError("mat must borrow the same values tensor")
+                mat.refresh()
+            U, S, V = mat.run(k, l, q, seed=seed, precision=precision)
+            ctx.mat = mat
+            ctx.set_materialize_grads(False)
+            ctx.save_for_backward(U, S, V)
+            return U, S, V
+
+        @staticmethod
+        def backward(ctx, dU, dS, dV):
+            U, S, V = ctx.saved_tensors
+            c = lambda t, dt: None if t is None else t.to(dt).contiguous()  # noqa: E731
+            dvalues = ctx.mat.backward(U, S, V, c(dU, U.dtype), c(dS, torch.float64), c(dV, V.dtype))
+            return dvalues, None, None, None, None, None, None, None, None
+
+    return FrpcaSVD
+
+
+_svd_fn = None
+
+
+def frpca_svd(values, indptr, indices, shape, k: int, l: int, q: int, seed: int = 0, mat=None):
+    """Differentiable rank-k frPCA: returns (U, S, V) with gradients flowing to
+    ``values`` (the CSR values, float32 -> FP32 path, float64 -> FP64 path).
+    ``mat`` may be an ``FrPCA`` that borrows ``values`` (reused across calls)."""
+    global _svd_fn
+    if _svd_fn is None:
+        _svd_fn = _make_svd_function()
+    return _svd_fn.apply(values, indptr, indices, shape, k, l, q, seed, mat)

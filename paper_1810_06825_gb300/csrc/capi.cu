@@ -27,7 +27,7 @@ struct frpca_ctx {
     DevBuf alt_A, alt_AT;                        // values converted to the other dtype
     bool alt_ready = false;
     SpmmPlan planA, planAT;
-    DevBuf ws_q, ws_w, ws_spmm, ws_gram, ws_eig, ws_lu, ws_small, ws_sign, ws_scratch, ws_scan;
+    DevBuf ws_q, ws_w, ws_spmm, ws_gram, ws_eig, ws_lu, ws_small, ws_sign, ws_scratch, ws_scan, ws_bwd;
     std::string err;
     // instrumentation
     bool timing = false;
@@ -445,7 +445,7 @@ frpca_status frpca_destroy(frpca_handle h) {
     h->planAT.free_all();
     for (DevBuf *b : {&h->own_rowptr, &h->own_colidx, &h->own_vals, &h->t_rowptr, &h->t_colidx, &h->t_vals,
                       &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
-                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan})
+                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd})
         b->release();
     for (auto &mk : h->marks) {
         cudaEventDestroy(mk.a);
@@ -607,6 +607,22 @@ frpca_status frpca_eigsvd(frpca_handle h, int64_t R, int l, void *M, int64_t ld,
     CK(launch_make_w(l, l, sm.w, sm.V, 0, 1, nullptr, dt, sm.W1, S, h->d_status, h->stream), "make_w");
     CK(launch_apply(R, l, M, ld, sm.W1, l, M, ld, dt, h->stream), "apply");
     CK(cudaMemcpyAsync(V, sm.V, sizeof(double) * (size_t)l * l, cudaMemcpyDeviceToDevice, h->stream), "copy V");
+    return read_status(h);
+}
+
+frpca_status frpca_backward(frpca_handle h, int k, const void *U, const double *S, const void *V,
+                            const void *dU, const double *dS, const void *dV, frpca_dtype dt, void *dvalues) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    if (!h->has_matrix) return fail(h, FRPCA_ERR_INVALID_ARG, "backward needs a handle created with a matrix");
+    if (dt != FRPCA_F32 && dt != FRPCA_F64) return fail(h, FRPCA_ERR_INVALID_ARG, "bad dtype");
+    if (k < 1 || k > h->A.rows || k > h->A.cols || !U || !S || !V || (h->A.nnz > 0 && !dvalues))
+        return fail(h, FRPCA_ERR_INVALID_ARG, "bad backward arguments");
+    if (k > FRPCA_MAX_L) return fail(h, FRPCA_ERR_UNSUPPORTED, "k > 160 is not supported");
+    frpca_status st = reset_status(h);
+    if (st != FRPCA_OK) return st;
+    CK(h->ws_bwd.ensure(backward_workspace_bytes(h->A.rows, h->A.cols, k, dt, h->num_sms)), "alloc backward workspace");
+    CK(launch_backward(h->A, k, U, S, V, dU, dS, dV, dt, dvalues, h->ws_bwd.ptr, h->num_sms, h->d_status, h->stream),
+       "backward launch");
     return read_status(h);
 }
 

@@ -110,4 +110,10 @@ cudaError_t launch_column_signs(int64_t R, int k, const void *X, int64_t ld, frp
 cudaError_t launch_scale_columns(int64_t R, int k, void *X, int64_t ld, frpca_dtype dt, const double *sign,
                                  cudaStream_t s);
 
+// ---- backward.cu
+size_t backward_workspace_bytes(int64_t m, int64_t n, int k, frpca_dtype dt, int sms);
+cudaError_t launch_backward(const DeviceCSR &A, int k, const void *U, const double *S, const void *V, const void *dU,
+                            const double *dS, const void *dV, frpca_dtype dt, void *dvalues, void *ws, int sms,
+                            int *d_status, cudaStream_t s);
+
 }  // namespace frpca
