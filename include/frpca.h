@@ -48,8 +48,9 @@ typedef enum frpca_dtype { FRPCA_F32 = 0, FRPCA_F64 = 1 } frpca_dtype;
 
 /* Arithmetic of a run.  FP64: every step in double.  FP32: SpMM, LU, Gram and
  * the apply step in float; the l x l eigendecomposition always returns double
- * precision eigenpairs.  FP32_SPLITGRAM: FP32 with the Gram matrix of eigSVD
- * formed on the tensor cores from split-BF16 operands. */
+ * precision eigenpairs.  FP32_SPLITGRAM: FP32 with the Gram matrix of the
+ * final eigSVD (the one over max(m, n) rows) formed on the tensor cores from
+ * split-BF16 operands; needs l <= 128 (see frpca_gram_splitbf16). */
 typedef enum frpca_precision {
     FRPCA_PREC_FP64 = 0,
     FRPCA_PREC_FP32 = 1,
@@ -197,6 +198,15 @@ frpca_status frpca_lu_noalloc(int64_t R, int l, void *M, int64_t ld, frpca_dtype
  * inside a tile of rows and in double across tiles; FP64 input in double
  * throughout.  Synchronizes. */
 frpca_status frpca_gram(frpca_handle h, int64_t R, int l, const void *M, int64_t ld, frpca_dtype dt, double *B);
+
+/* Step 1 of eigSVD (Alg. 2) in the precision form FRPCA_PREC_FP32_SPLITGRAM:
+ * B = M^T M (l x l double, ld l) for an FP32 block M (R x l, R >= 1,
+ * l <= 128, ld a multiple of 4, M 16-byte aligned) on the tcgen05 tensor
+ * cores.  Each entry is split into three BF16 terms (x = h + m + s exactly);
+ * the six products above 2^-24 relative are accumulated in FP32 in tensor
+ * memory over 128-row chunks and summed across chunks in FP64; B is returned
+ * exactly symmetric.  Synchronizes; FRPCA_ERR_UNSUPPORTED for l > 128. */
+frpca_status frpca_gram_splitbf16(frpca_handle h, int64_t R, int l, const float *M, int64_t ld, double *B);
 
 /* Step 2 of eigSVD (Alg. 2): eigenvalues w (ascending) and orthonormal
  * eigenvectors V (n x n, column c for w[c]) of the symmetric n x n double

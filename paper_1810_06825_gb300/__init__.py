@@ -28,7 +28,7 @@ EXPORTED = [
     "frpca_create", "frpca_destroy", "frpca_last_error", "frpca_run", "frpca_run_async", "frpca_sync",
     "frpca_refresh", "frpca_set_timing", "frpca_get_stats", "frpca_reset_stats",
     "frpca_gaussian", "frpca_spmm", "frpca_get_transpose", "frpca_lu", "frpca_gram", "frpca_eig",
-    "frpca_eigsvd", "frpca_backward",
+    "frpca_eigsvd", "frpca_backward", "frpca_gram_splitbf16",
 ]
 
 
@@ -95,6 +95,7 @@ def library() -> ctypes.CDLL:
         "frpca_eig": [P, I, P, P, P],
         "frpca_eigsvd": [P, I64, I, P, I64, I, P, P],
         "frpca_backward": [P, I, P, P, P, P, P, P, I, P],
+        "frpca_gram_splitbf16": [P, I64, I, P, I64, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -193,6 +194,10 @@ def frpca_eigsvd(h, R, l, M, ld, dtype, S, V) -> None:
 
 
 # ---------------------------------------------------------------- torch helpers
+def frpca_gram_splitbf16(h, R, l, M, ld, B) -> None:
+    _check(library().frpca_gram_splitbf16(h, R, l, M, ld, B), h)
+
+
 def frpca_backward(h, k, U, S, V, dU, dS, dV, dtype, dvalues) -> None:
     _check(library().frpca_backward(h, k, U, S, V, dU, dS, dV, dtype, dvalues), h)
 
@@ -396,6 +401,20 @@ def gram(M):
         M = M.contiguous()
     B = torch.empty((l, l), dtype=torch.float64, device=M.device)
     frpca_gram(_Context.get(), R, l, M.data_ptr(), M.stride(0), _dtype_code(M), B.data_ptr())
+    return B
+
+
+def gram_splitbf16(M):
+    """B = M^T M (float64) of an FP32 block on the tensor cores (split BF16)."""
+    torch = _torch()
+    _need_cuda(M)
+    R, l = M.shape
+    if M.dtype != torch.float32:
+        raise TypeError("gram_splitbf16 takes float32 blocks")
+    if M.stride(1) != 1 or M.stride(0) % 4 or M.data_ptr() % 16:
+        M = empty_block(R, l, torch.float32, M.device).copy_(M)
+    B = torch.empty((l, l), dtype=torch.float64, device=M.device)
+    frpca_gram_splitbf16(_Context.get(), R, l, M.data_ptr(), M.stride(0), B.data_ptr())
     return B
 
 

@@ -190,13 +190,21 @@ frpca_status lu_step(frpca_ctx *h, int64_t R, int l, void *M, int64_t ld, frpca_
 }
 
 // Gram + eig of an R x l block: eigenvalues (ascending) into w, vectors into V.
+// With tensor_gram (FP32 only, l <= 128) the Gram is formed on the tensor
+// cores from split-BF16 operands (the FP32_SPLITGRAM precision form).
 frpca_status gram_eig(frpca_ctx *h, int64_t R, int l, const void *M, int64_t ld, frpca_dtype dt, double *B, double *w,
-                      double *V) {
-    CK(h->ws_gram.ensure(gram_workspace_bytes(R, l, h->num_sms)), "alloc gram workspace");
+                      double *V, bool tensor_gram = false) {
+    CK(h->ws_gram.ensure(tensor_gram ? gram_tc_workspace_bytes(R, l, h->num_sms)
+                                     : gram_workspace_bytes(R, l, h->num_sms)),
+       "alloc gram workspace");
     CK(h->ws_eig.ensure(eig_workspace_bytes(l)), "alloc eig workspace");
     {
         PhaseTimer t(h, PH_GRAM);
-        CK(launch_gram(R, l, M, ld, dt, B, h->ws_gram.ptr, h->num_sms, h->stream), "gram launch");
+        if (tensor_gram)
+            CK(launch_gram_tc(R, l, (const float *)M, ld, B, h->ws_gram.ptr, h->num_sms, h->d_status, h->stream),
+               "tensor-core gram launch");
+        else
+            CK(launch_gram(R, l, M, ld, dt, B, h->ws_gram.ptr, h->num_sms, h->stream), "gram launch");
     }
     PhaseTimer t(h, PH_EIG);
     CK(launch_eig(l, B, w, V, h->ws_eig.ptr, h->d_status, h->stream), "eig launch");
@@ -245,10 +253,12 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
     if (k < 1 || l < k || (int64_t)l > std::min(m, n) || q < 2)
         return fail(h, FRPCA_ERR_INVALID_ARG, "need 1 <= k <= l <= min(m, n) and q >= 2");
     if (l > FRPCA_MAX_L) return fail(h, FRPCA_ERR_UNSUPPORTED, "l > 160 is not supported");
-    if (o->precision == FRPCA_PREC_FP32_SPLITGRAM)
-        return fail(h, FRPCA_ERR_UNSUPPORTED, "FP32_SPLITGRAM is not available in this build");
-    if (o->precision != FRPCA_PREC_FP64 && o->precision != FRPCA_PREC_FP32)
+    if (o->precision != FRPCA_PREC_FP64 && o->precision != FRPCA_PREC_FP32 &&
+        o->precision != FRPCA_PREC_FP32_SPLITGRAM)
         return fail(h, FRPCA_ERR_INVALID_ARG, "unknown precision");
+    const bool split_gram = o->precision == FRPCA_PREC_FP32_SPLITGRAM;
+    if (split_gram && l > gram_tc_max_l())
+        return fail(h, FRPCA_ERR_UNSUPPORTED, "FP32_SPLITGRAM needs l <= 128");
     int alg = o->alg ? o->alg : (m >= n ? 6 : 5);
     if ((alg != 5 && alg != 6) || (alg == 6 && m < n) || (alg == 5 && m > n))
         return fail(h, FRPCA_ERR_INVALID_ARG, "Alg. 6 needs m >= n and Alg. 5 needs m <= n");
@@ -307,7 +317,11 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
     // Final pass: [U^, S^, V^] = eigSVD(A Q); ind = k+s : -1 : s+1 keeps the k
     // largest in descending order; U = U^(:, ind), V = Q V^(:, ind).
     if ((st = spmm_pass(h, fwd_trans, l, Q, ld, W, ld, dt)) != FRPCA_OK) return st;
-    if ((st = gram_eig(h, rw, l, W, ld, dt, sm.B, sm.w, sm.V)) != FRPCA_OK) return st;
+    // The precision form takes this Gram (the big one, R = max(m, n) rows) to
+    // the tensor cores; its condition number is that of A Q's singular values
+    // (about 1e2 squared), which the split-BF16 product with 128-row FP32
+    // accumulation carries.  The power-iteration Gram keeps double-float.
+    if ((st = gram_eig(h, rw, l, W, ld, dt, sm.B, sm.w, sm.V, split_gram)) != FRPCA_OK) return st;
     PhaseTimer fin(h, PH_FINISH);
     void *thin = (alg == 6) ? V : U;  // Q V^(:, ind), rq x k
     void *wide = (alg == 6) ? U : V;  // U^(:, ind),   rw x k
@@ -579,6 +593,18 @@ frpca_status frpca_gram(frpca_handle h, int64_t R, int l, const void *M, int64_t
     CK(launch_gram(R, l, M, ld, dt, B, h->ws_gram.ptr, h->num_sms, h->stream), "gram launch");
     CK(cudaStreamSynchronize(h->stream), "synchronize");
     return FRPCA_OK;
+}
+
+frpca_status frpca_gram_splitbf16(frpca_handle h, int64_t R, int l, const float *M, int64_t ld, double *B) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    if (l < 1 || R < 1 || !ld_ok(ld, l, FRPCA_F32) || !B || !M || !aligned16(M))
+        return fail(h, FRPCA_ERR_INVALID_ARG, "bad gram arguments");
+    if (l > gram_tc_max_l()) return fail(h, FRPCA_ERR_UNSUPPORTED, "l > 128 is not supported on the tensor cores");
+    frpca_status st = reset_status(h);
+    if (st != FRPCA_OK) return st;
+    CK(h->ws_gram.ensure(gram_tc_workspace_bytes(R, l, h->num_sms)), "alloc gram workspace");
+    CK(launch_gram_tc(R, l, M, ld, B, h->ws_gram.ptr, h->num_sms, h->d_status, h->stream), "tensor-core gram launch");
+    return read_status(h);
 }
 
 frpca_status frpca_eig(frpca_handle h, int n, const double *B, double *w, double *V) {

@@ -110,6 +110,12 @@ cudaError_t launch_column_signs(int64_t R, int k, const void *X, int64_t ld, frp
 cudaError_t launch_scale_columns(int64_t R, int k, void *X, int64_t ld, frpca_dtype dt, const double *sign,
                                  cudaStream_t s);
 
+// ---- gram_tc.cu (split-BF16 Gram on the tcgen05 tensor cores, FP32 input)
+int gram_tc_max_l();
+size_t gram_tc_workspace_bytes(int64_t R, int l, int sms);
+cudaError_t launch_gram_tc(int64_t R, int l, const float *M, int64_t ld, double *B, void *ws, int sms, int *d_status,
+                           cudaStream_t s);
+
 // ---- backward.cu
 size_t backward_workspace_bytes(int64_t m, int64_t n, int k, frpca_dtype dt, int sms);
 cudaError_t launch_backward(const DeviceCSR &A, int k, const void *U, const double *S, const void *V, const void *dU,
