@@ -29,7 +29,27 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "powerlaw_200000x50000_deg100"
+BWD_WORKLOAD = "powerlaw_100000x20000_deg50"
 L2_BYTES = 129 * 2**20
+PRECISIONS = ("fp32", "fp64", "fp32_splitgram")
+
+# DRAM traffic of one SpMM pass (dram__bytes_read.sum + dram__bytes_write.sum),
+# averaged over the q = 5 schedule (3 passes with A, 2 with A^T), from the ncu
+# capture summarized in profiles/spmm_kernel_powerlaw_200000x50000.md.  Valid
+# only while spmm_kernel is unchanged since that capture.
+NCU_SPMM_TRAFFIC = {(WORKLOAD, "f32", 5): (3 * 272.0e6 + 2 * 1379.0e6) / 5}
+
+
+def _max_sine(X, Y):
+    """Largest principal-angle sine between the column spaces of X and Y."""
+    Qx, _ = np.linalg.qr(np.asarray(X, dtype=np.float64))
+    Qy, _ = np.linalg.qr(np.asarray(Y, dtype=np.float64))
+    return float(np.linalg.norm(Qy - Qx @ (Qx.T @ Qy), 2))
+
+
+def _errors(U, S, V, ref):
+    Uo, So, Vo = ref
+    return {"sigma_rel": float(np.max(np.abs(S - So) / So)), "sine_U": _max_sine(U, Uo), "sine_V": _max_sine(V, Vo)}
 
 
 def _peaks():
@@ -113,7 +133,8 @@ def _max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -156,6 +177,71 @@ def _config(args, w):
             "exceeds 129 MB), no flush between steps", "parallelism": f"independent replicas x{args.gpus}"}
 
 
+def _fwd_bwd(dev, with_ref: bool) -> dict:
+    """Forward + backward of the differentiation workload (100,000 x 20,000,
+    ~5M nnz, k=32, l=48, q=4, FP32): loss = sum(S) + ||U^T Y||^2 with Y a
+    100,000 x 8 Gaussian, through the autograd Function (frpca_run, then
+    frpca_backward).  Device time per forward and per backward, and the
+    errors against the oracle (singular values; gradient against the oracle's
+    adjoint of the same U, S, V and cotangents)."""
+    import torch
+
+    import paper_1810_06825_gb300 as frpca
+    import synthetic
+
+    w = synthetic.WORKLOADS[BWD_WORKLOAD]
+    k, l, q = w["k"], w["l"], w["q"]
+    A = synthetic.make_workload(BWD_WORKLOAD, seed=1, dtype=np.float32)
+    vals = torch.tensor(A.data, device=dev, requires_grad=True)
+    ip, ix = torch.tensor(A.indptr, device=dev), torch.tensor(A.indices, device=dev)
+    mat = frpca.FrPCA(ip, ix, vals.detach(), (A.m, A.n))
+    Y = torch.from_numpy(np.random.default_rng(2).standard_normal((A.m, 8)).astype(np.float32)).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        vals.grad = None
+        U, S, V = frpca.frpca_svd(vals, ip, ix, (A.m, A.n), k, l, q, seed=0, mat=mat)
+        if ev is not None:
+            ev.record(stream)
+        loss = S.sum() + ((U.T @ Y) ** 2).sum().double()
+        loss.backward()
+        return U, S, V
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    n = 5
+    marks = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+              torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for a, b, c in marks:
+        a.record(stream)
+        step(b)
+        c.record(stream)
+    torch.cuda.synchronize()
+    fwd = float(np.mean([a.elapsed_time(b) for a, b, _ in marks]))
+    tot = float(np.mean([a.elapsed_time(c) for a, _, c in marks]))
+    out = {"workload": BWD_WORKLOAD, "m": A.m, "n": A.n, "nnz": int(A.nnz), "k": k, "l": l, "q": q,
+           "precision": "fp32", "loss": "sum(S) + ||U^T Y||^2, Y 100000 x 8", "fwd_ms": fwd, "bwd_ms": tot - fwd,
+           "fwd_bwd_ms": tot}
+    if with_ref:
+        import oracle
+        oracle.build()
+        U, S, V = step()
+        torch.cuda.synchronize()
+        Un, Sn, Vn = (t.detach().double().cpu().numpy() for t in (U, S, V))
+        Yn = Y.double().cpu().numpy()
+        g = vals.grad.double().cpu().numpy()
+        gref = oracle.svd_adjoint_sddmm(A.m, A.n, A.indptr, A.indices, Un, Sn, Vn, 2.0 * Yn @ (Yn.T @ Un),
+                                        np.ones(k), None)
+        Uo, So, Vo = oracle.frpca(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64), k, l, q, 0)
+        out.update({"sigma_rel": float(np.max(np.abs(Sn - So) / So)), "sine_U": _max_sine(Un, Uo),
+                    "sine_V": _max_sine(Vn, Vo),
+                    "grad_rel": float(np.max(np.abs(g - gref)) / np.max(np.abs(gref))),
+                    "errors_vs": "FP64 CPU oracle (forward); oracle adjoint of the GPU's U, S, V (gradient)"})
+    mat.close()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -166,7 +252,7 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     w = synthetic.WORKLOADS[args.workload]
     k, l, q = w["k"], w["l"], args.q
-    dt_np = np.float64 if args.precision == "fp64" else np.float32
+    dt_np = np.float32  # the workload's values are FP32; the FP64 path converts them once
     A = synthetic.make_workload(args.workload, seed=1 + rank, dtype=dt_np)
     indptr = torch.from_numpy(A.indptr).to(dev)
     indices = torch.from_numpy(A.indices).to(dev)
@@ -244,24 +330,58 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = _peaks()
     spmm_ms_per_pass = st["spmm_ms"] / max(st["spmm_passes"], 1)
     achieved = (st["spmm_bytes"] / max(st["spmm_passes"], 1)) / (spmm_ms_per_pass * 1e-3) / 1e9
+    dtype_tag = "f64" if args.precision == "fp64" else "f32"
     roofline = {"bound": "hbm", "kernel": "spmm_kernel (+ fix-up), one SpMM pass", "achieved": achieved,
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "ms_per_pass": spmm_ms_per_pass,
+                "traffic": NCU_SPMM_TRAFFIC.get((args.workload, dtype_tag, args.q)), "ms_per_pass": spmm_ms_per_pass,
                 "bytes_per_pass": st["spmm_bytes"] / max(st["spmm_passes"], 1),
                 "fp32_tflops": st["spmm_flops"] / max(st["spmm_ms"], 1e-9) / 1e9}
     phases = {key: st[key] / args.steps for key in ("spmm_ms", "lu_ms", "gram_ms", "eig_ms", "apply_ms",
                                                     "gaussian_ms", "transpose_ms", "finish_ms")}
 
-    cpu = None
+    cpu, ref = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
         vals = A.data.astype(np.float64)
         t0 = time.perf_counter()
-        oracle.frpca(A.m, A.n, A.indptr, A.indices, vals, k, l, q, 0)
+        ref = oracle.frpca(A.m, A.n, A.indptr, A.indices, vals, k, l, q, 0)
         cpu_s = time.perf_counter() - t0
         cpu = {"value": cpu_s, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": f"the whole workload, one FP64 frPCA run (q={q})"}
+
+    # The precision forms side by side on the same matrix: device time of one
+    # step (A^T rebuild + run) and, when the oracle ran, the error against it.
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = {}
+        for prec in PRECISIONS:
+            pdt = torch.float64 if prec == "fp64" else torch.float32
+            Up = torch.empty((A.m, k), dtype=pdt, device=dev)
+            Vp = torch.empty((A.n, k), dtype=pdt, device=dev)
+
+            def pstep():
+                mat.refresh()
+                mat.run(k, l, q, seed=0, precision=prec, out=(Up, S, Vp), sync=False)
+
+            for _ in range(3):
+                pstep()
+            frpca.frpca_sync(mat.handle)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(5):
+                pstep()
+            a1.record(stream)
+            frpca.frpca_sync(mat.handle)
+            entry = {"ms_per_step": a0.elapsed_time(a1) / 5}
+            if ref is not None:
+                entry.update(_errors(Up.double().cpu().numpy(), S.cpu().numpy(), Vp.double().cpu().numpy(), ref))
+            forms[prec] = entry
+        forms["errors_vs"] = "FP64 CPU oracle, same Philox Omega" if ref is not None else None
+
+    fwd_bwd = None
+    if rank == 0 and not args.no_fwd_bwd:
+        fwd_bwd = _fwd_bwd(dev, with_ref=not args.no_cpu_baseline)
 
     if rank == 0:
         line = {
@@ -270,7 +390,7 @@ def run_ours(args, world, rank, local):
             "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
             "config": _config(args, w), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(st["kernel_launches"]), "clocks": clk, "phases_ms_per_step": phases,
-            "nnz": int(A.nnz),
+            "nnz": int(A.nnz), "precision_forms": forms, "fwd_bwd": fwd_bwd,
         }
         print(json.dumps(line), flush=True)
     mat.close()
@@ -285,9 +405,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--q", type=int, default=5)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=list(PRECISIONS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the per-precision comparison")
+    ap.add_argument("--no-fwd-bwd", action="store_true", help="skip the forward + backward measurement")
     args = ap.parse_args()
     world, rank, local = _dist()
     if world > 1:
