@@ -32,7 +32,7 @@ namespace frpca {
 namespace {
 
 constexpr int kJacobiThreads = 1024;
-constexpr int kJacobiCtas = 8;  // CTAs sharing the rows of V (each holds all of A)
+constexpr int kJacobiCtas = 60;  // CTAs sharing the rows of V (each holds all of A)
 constexpr int kJacobiMaxSweeps = 24;
 constexpr int kRefineSteps = 5;
 constexpr int kLevels = 3;
@@ -44,19 +44,6 @@ __device__ inline bool converged(const unsigned long long *emax) {
     return emax && *emax <= (unsigned long long)__double_as_longlong(1.0e-15);
 }
 
-__device__ inline void pair_of(int r, int k, int np, int &p, int &q) {
-    int a, b;
-    if (k == 0) {
-        a = np - 1;
-        b = r;
-    } else {
-        a = (r + k) % (np - 1);
-        b = (r - k + (np - 1)) % (np - 1);
-    }
-    p = min(a, b);
-    q = max(a, b);
-}
-
 __device__ inline int dim_of(const int *dn, int n_static) { return dn ? *dn : n_static; }
 
 // Float Jacobi on the n x n block of B (leading dimension ld), scaled by its
@@ -64,19 +51,26 @@ __device__ inline int dim_of(const int *dn, int n_static) { return dn ? *dn : n_
 // A pair is rotated while |a_pq| > 2^-23 sqrt(|a_pp a_qq|) (the relative test
 // that lets Jacobi resolve small eigenvalues of a definite matrix to float
 // accuracy); the sweep loop stops at the first sweep without rotations or
-// after kJacobiMaxSweeps.
+// after kJacobiMaxSweeps.  Rotations use the fast reciprocal and reciprocal
+// square root: any rotation close to the exact one keeps the iteration
+// convergent, and its orthogonality error (a few ulps) is removed by the
+// double-precision refinement that follows.
 //
-// The round is bound by shared-memory traffic, so the work is split over
-// gridDim.x CTAs without any communication: every CTA runs the same
-// deterministic sequence of rotations on its own copy of A (only the upper
-// triangle is updated) and accumulates only its own slice of the rows of V.
-__global__ void __launch_bounds__(kJacobiThreads)
+// The round is bound by shared-memory traffic and instruction issue in one
+// SM, so the work is split over gridDim.x CTAs without any communication:
+// every CTA runs the same deterministic sequence of rotations on its own copy
+// of A (only the upper triangle is updated) and accumulates only its own
+// slice of the rows of V (one or two rows each with 60 CTAs).  Each thread's
+// items (2 x 2 blocks of A, entries of V) are fixed for the whole kernel and
+// kept in registers; NI = items per thread.
+template <int NI>
+__global__ void __launch_bounds__(kJacobiThreads, 1)
 jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int ld, double *__restrict__ X) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = dim_of(dn, n_static);
     if (n < 1) return;
     const int np = n + (n & 1);
-    const int nb = np / 2;
+    const int nb = np / 2, m1 = np - 1;
     const int nblk = nb * (nb + 1) / 2;
     const int vrows = (np + gridDim.x - 1) / gridDim.x;
     const int v0 = blockIdx.x * vrows;
@@ -84,11 +78,8 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
     const int lda = np + 1;  // odd row strides: fewer shared-memory bank conflicts
     float *A = reinterpret_cast<float *>(smem_raw);
     float *V = A + np * lda;  // rows v0 .. v0 + vcnt - 1 of V, stride lda
-    ushort2 *blk = reinterpret_cast<ushort2 *>(V + (size_t)vrows * lda);
-    auto up = [lda](int r, int c) { return r <= c ? r * lda + c : c * lda + r; };
     __shared__ float4 rot[FRPCA_MAX_L / 2];  // (c, s, p, q) of each pair, one 16-byte load
-    __shared__ int rotations;
-    __shared__ unsigned long long maxdiag;  // bit pattern of max |B_ii| (monotone)
+    __shared__ unsigned long long maxdiag;   // bit pattern of max |B_ii| (monotone)
     __shared__ double scale;
 
     if (threadIdx.x == 0) maxdiag = 0ull;
@@ -109,82 +100,114 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
         const int i = v0 + idx / np, j = idx % np;
         V[(idx / np) * lda + j] = (i == j) ? 1.0f : 0.0f;
     }
-    for (int idx = threadIdx.x; idx < nb * nb; idx += kJacobiThreads) {
-        const int a = idx / nb, b = idx - a * nb;
-        if (a <= b) blk[a * nb - a * (a - 1) / 2 + (b - a)] = make_ushort2((unsigned short)a, (unsigned short)b);
+    // This thread's items: kind 0 = block (ka, kb) of pairs, ka <= kb;
+    // kind 1 = entry (row, pair k) of the V slice; -1 = none.
+    int kind[NI], ia[NI], ib[NI];
+#pragma unroll
+    for (int u = 0; u < NI; ++u) {
+        int idx = threadIdx.x + u * kJacobiThreads;
+        kind[u] = -1;
+        ia[u] = 0;
+        ib[u] = 0;
+        if (idx < nblk) {
+            int a = 0;
+            while (idx >= nb - a) {
+                idx -= nb - a;
+                ++a;
+            }
+            kind[u] = 0;
+            ia[u] = a;
+            ib[u] = a + idx;
+        } else if (idx < nblk + vcnt * nb) {
+            const int v = idx - nblk;
+            kind[u] = 1;
+            ia[u] = v / nb;
+            ib[u] = v - (v / nb) * nb;
+        }
     }
-    __syncthreads();
 
     for (int sweep = 0; sweep < kJacobiMaxSweeps; ++sweep) {
-        if (threadIdx.x == 0) rotations = 0;
-        __syncthreads();
-        for (int r = 0; r < np - 1; ++r) {
+        int rotated = 0;
+        for (int r = 0; r < m1; ++r) {
+            __syncthreads();
             if ((int)threadIdx.x < nb) {
-                int p, q;
-                pair_of(r, threadIdx.x, np, p, q);
-                float c = 1.0f, s = 0.0f;
+                // Pair k of round r of the round-robin ordering.
+                const int k = threadIdx.x;
+                int a = m1, b = r;
+                if (k > 0) {
+                    a = r + k;
+                    if (a >= m1) a -= m1;
+                    b = r - k;
+                    if (b < 0) b += m1;
+                }
+                const int p = min(a, b), q = max(a, b);
+                float c = 1.0f, sn = 0.0f;
                 if (q < n) {
                     const float apq = A[p * lda + q], app = A[p * lda + p], aqq = A[q * lda + q];
-                    if (apq != 0.0f && fabsf(apq) > 0x1p-23f * sqrtf(fabsf(app) * fabsf(aqq))) {
-                        const float tau = (aqq - app) / (2.0f * apq);
-                        const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
-                        c = 1.0f / sqrtf(1.0f + t * t);
-                        s = t * c;
-                        atomicAdd(&rotations, 1);
+                    if (apq != 0.0f && apq * apq > 0x1p-46f * fabsf(app * aqq)) {
+                        const float tau = __fdividef(aqq - app, 2.0f * apq);
+                        const float at = fabsf(tau);
+                        const float h = fmaf(tau, tau, 1.0f);
+                        const float t = at < 1e18f ? copysignf(__fdividef(1.0f, at + h * rsqrtf(h)), tau)
+                                                   : __fdividef(0.5f, tau);
+                        c = rsqrtf(fmaf(t, t, 1.0f));
+                        sn = t * c;
+                        rotated = 1;
                     }
                 }
-                rot[threadIdx.x] = make_float4(c, s, __int_as_float(p), __int_as_float(q));
+                rot[k] = make_float4(c, sn, __int_as_float(p), __int_as_float(q));
             }
             __syncthreads();
-            const int total = nblk + vcnt * nb;
-            for (int idx = threadIdx.x; idx < total; idx += kJacobiThreads) {
-                if (idx < nblk) {
+#pragma unroll
+            for (int u = 0; u < NI; ++u) {
+                if (kind[u] == 0) {
                     // A <- J^T A J on the 2x2 block of pairs (ka, kb), upper triangle.
-                    const ushort2 ab = blk[idx];
-                    const int ka = ab.x, kb = ab.y;
+                    const int ka = ia[u], kb = ib[u];
                     const float4 ra = rot[ka], rb = rot[kb];
                     const float ca = ra.x, sa = ra.y, cb = rb.x, sb = rb.y;
                     if (sa == 0.0f && sb == 0.0f) continue;
                     const int pa = __float_as_int(ra.z), qa = __float_as_int(ra.w);
                     const int pb = __float_as_int(rb.z), qb = __float_as_int(rb.w);
-                    const int i11 = up(pa, pb), i12 = up(pa, qb), i21 = up(qa, pb), i22 = up(qa, qb);
+                    const int i11 = min(pa, pb) * lda + max(pa, pb), i12 = min(pa, qb) * lda + max(pa, qb);
+                    const int i21 = min(qa, pb) * lda + max(qa, pb), i22 = min(qa, qb) * lda + max(qa, qb);
                     const float a11 = A[i11], a12 = A[i12], a21 = A[i21], a22 = A[i22];
                     const float t11 = ca * a11 - sa * a21, t12 = ca * a12 - sa * a22;
                     const float t21 = sa * a11 + ca * a21, t22 = sa * a12 + ca * a22;
-                    const float n11 = t11 * cb - t12 * sb, n22 = t21 * sb + t22 * cb;
+                    A[i11] = t11 * cb - t12 * sb;
+                    A[i22] = t21 * sb + t22 * cb;
                     if (ka == kb) {
-                        A[i11] = n11;
                         A[i12] = 0.0f;  // (pa, qa): the rotation annihilates it
-                        A[i22] = n22;
                     } else {
-                        A[i11] = n11;
                         A[i12] = t11 * sb + t12 * cb;
                         A[i21] = t21 * cb - t22 * sb;
-                        A[i22] = n22;
                     }
-                } else {
+                } else if (kind[u] == 1) {
                     // V <- V J, one row of this CTA's slice and one pair.
-                    const int v = idx - nblk;
-                    const int row = v / nb, k = v - row * nb;
-                    const float4 rk = rot[k];
-                    const float c = rk.x, s = rk.y;
-                    if (s == 0.0f) continue;
+                    const float4 rk = rot[ib[u]];
+                    const float c = rk.x, sn = rk.y;
+                    if (sn == 0.0f) continue;
                     const int p = __float_as_int(rk.z), q = __float_as_int(rk.w);
-                    float *vr = V + row * lda;
+                    float *vr = V + ia[u] * lda;
                     const float x = vr[p], y = vr[q];
-                    vr[p] = c * x - s * y;
-                    vr[q] = s * x + c * y;
+                    vr[p] = c * x - sn * y;
+                    vr[q] = sn * x + c * y;
                 }
             }
-            __syncthreads();
         }
-        if (rotations == 0) break;
-        __syncthreads();
+        if (!__syncthreads_or(rotated)) break;
     }
     for (int idx = threadIdx.x; idx < vcnt * n; idx += kJacobiThreads) {
         const int r = idx / n, j = idx - r * n;
         if (v0 + r < n) X[(v0 + r) * ld + j] = (double)V[r * lda + j];
     }
+}
+
+// Items per thread for a Jacobi launch on blocks of at most n (the deflated
+// levels are smaller), and the matching kernel.
+int jacobi_items(int n) {
+    const int np = n + (n & 1), nb = np / 2;
+    const int vrows = (np + kJacobiCtas - 1) / kJacobiCtas;
+    return (int)ceil_div(nb * (nb + 1) / 2 + vrows * nb, kJacobiThreads);
 }
 
 // C (M x N) = op(A) (M x K) * Bm (K x N) (+ Cadd); all row-major with leading
@@ -426,12 +449,13 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
                           cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
     const int np = n + (n & 1);
-    const int nb = np / 2;
     const int vrows = (np + kJacobiCtas - 1) / kJacobiCtas;
-    const size_t smem = sizeof(float) * ((size_t)np * (np + 1) + (size_t)vrows * (np + 1)) +
-                        sizeof(ushort2) * (size_t)nb * (nb + 1) / 2;
-    if ((e = cudaFuncSetAttribute(jacobi_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
+    const size_t smem = sizeof(float) * ((size_t)np * (np + 1) + (size_t)vrows * (np + 1));
+    const int items = jacobi_items(n);
+    void (*jacobi)(const int *, int, const double *, int, double *) =
+        items <= 2 ? jacobi_f32_kernel<2> : items <= 3 ? jacobi_f32_kernel<3> : jacobi_f32_kernel<4>;
+    if (items > 4) return cudaErrorInvalidValue;
+    if ((e = cudaFuncSetAttribute(jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     set_identity_kernel<<<1, 256, 0, s>>>(n, ld, X, dims, kLevels, emax, kLevels * kRefineSteps);
     count_launch();
@@ -441,7 +465,7 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
         // C = Xa^T B Xa on the active columns (the first b columns of X).
         gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, nullptr, n, 0, n, ld, Bl, X, nullptr, T, nullptr);
         gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, nullptr, 0, 0, n, ld, X, T, nullptr, Cm, nullptr);
-        jacobi_f32_kernel<<<kJacobiCtas, kJacobiThreads, smem, s>>>(db, 0, Cm, ld, Z);
+        jacobi<<<kJacobiCtas, kJacobiThreads, smem, s>>>(db, 0, Cm, ld, Z);
         count_launch(3);
         for (int it = 0; it < kRefineSteps; ++it) {
             const unsigned long long *skip = it ? emax + lv * kRefineSteps + it - 1 : nullptr;
