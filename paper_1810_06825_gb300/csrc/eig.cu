@@ -38,11 +38,9 @@ constexpr int kRefineSteps = 5;
 constexpr int kLevels = 3;
 constexpr double kTau = 1.0e-3;  // bottom block: lambda < kTau * lambda_max of the block
 
-// A refinement step is skipped once the previous one moved X by less than
-// this (max |E_ij|): X is then converged to double precision.
-__device__ inline bool converged(const unsigned long long *emax) {
-    return emax && *emax <= (unsigned long long)__double_as_longlong(1.0e-15);
-}
+// Refinement stops after a step that moved X by less than this (max |E_ij|):
+// X is then converged to double precision.
+constexpr double kRefineDone = 1.0e-15;
 
 __device__ inline int dim_of(const int *dn, int n_static) { return dn ? *dn : n_static; }
 
@@ -216,16 +214,11 @@ int jacobi_items(int n) {
 template <bool TA>
 __global__ void gemm64_kernel(const int *dM, const int *dN, const int *dK, int Ms, int Ns, int Ks, int ld,
                               const double *__restrict__ A, const double *__restrict__ Bm,
-                              const double *__restrict__ Cadd, double *__restrict__ C,
-                              const unsigned long long *skip) {
+                              const double *__restrict__ Cadd, double *__restrict__ C) {
     const int M = dim_of(dM, Ms), N = dim_of(dN, Ns), K = dim_of(dK, Ks);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
     if (blockIdx.y * 16 >= M || blockIdx.x * 16 >= N) return;
-    if (converged(skip)) {  // refinement converged: C = Cadd (a copy) or nothing
-        if (Cadd && i < M && j < N) C[i * ld + j] = Cadd[i * ld + j];
-        return;
-    }
     __shared__ double As[16][17], Bs[16][17];
     double acc = 0.0;
     for (int k0 = 0; k0 < K; k0 += 16) {
@@ -258,41 +251,6 @@ __device__ inline double block_sum(double v, double *red) {
     return red[0];
 }
 
-// lambda_i = S_ii / (1 - R_ii) = S_ii / G_ii.
-__device__ inline double oa_lambda(const double *S, const double *Gm, int ld, int i) {
-    return S[i * ld + i] / Gm[i * ld + i];
-}
-
-constexpr int kOaRows = 4;  // rows of E per CTA
-
-// Partial sums of |S - diag(lambda)|_F^2, |C|_F^2 and |R|_F^2 over kOaRows rows.
-__global__ void oa_norms_kernel(const int *dn, int ld, const double *__restrict__ Cm, const double *__restrict__ Gm,
-                                const double *__restrict__ S, double *__restrict__ part,
-                                const unsigned long long *skip) {
-    const int n = *dn;
-    const int r0 = blockIdx.x * kOaRows;
-    if (n < 1 || r0 >= n || converged(skip)) return;
-    __shared__ double red[32];
-    double sS = 0.0, sB = 0.0, sR = 0.0;
-    const int r1 = min(n, r0 + kOaRows);
-    for (int idx = threadIdx.x; idx < (r1 - r0) * n; idx += blockDim.x) {
-        const int i = r0 + idx / n, j = idx % n;
-        const double rij = (i == j ? 1.0 : 0.0) - Gm[i * ld + j];
-        const double d = (i == j) ? S[i * ld + j] - oa_lambda(S, Gm, ld, i) : S[i * ld + j];
-        const double b = Cm[i * ld + j];
-        sS += d * d;
-        sB += b * b;
-        sR += rij * rij;
-    }
-    sS = block_sum(sS, red);
-    sB = block_sum(sB, red);
-    sR = block_sum(sR, red);
-    if (threadIdx.x == 0) {
-        part[3 * blockIdx.x + 0] = sS;
-        part[3 * blockIdx.x + 1] = sB;
-        part[3 * blockIdx.x + 2] = sR;
-    }
-}
 
 // 1/g to double accuracy: float reciprocal, one Newton step in double.
 __device__ inline double recip(double g) {
@@ -303,55 +261,142 @@ __device__ inline double recip(double g) {
     return fma(r0, e, r0);
 }
 
-// E for kOaRows rows (see the header): pairs separated by more than delta are
-// rotated to first order; pairs closer than delta, and pairs whose eigenvalues
-// both lie below kTau * max|lambda|, are only orthogonalized (E_ij = R_ij / 2):
-// float cannot separate the latter at this level, a first-order rotation
-// between them would be unreliable, and the next deflation level resolves them.
-__global__ void oa_e_kernel(const int *dn, int ld, const double *__restrict__ Gm, const double *__restrict__ S,
-                            const double *__restrict__ part, double *__restrict__ E, double *__restrict__ lam,
-                            const unsigned long long *skip, unsigned long long *emax) {
-    const int n = *dn;
-    const int r0 = blockIdx.x * kOaRows;
-    if (n < 1 || r0 >= n) return;
-    if (converged(skip)) {  // keep the converged mark for the following steps
-        if (blockIdx.x == 0 && threadIdx.x == 0) *emax = 0ull;
-        return;
+// One 16 x 16 tile (ti, tj) of C = op(A) Bm (+ Cadd) for b x b blocks with
+// leading dimension ld; op(A) = A^T when TA.  Operands written by other CTAs
+// of the same launch are read past L1 (__ldcg).
+template <bool TA>
+__device__ void tile_gemm(int b, int ld, int ti, int tj, const double *A, const double *Bm, const double *Cadd,
+                          double *C, double (*As)[17], double (*Bs)[17]) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i = ti * 16 + ty, j = tj * 16 + tx;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < b; k0 += 16) {
+        const int ka = k0 + tx, kb = k0 + ty;
+        if (TA)
+            As[ty][tx] = (i < b && ka < b) ? __ldcg(A + ka * ld + i) : 0.0;
+        else
+            As[ty][tx] = (i < b && ka < b) ? __ldcg(A + i * ld + ka) : 0.0;
+        Bs[ty][tx] = (kb < b && j < b) ? __ldcg(Bm + kb * ld + j) : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc = fma(As[ty][k], Bs[k][tx], acc);
+        __syncthreads();
     }
-    __shared__ unsigned long long emax_s;
-    if (threadIdx.x == 0) emax_s = 0ull;
+    if (i < b && j < b) C[i * ld + j] = acc + (Cadd ? __ldcg(Cadd + i * ld + j) : 0.0);
+}
+
+// The Ogita-Aishima refinement of one level (see the header), all steps in
+// one cooperative launch: every step is five phases separated by grid
+// barriers -- (1) G = Z^T Z and T = C Z, (2) S = Z^T T, (3) partial sums of
+// |S - diag(lambda)|_F^2, |C|_F^2, |R|_F^2 over this CTA's rows, (4) lambda,
+// delta and E on this CTA's rows, (5) Z' = Z + Z E -- and the loop ends after
+// kRefineSteps steps or after a step whose max |E_ij| was below kRefineDone.
+// E: pairs separated by more than delta are rotated to first order; pairs
+// closer than delta, and pairs whose eigenvalues both lie below
+// kTau * max|lambda|, are only orthogonalized (E_ij = R_ij / 2): float cannot
+// separate the latter at this level, a first-order rotation between them
+// would be unreliable, and the next deflation level resolves them.  The
+// refined vectors end in Z, the eigenvalue estimates in lam.  Tiles of the
+// b x b products go round-robin over the CTAs, rows of E in contiguous runs.
+__global__ void __launch_bounds__(256)
+oa_refine_kernel(const int *dn, int ld, const double *__restrict__ Cm, double *Z, double *Z2, double *Gm, double *T,
+                 double *S, double *E, double *part, double *lam, unsigned long long *emax, GridBarrier *bar,
+                 int *status, long long limit_cycles) {
+    const int b = *dn;
+    if (b < 1) return;
+    __shared__ double As[16][17], Bs[16][17];
+    __shared__ double red[32];
     __shared__ double lam_s[FRPCA_MAX_L];
     __shared__ double s_delta, s_low;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) lam_s[i] = oa_lambda(S, Gm, ld, i);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sS = 0.0, sB = 0.0, sR = 0.0, top = 0.0;
-        const int nparts = (n + kOaRows - 1) / kOaRows;
-        for (int p = 0; p < nparts; ++p) {
-            sS += part[3 * p];
-            sB += part[3 * p + 1];
-            sR += part[3 * p + 2];
+    __shared__ unsigned long long emax_s;
+    const int G = gridDim.x;
+    const int tb = (b + 15) / 16, ntiles = tb * tb;
+    const int rows = (b + G - 1) / G;
+    const int r0 = min(b, (int)blockIdx.x * rows), r1 = min(b, r0 + rows);
+    double *Zc = Z, *Zn = Z2;
+    for (int it = 0; it < kRefineSteps; ++it) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) emax[it] = 0ull;
+        // (1) G = Z^T Z, T = C Z
+        for (int t = blockIdx.x; t < ntiles; t += G) {
+            tile_gemm<true>(b, ld, t / tb, t % tb, Zc, Zc, nullptr, Gm, As, Bs);
+            tile_gemm<false>(b, ld, t / tb, t % tb, Cm, Zc, nullptr, T, As, Bs);
         }
-        for (int i = 0; i < n; ++i) top = fmax(top, fabs(lam_s[i]));
-        s_delta = 2.0 * (sqrt(sS) + sqrt(sB) * sqrt(sR));
-        s_low = kTau * top;
+        if (!grid_barrier(bar, G, status, limit_cycles)) return;
+        // (2) S = Z^T C Z
+        for (int t = blockIdx.x; t < ntiles; t += G) tile_gemm<true>(b, ld, t / tb, t % tb, Zc, T, nullptr, S, As, Bs);
+        if (!grid_barrier(bar, G, status, limit_cycles)) return;
+        // (3) partial norms over rows r0 .. r1 - 1
+        {
+            double sS = 0.0, sB = 0.0, sR = 0.0;
+            for (int idx = threadIdx.x; idx < (r1 - r0) * b; idx += blockDim.x) {
+                const int i = r0 + idx / b, j = idx % b;
+                const double g = __ldcg(Gm + i * ld + j), sij = __ldcg(S + i * ld + j);
+                const double rij = (i == j ? 1.0 : 0.0) - g;
+                const double d = (i == j) ? sij - sij / g : sij;
+                const double c = Cm[i * ld + j];
+                sS += d * d;
+                sB += c * c;
+                sR += rij * rij;
+            }
+            sS = block_sum(sS, red);
+            sB = block_sum(sB, red);
+            sR = block_sum(sR, red);
+            if (threadIdx.x == 0) {
+                part[3 * blockIdx.x + 0] = sS;
+                part[3 * blockIdx.x + 1] = sB;
+                part[3 * blockIdx.x + 2] = sR;
+            }
+        }
+        if (!grid_barrier(bar, G, status, limit_cycles)) return;
+        // (4) lambda_i = S_ii / (1 - R_ii) = S_ii / G_ii, delta, E on rows r0 .. r1 - 1
+        for (int i = threadIdx.x; i < b; i += blockDim.x) lam_s[i] = __ldcg(S + i * ld + i) / __ldcg(Gm + i * ld + i);
+        if (threadIdx.x == 0) emax_s = 0ull;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sS = 0.0, sB = 0.0, sR = 0.0, top = 0.0;
+            for (int p = 0; p < G; ++p) {
+                sS += __ldcg(part + 3 * p);
+                sB += __ldcg(part + 3 * p + 1);
+                sR += __ldcg(part + 3 * p + 2);
+            }
+            for (int i = 0; i < b; ++i) top = fmax(top, fabs(lam_s[i]));
+            s_delta = 2.0 * (sqrt(sS) + sqrt(sB) * sqrt(sR));
+            s_low = kTau * top;
+        }
+        __syncthreads();
+        {
+            const double delta = s_delta, low = s_low;
+            for (int idx = threadIdx.x; idx < (r1 - r0) * b; idx += blockDim.x) {
+                const int i = r0 + idx / b, j = idx % b;
+                const double rij = (i == j ? 1.0 : 0.0) - __ldcg(Gm + i * ld + j);
+                const double gap = lam_s[j] - lam_s[i];
+                const bool both_low = fabs(lam_s[i]) < low && fabs(lam_s[j]) < low;
+                const double e = (fabs(gap) > delta && !both_low)
+                                     ? fma(lam_s[j], rij, __ldcg(S + i * ld + j)) * recip(gap)
+                                     : 0.5 * rij;
+                E[i * ld + j] = e;
+                atomicMax(&emax_s, (unsigned long long)__double_as_longlong(e) & 0x7fffffffffffffffull);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && r1 > r0) atomicMax(emax + it, emax_s);
+            if (blockIdx.x == 0)
+                for (int i = threadIdx.x; i < b; i += blockDim.x) lam[i] = lam_s[i];
+        }
+        if (!grid_barrier(bar, G, status, limit_cycles)) return;
+        // (5) Z' = Z + Z E
+        for (int t = blockIdx.x; t < ntiles; t += G) tile_gemm<false>(b, ld, t / tb, t % tb, Zc, E, Zc, Zn, As, Bs);
+        if (!grid_barrier(bar, G, status, limit_cycles)) return;
+        double *tmp = Zc;
+        Zc = Zn;
+        Zn = tmp;
+        const unsigned long long m = __ldcg(emax + it);
+        if (m <= (unsigned long long)__double_as_longlong(kRefineDone)) break;
     }
-    __syncthreads();
-    const double delta = s_delta, low = s_low;
-    const int r1 = min(n, r0 + kOaRows);
-    for (int idx = threadIdx.x; idx < (r1 - r0) * n; idx += blockDim.x) {
-        const int i = r0 + idx / n, j = idx % n;
-        const double rij = (i == j ? 1.0 : 0.0) - Gm[i * ld + j];
-        const double gap = lam_s[j] - lam_s[i];
-        const bool both_low = fabs(lam_s[i]) < low && fabs(lam_s[j]) < low;
-        const double e = (fabs(gap) > delta && !both_low) ? fma(lam_s[j], rij, S[i * ld + j]) * recip(gap) : 0.5 * rij;
-        E[i * ld + j] = e;
-        atomicMax(&emax_s, (unsigned long long)__double_as_longlong(e) & 0x7fffffffffffffffull);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) atomicMax(emax, emax_s);
-    if (blockIdx.x == 0)
-        for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = lam_s[i];
+    if (Zc != Z)  // leave the result in Z
+        for (int t = blockIdx.x; t < ntiles; t += G) {
+            const int i = (t / tb) * 16 + (threadIdx.x >> 4), j = (t % tb) * 16 + (threadIdx.x & 15);
+            if (i < b && j < b) Z[i * ld + j] = __ldcg(Zc + i * ld + j);
+        }
 }
 
 // After a level: sort the active block ascending by lambda (its columns of X,
@@ -430,7 +475,7 @@ __global__ void copy_out_kernel(int n, int ld, const double *__restrict__ lam_al
 
 size_t eig_workspace_bytes(int n) {
     const size_t ld = FRPCA_MAX_L;
-    return sizeof(double) * (10 * ld * ld + 5 * ld) + 64 * sizeof(int) + 8 * kLevels * kRefineSteps + 256;
+    return sizeof(double) * (10 * ld * ld + 5 * ld) + 64 * sizeof(int) + 8 * kLevels * kRefineSteps + 512;
 }
 
 cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, int *d_status, cudaStream_t s) {
@@ -443,6 +488,7 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
     double *Pn = lam_all + ld;  // norm partials, 3 per row group
     int *dims = (int *)(Pn + 3 * ld);
     unsigned long long *emax = (unsigned long long *)(dims + 64);  // max |E| per level and step
+    GridBarrier *bar = (GridBarrier *)(emax + round_up(kLevels * kRefineSteps, 32));
     cudaError_t e;
     // B copied to leading dimension ld.
     e = cudaMemcpy2DAsync(Bl, sizeof(double) * ld, B, sizeof(double) * n, sizeof(double) * n, n,
@@ -457,30 +503,38 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
     if (items > 4) return cudaErrorInvalidValue;
     if ((e = cudaFuncSetAttribute(jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oa_refine_kernel, 256, 0)) != cudaSuccess)
+        return e;
+    const int refine_ctas = std::max(1, sms * per_sm);
     set_identity_kernel<<<1, 256, 0, s>>>(n, ld, X, dims, kLevels, emax, kLevels * kRefineSteps);
     count_launch();
     const dim3 g2((n + 15) / 16, (n + 15) / 16);
     for (int lv = 0; lv < kLevels; ++lv) {
         const int *db = dims + lv;  // active block size (0: nothing left)
         // C = Xa^T B Xa on the active columns (the first b columns of X).
-        gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, nullptr, n, 0, n, ld, Bl, X, nullptr, T, nullptr);
-        gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, nullptr, 0, 0, n, ld, X, T, nullptr, Cm, nullptr);
+        gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, nullptr, n, 0, n, ld, Bl, X, nullptr, T);
+        gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, nullptr, 0, 0, n, ld, X, T, nullptr, Cm);
         jacobi<<<kJacobiCtas, kJacobiThreads, smem, s>>>(db, 0, Cm, ld, Z);
         count_launch(3);
-        for (int it = 0; it < kRefineSteps; ++it) {
-            const unsigned long long *skip = it ? emax + lv * kRefineSteps + it - 1 : nullptr;
-            unsigned long long *em = emax + lv * kRefineSteps + it;
-            gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Z, Z, nullptr, G, skip);   // Z^T Z
-            gemm64_kernel<false><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Cm, Z, nullptr, T, skip); // C Z
-            gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Z, T, nullptr, S, skip);   // Z^T C Z
-            oa_norms_kernel<<<(n + kOaRows - 1) / kOaRows, 256, 0, s>>>(db, ld, Cm, G, S, Pn, skip);
-            oa_e_kernel<<<(n + kOaRows - 1) / kOaRows, 256, 0, s>>>(db, ld, G, S, Pn, E, lam_b, skip, em);
-            gemm64_kernel<false><<<g2, 256, 0, s>>>(db, db, db, 0, 0, 0, ld, Z, E, Z, Z2, skip);       // Z + Z E
-            count_launch(6);
-            std::swap(Z, Z2);
+        {
+            if ((e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s)) != cudaSuccess) return e;
+            const int *dn = db;
+            int ldv = ld;
+            const double *cm = Cm;
+            unsigned long long *em = emax + lv * kRefineSteps;
+            long long lim = kBarrierLimitCycles;
+            void *args[] = {(void *)&dn, &ldv, (void *)&cm, &Z, &Z2, &G, &T, &S, &E, &Pn, &lam_b, &em, &bar,
+                            &d_status, &lim};
+            const int grid = std::min(refine_ctas, (int)((n + 15) / 16) * (int)((n + 15) / 16));
+            e = cudaLaunchCooperativeKernel((const void *)oa_refine_kernel, grid, 256, args, 0, s);
+            if (e != cudaSuccess) return e;
+            count_launch();
         }
         // Xa <- Xa Z, then sort the active block and choose the next one.
-        gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, db, n, 0, 0, ld, X, Z, nullptr, Xn, nullptr);
+        gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, db, n, 0, 0, ld, X, Z, nullptr, Xn);
         level_split_kernel<<<1, 256, 0, s>>>(n, ld, db, lam_b, Xn, X, lam_all, dims + lv + 1, d_status);
         count_launch(2);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
