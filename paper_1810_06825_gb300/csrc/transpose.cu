@@ -5,19 +5,26 @@
 // it once.  The transpose is a stable sort of the entries by column index:
 // entries start in row-major order, so a stable sort leaves every column's
 // rows ascending, and the result is unique (bit-exact whatever the schedule).
-// The sort is an LSD radix sort over 8-bit digits of the column index; each
-// pass is a stable counting sort in which a warp owns a tile of 4096 entries,
-// ranks equal digits with __match_any_sync inside 32-entry chunks, and takes
-// its per-digit base from a digit-major scan of all tiles' histograms.
+// The sort is an LSD radix sort over 8-bit digits of the column index that
+// carries each entry's row and value along.  Each pass is a stable counting
+// sort over CTA tiles of 8192 entries: a tile's digit counts come from a
+// digit-major scan of all tiles' histograms; inside the tile, warps rank equal
+// digits with __match_any_sync in entry order, the tile is reordered by digit
+// in shared memory, and each digit's run is written out contiguously.  The
+// row pointers of A^T are read off the sorted column indices.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
 namespace frpca {
 namespace {
 
-constexpr int kWarpsPerBlock = 8;
-constexpr int kTileItems = 4096;  // entries per warp-tile
 constexpr int kRadix = 256;
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kChunks = 16;                        // 32-entry chunks per warp
+constexpr int kSortTile = kSortWarps * kChunks * 32;  // 8192 entries per CTA tile
 
 // ------------------------------------------------------------------ scan
 constexpr int kScanThreads = 1024;
@@ -140,76 +147,124 @@ __global__ void validate_kernel(int64_t m, int64_t n, int64_t nnz, const int64_t
 }
 
 // ------------------------------------------------------------------ radix passes
-__device__ inline int digit_of(uint32_t key, int shift, bool valid) {
-    return valid ? (int)((key >> shift) & (kRadix - 1)) : kRadix;
+__device__ inline int digit_of(uint32_t key, int shift) { return (int)((key >> shift) & (kRadix - 1)); }
+
+// Entry e of tile t, chunk c of warp w, lane: tiles are contiguous ranges and
+// so are a warp's chunks, so ranks follow entry order.
+__device__ inline int64_t entry_of(int64_t t, int warp, int c, int lane) {
+    return t * kSortTile + (int64_t)(warp * kChunks + c) * 32 + lane;
 }
 
-// Pass input: keys (nullptr -> read from colidx) and perm (nullptr -> identity).
-__global__ void radix_hist_kernel(const uint32_t *__restrict__ keys, int64_t nnz, int shift, int64_t ntiles,
-                                  int32_t *__restrict__ counts) {
-    __shared__ int32_t cnt[kWarpsPerBlock][kRadix];
+// counts[d * ntiles + t] = number of entries of tile t with digit d.
+__global__ void __launch_bounds__(kSortThreads)
+radix_hist_kernel(const uint32_t *__restrict__ keys, int64_t nnz, int shift, int64_t ntiles,
+                  int32_t *__restrict__ counts) {
+    __shared__ int32_t cnt[kRadix];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-    for (int d = lane; d < kRadix; d += 32) cnt[warp][d] = 0;
-    __syncwarp();
-    if (t >= ntiles) return;
-    const int64_t t0 = t * kTileItems;
-    for (int64_t c = 0; c < kTileItems; c += 32) {
-        const int64_t e = t0 + c + lane;
+    const int64_t t = blockIdx.x;
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) cnt[d] = 0;
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < kChunks; ++c) {
+        const int64_t e = entry_of(t, warp, c, lane);
         const bool valid = e < nnz;
-        const int d = digit_of(valid ? keys[e] : 0u, shift, valid);
+        const int d = valid ? digit_of(keys[e], shift) : kRadix;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int leader = 31 - __clz(peers);
-        if (valid && lane == leader) cnt[warp][d] += __popc(peers);
-        __syncwarp();
-        if (t0 + c + 32 >= nnz) break;
+        if (valid && lane == 31 - __clz(peers)) atomicAdd(&cnt[d], __popc(peers));
     }
-    __syncwarp();
-    for (int d = lane; d < kRadix; d += 32) counts[(int64_t)d * ntiles + t] = cnt[warp][d];
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) counts[(int64_t)d * ntiles + t] = cnt[d];
 }
 
-__global__ void radix_scatter_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ perm,
-                                     int64_t nnz, int shift, int64_t ntiles, const int64_t *__restrict__ offs,
-                                     uint32_t *__restrict__ keys_out, int32_t *__restrict__ perm_out) {
-    __shared__ int64_t base[kWarpsPerBlock][kRadix];
+// One stable counting-sort pass of a tile: (key, row, value) go to
+// offs[d * ntiles + t] + (rank of the entry among the tile's entries of digit d).
+template <typename T>
+__global__ void __launch_bounds__(kSortThreads)
+radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const int32_t *__restrict__ rows_in,
+                     const T *__restrict__ vals_in, int64_t nnz, int shift, int64_t ntiles,
+                     const int64_t *__restrict__ offs, uint32_t *__restrict__ keys_out,
+                     int32_t *__restrict__ rows_out, T *__restrict__ vals_out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *sval = reinterpret_cast<T *>(smem);
+    uint32_t *skey = reinterpret_cast<uint32_t *>(sval + kSortTile);
+    int32_t *srow = reinterpret_cast<int32_t *>(skey + kSortTile);
+    int32_t *wrun = srow + kSortTile;        // [kSortWarps][kRadix]: counts, then running positions
+    int32_t *lstart = wrun + kSortWarps * kRadix;  // first local position of each digit
+    __shared__ int64_t wt[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t t = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-    if (t >= ntiles) return;
-    for (int d = lane; d < kRadix; d += 32) base[warp][d] = offs[(int64_t)d * ntiles + t];
-    __syncwarp();
     const unsigned lt = (1u << lane) - 1u;
-    const int64_t t0 = t * kTileItems;
-    for (int64_t c = 0; c < kTileItems; c += 32) {
-        const int64_t e = t0 + c + lane;
+    const int64_t t = blockIdx.x;
+    const int count = (int)min((int64_t)kSortTile, nnz - t * kSortTile);
+
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) wrun[i] = 0;
+    __syncthreads();
+    uint32_t key[kChunks];
+    int dig[kChunks];
+    unsigned peer[kChunks];
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) {
+        const int64_t e = entry_of(t, warp, c, lane);
         const bool valid = e < nnz;
-        const uint32_t key = valid ? keys[e] : 0u;
-        const int32_t p = valid ? (perm ? perm[e] : (int32_t)e) : 0;
-        const int d = digit_of(key, shift, valid);
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int leader = 31 - __clz(peers);
-        if (valid) {
-            const int64_t pos = base[warp][d] + __popc(peers & lt);
-            if (keys_out) keys_out[pos] = key;
-            perm_out[pos] = p;
+        key[c] = valid ? keys_in[e] : 0u;
+        dig[c] = valid ? digit_of(key[c], shift) : kRadix;
+        peer[c] = __match_any_sync(0xffffffffu, dig[c]);
+        if (valid && lane == 31 - __clz(peer[c])) wrun[warp * kRadix + dig[c]] += __popc(peer[c]);
+        __syncwarp();
+    }
+    __syncthreads();
+    // Digit d: warps' exclusive offsets within the digit, then the tile-local
+    // start of the digit (exclusive scan of the digit totals).
+    int64_t total = 0;
+    if (threadIdx.x < kRadix) {
+        const int d = threadIdx.x;
+        for (int w = 0; w < kSortWarps; ++w) {
+            const int c = wrun[w * kRadix + d];
+            wrun[w * kRadix + d] = (int32_t)total;
+            total += c;
+        }
+    }
+    int64_t block_total;
+    const int64_t start = block_exclusive_scan<int64_t>(total, wt, block_total);
+    if (threadIdx.x < kRadix) {
+        lstart[threadIdx.x] = (int32_t)start;
+        for (int w = 0; w < kSortWarps; ++w) wrun[w * kRadix + threadIdx.x] += (int32_t)start;
+    }
+    __syncthreads();
+    // Reorder the tile by digit in shared memory (stable: chunks in order,
+    // lanes ranked within a chunk).
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) {
+        const int64_t e = entry_of(t, warp, c, lane);
+        if (e < nnz) {
+            const int pos = wrun[warp * kRadix + dig[c]] + __popc(peer[c] & lt);
+            skey[pos] = key[c];
+            srow[pos] = rows_in[e];
+            sval[pos] = vals_in[e];
         }
         __syncwarp();
-        if (valid && lane == leader) base[warp][d] += __popc(peers);
+        if (e < nnz && lane == 31 - __clz(peer[c])) wrun[warp * kRadix + dig[c]] += __popc(peer[c]);
         __syncwarp();
-        if (t0 + c + 32 >= nnz) break;
+    }
+    __syncthreads();
+    // Each digit's run goes to consecutive global positions.
+    for (int i = threadIdx.x; i < count; i += kSortThreads) {
+        const uint32_t k = skey[i];
+        const int d = digit_of(k, shift);
+        const int64_t g = offs[(int64_t)d * ntiles + t] + (i - lstart[d]);
+        if (keys_out) keys_out[g] = k;
+        rows_out[g] = srow[i];
+        vals_out[g] = sval[i];
     }
 }
 
-// Column histogram.  Hot columns (a power-law matrix can put ~m entries in one
-// column) would serialize plain atomics, so equal columns within a warp are
-// combined first and one lane adds their count.
-__global__ void column_count_kernel(const int32_t *__restrict__ colidx, int64_t nnz, int32_t *__restrict__ cnt) {
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < nnz; base += stride) {
-        const int64_t e = base + lane;
-        const int c = e < nnz ? colidx[e] : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, c);
-        if (c >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[c], __popc(peers));
+// Row pointers of A^T from the sorted column indices: column j starts at the
+// first entry whose column is >= j (rowptrT[n] = nnz).
+__global__ void rowptr_from_sorted_kernel(const uint32_t *__restrict__ keys, int64_t nnz, int64_t n,
+                                          int64_t *__restrict__ rowptrT) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cur = p < nnz ? (int64_t)keys[p] : n;
+        const int64_t prev = p > 0 ? (int64_t)keys[p - 1] : -1;
+        for (int64_t j = prev + 1; j <= cur; ++j) rowptrT[j] = p;
     }
 }
 
@@ -218,17 +273,6 @@ __global__ void row_of_entry_kernel(int64_t m, const int64_t *__restrict__ rowpt
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= m) return;
     for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) row_of[p] = (int32_t)i;
-}
-
-template <typename T>
-__global__ void gather_transpose_kernel(int64_t nnz, const int32_t *__restrict__ perm,
-                                        const int32_t *__restrict__ row_of, const T *__restrict__ vals,
-                                        int32_t *__restrict__ colT, T *__restrict__ valT) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t e = perm[p];
-        colT[p] = row_of[e];
-        valT[p] = vals[e];
-    }
 }
 
 template <typename TI, typename TO>
@@ -271,64 +315,73 @@ cudaError_t launch_convert(const void *in, frpca_dtype din, void *out, frpca_dty
     return cudaGetLastError();
 }
 
-cudaError_t csr_transpose(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, DevBuf &scan_scratch,
-                          cudaStream_t s) {
+template <typename T>
+cudaError_t transpose_typed(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, DevBuf &scan_scratch,
+                            cudaStream_t s) {
     const int64_t nnz = A.nnz, n = A.cols;
     cudaError_t e;
-    // rowptr of A^T from column counts.
-    const int64_t ntiles = ceil_div(nnz > 0 ? nnz : 1, kTileItems);
-    const size_t cnt_bytes = sizeof(int32_t) * (size_t)round_up(n > kRadix * ntiles ? n : kRadix * ntiles, 64);
+    if (nnz == 0) {
+        rowptr_from_sorted_kernel<<<1, 256, 0, s>>>(nullptr, 0, n, AT.rowptr);
+        count_launch();
+        return cudaGetLastError();
+    }
+    const int64_t ntiles = ceil_div(nnz, kSortTile);
+    const size_t cnt_bytes = sizeof(int32_t) * (size_t)round_up(kRadix * ntiles, 64);
     const size_t off_bytes = sizeof(int64_t) * (size_t)round_up(kRadix * ntiles + 1, 64);
-    const size_t arr_bytes = sizeof(int32_t) * (size_t)round_up(nnz > 0 ? nnz : 1, 64);
-    const size_t need = cnt_bytes + off_bytes + 5 * arr_bytes;
+    const size_t i32_bytes = sizeof(int32_t) * (size_t)round_up(nnz, 64);
+    const size_t val_bytes = sizeof(T) * (size_t)round_up(nnz, 64);
+    const size_t need = cnt_bytes + off_bytes + 5 * i32_bytes + 2 * val_bytes;
     if ((e = scratch.ensure(need)) != cudaSuccess) return e;
     char *p = (char *)scratch.ptr;
     int32_t *counts = (int32_t *)p; p += cnt_bytes;
     int64_t *offs = (int64_t *)p; p += off_bytes;
-    uint32_t *keys0 = (uint32_t *)p; p += arr_bytes;
-    uint32_t *keys1 = (uint32_t *)p; p += arr_bytes;
-    int32_t *perm0 = (int32_t *)p; p += arr_bytes;
-    int32_t *perm1 = (int32_t *)p; p += arr_bytes;
-    int32_t *row_of = (int32_t *)p; p += arr_bytes;
+    uint32_t *keys[2] = {(uint32_t *)p, (uint32_t *)(p + i32_bytes)}; p += 2 * i32_bytes;
+    int32_t *rows[2] = {(int32_t *)p, (int32_t *)(p + i32_bytes)}; p += 2 * i32_bytes;
+    int32_t *row_of = (int32_t *)p; p += i32_bytes;
+    T *vals[2] = {(T *)p, (T *)(p + val_bytes)};
 
-    if ((e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n, s)) != cudaSuccess) return e;
-    if (nnz > 0) {
-        column_count_kernel<<<grid_for(nnz, 256), 256, 0, s>>>(A.colidx, nnz, counts); count_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if ((e = exclusive_scan<int32_t>(counts, AT.rowptr, n, scan_scratch, s)) != cudaSuccess) return e;
-    if (nnz == 0) return cudaSuccess;
+    row_of_entry_kernel<<<(unsigned)ceil_div(A.rows * 32, 256), 256, 0, s>>>(A.rows, A.rowptr, row_of);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
     int bits = 1;
     while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
     const int passes = (bits + 7) / 8;
+    const size_t smem = (size_t)kSortTile * (sizeof(T) + 8) + sizeof(int32_t) * (kSortWarps + 1) * kRadix;
+    if ((e = cudaFuncSetAttribute(radix_scatter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
     const uint32_t *kin = (const uint32_t *)A.colidx;
-    const int32_t *pin = nullptr;
-    const unsigned blocks = (unsigned)ceil_div(ntiles, kWarpsPerBlock);
+    const int32_t *rin = row_of;
+    const T *vin = (const T *)A.vals;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
-        uint32_t *kout = (pass % 2 == 0) ? keys0 : keys1;
-        int32_t *pout = (pass % 2 == 0) ? perm0 : perm1;
-        radix_hist_kernel<<<blocks, 32 * kWarpsPerBlock, 0, s>>>(kin, nnz, shift, ntiles, counts); count_launch();
+        const bool last = pass + 1 == passes;
+        uint32_t *kout = keys[pass & 1];
+        int32_t *rout = last ? AT.colidx : rows[pass & 1];
+        T *vout = last ? (T *)AT.vals : vals[pass & 1];
+        radix_hist_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, nnz, shift, ntiles, counts);
+        count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = exclusive_scan<int32_t>(counts, offs, kRadix * ntiles, scan_scratch, s)) != cudaSuccess) return e;
-        radix_scatter_kernel<<<blocks, 32 * kWarpsPerBlock, 0, s>>>(
-            kin, pin, nnz, shift, ntiles, offs, (pass + 1 < passes) ? kout : nullptr, pout); count_launch();
+        radix_scatter_kernel<T><<<(unsigned)ntiles, kSortThreads, smem, s>>>(kin, rin, vin, nnz, shift, ntiles, offs,
+                                                                             kout, rout, vout);
+        count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         kin = kout;
-        pin = pout;
+        rin = rout;
+        vin = vout;
     }
-    row_of_entry_kernel<<<(unsigned)ceil_div(A.rows * 32, 256), 256, 0, s>>>(A.rows, A.rowptr, row_of); count_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (A.dtype == FRPCA_F32) {
-        gather_transpose_kernel<float><<<grid_for(nnz, 256), 256, 0, s>>>(
-            nnz, pin, row_of, (const float *)A.vals, AT.colidx, (float *)AT.vals);
-    } else {
-        gather_transpose_kernel<double><<<grid_for(nnz, 256), 256, 0, s>>>(
-            nnz, pin, row_of, (const double *)A.vals, AT.colidx, (double *)AT.vals);
-    }
+    rowptr_from_sorted_kernel<<<(unsigned)std::min<int64_t>(ceil_div(nnz + 1, 256), 1 << 20), 256, 0, s>>>(
+        kin, nnz, n, AT.rowptr);
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t csr_transpose(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, DevBuf &scan_scratch,
+                          cudaStream_t s) {
+    if (A.dtype == FRPCA_F32) return transpose_typed<float>(A, AT, scratch, scan_scratch, s);
+    return transpose_typed<double>(A, AT, scratch, scan_scratch, s);
 }
 
 cudaError_t DevBuf::ensure(size_t need) {
