@@ -5,7 +5,8 @@
 // Y = M W with M tall (R x l) and W small (l x kout): a persistent grid walks
 // row tiles; each block keeps W (converted to the block's type) in shared
 // memory for all its tiles and stages one tile of M rows at a time, so M is
-// read once and may be overwritten in place by Y.
+// read once and may be overwritten in place by Y.  Each thread computes 4 x 4
+// output blocks.
 #include <algorithm>
 
 #include "common.cuh"
@@ -41,47 +42,72 @@ __global__ void make_w_kernel(int l, int kout, const double *__restrict__ w, con
     }
 }
 
+// Four consecutive entries of a shared-memory row of W (16-byte aligned).
+__device__ inline void load4(const float *p, float &a, float &b, float &c, float &d) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ inline void load4(const double *p, double &a, double &b, double &c, double &d) {
+    const double2 u = *reinterpret_cast<const double2 *>(p), v = *reinterpret_cast<const double2 *>(p + 2);
+    a = u.x; b = u.y; c = v.x; d = v.y;
+}
+
+// Each thread computes 4 x 4 blocks of a tile's output: per inner index a,
+// four M values (broadcast within the warp) and one 16-byte row piece of W
+// feed 16 FMAs.
 template <typename T>
 __global__ void __launch_bounds__(kApplyThreads)
 apply_kernel(int64_t R, int l, const T *M, int64_t ldm, const T *__restrict__ W, int kout, T *Y, int64_t ldy,
              int tile_rows) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int kp = (int)round_up(kout, 4);
+    const int lms = l + 1;                          // odd stride of the staged rows
     T *Ws = reinterpret_cast<T *>(smem_raw);       // l x kp
-    T *Ms = Ws + (size_t)l * kp;                    // tile_rows x l
+    T *Ms = Ws + (size_t)l * kp;                    // tile_rows x lms
     for (int idx = threadIdx.x; idx < l * kp; idx += kApplyThreads) {
         const int a = idx / kp, j = idx - a * kp;
         Ws[idx] = (j < kout) ? W[a * kout + j] : T(0);
     }
-    const int groups = kp / 4;
+    const int cgroups = kp / 4;
     const int64_t ntile = ceil_div(R, tile_rows);
     for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x) {
         const int64_t row0 = t * tile_rows;
         const int rows = (int)std::min<int64_t>(tile_rows, R - row0);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < rows * l; idx += kApplyThreads) {
+        for (int idx = threadIdx.x; idx < tile_rows * l; idx += kApplyThreads) {
             const int r = idx / l, a = idx - r * l;
-            Ms[idx] = M[(row0 + r) * ldm + a];
+            Ms[r * lms + a] = r < rows ? M[(row0 + r) * ldm + a] : T(0);
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < rows * groups; idx += kApplyThreads) {
-            const int r = idx / groups, g = idx - r * groups;
-            const T *mr = Ms + r * l;
-            T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+        const int rgroups = (rows + 3) / 4;
+        for (int blk = threadIdx.x; blk < rgroups * cgroups; blk += kApplyThreads) {
+            const int rg = blk / cgroups, cg = blk - rg * cgroups;
+            const T *m0 = Ms + (4 * rg) * lms;
+            T acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+#pragma unroll 4
             for (int a = 0; a < l; ++a) {
-                const T m = mr[a];
-                const T *wr = Ws + a * kp + 4 * g;
-                acc0 = fma(m, wr[0], acc0);
-                acc1 = fma(m, wr[1], acc1);
-                acc2 = fma(m, wr[2], acc2);
-                acc3 = fma(m, wr[3], acc3);
+                T w[4];
+                load4(Ws + a * kp + 4 * cg, w[0], w[1], w[2], w[3]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const T m = m0[i * lms + a];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(m, w[j], acc[i][j]);
+                }
             }
-            T *yr = Y + (row0 + r) * ldy + 4 * g;
-            const int j0 = 4 * g;
-            if (j0 + 0 < kout) yr[0] = acc0;
-            if (j0 + 1 < kout) yr[1] = acc1;
-            if (j0 + 2 < kout) yr[2] = acc2;
-            if (j0 + 3 < kout) yr[3] = acc3;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = 4 * rg + i;
+                if (r >= rows) break;
+                T *yr = Y + (row0 + r) * ldy + 4 * cg;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (4 * cg + j < kout) yr[j] = acc[i][j];
+            }
         }
     }
 }
@@ -171,12 +197,12 @@ cudaError_t launch_apply(int64_t R, int l, const void *M, int64_t ldm, const voi
     const size_t es = dt == FRPCA_F32 ? 4 : 8;
     const int kp = (int)round_up(kout, 4);
     const size_t wbytes = es * (size_t)l * kp;
-    // Largest tile that fits next to W in shared memory.
+    // Largest tile (up to 64 rows) that fits next to W in shared memory.
     const size_t budget = 220 * 1024;
-    if (wbytes + es * l * 8 > budget) return cudaErrorInvalidValue;
-    int tile = (int)std::min<size_t>(64, (budget - wbytes) / (es * l));
+    if (wbytes + es * (l + 1) * 8 > budget) return cudaErrorInvalidValue;
+    int tile = (int)std::min<size_t>(64, (budget - wbytes) / (es * (l + 1)));
     tile = std::max(8, tile - tile % 8);
-    const size_t smem = wbytes + es * (size_t)tile * l;
+    const size_t smem = wbytes + es * (size_t)tile * (l + 1);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
