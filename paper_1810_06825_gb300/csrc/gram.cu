@@ -37,31 +37,42 @@ __device__ inline void df_fma(float x, float y, float &hi, float &lo) {
     lo = __fadd_rn(lo, __fadd_rn(err, e));
 }
 
-__global__ void __launch_bounds__(kThreads)
+// FP32 input: each thread accumulates one 8 x 4 tile (rows 8 ti .., columns
+// 4 tj .., tj >= 2 ti, which covers the upper triangle exactly once) in
+// double-float; 240 tiles for l = 120, so 256 (or, for l > 128, 512) threads
+// keep every tile busy with 64 accumulator registers per thread.
+constexpr int kTi = 8, kTj = 4;
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT)
 gram_partial_df_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, double *__restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *Ms = reinterpret_cast<float *>(smem_raw);
-    const int lp = (int)round_up(l, kTile);
-    const int nt = lp / kTile;
-    const int ntiles = nt * (nt + 1) / 2;
+    const int n8 = (int)ceil_div(l, kTi), n4 = n8 * 2;
+    const int lp = n8 * kTi;
     int ti = -1, tj = -1;
-    if ((int)threadIdx.x < ntiles) {
+    {
         int t = threadIdx.x, r = 0;
-        while (t >= nt - r) { t -= nt - r; ++r; }
-        ti = r;
-        tj = r + t;
+        while (r < n8 && t >= n4 - 2 * r) {
+            t -= n4 - 2 * r;
+            ++r;
+        }
+        if (r < n8) {
+            ti = r;
+            tj = 2 * r + t;
+        }
     }
-    float hi[kTile][kTile], lo[kTile][kTile];
+    float hi[kTi][kTj], lo[kTi][kTj];
 #pragma unroll
-    for (int a = 0; a < kTile; ++a)
+    for (int a = 0; a < kTi; ++a)
 #pragma unroll
-        for (int b = 0; b < kTile; ++b) hi[a][b] = lo[a][b] = 0.0f;
+        for (int b = 0; b < kTj; ++b) hi[a][b] = lo[a][b] = 0.0f;
     const int64_t G = gridDim.x;
     const int64_t r0 = (int64_t)blockIdx.x * R / G, r1 = (int64_t)(blockIdx.x + 1) * R / G;
     for (int64_t c0 = r0; c0 < r1; c0 += kChunk) {
         const int rows = (int)std::min<int64_t>(kChunk, r1 - c0);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < kChunk * lp; idx += kThreads) {
+        for (int idx = threadIdx.x; idx < kChunk * lp; idx += blockDim.x) {
             const int rr = idx / lp, cc = idx - rr * lp;
             Ms[idx] = (rr < rows && cc < l) ? M[(c0 + rr) * ld + cc] : 0.0f;
         }
@@ -69,27 +80,26 @@ gram_partial_df_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld
         if (ti >= 0) {
             for (int rr = 0; rr < rows; ++rr) {
                 const float *row = Ms + rr * lp;
-                float x[kTile], y[kTile];
+                const float4 x0 = *reinterpret_cast<const float4 *>(row + ti * kTi);
+                const float4 x1 = *reinterpret_cast<const float4 *>(row + ti * kTi + 4);
+                const float4 y = *reinterpret_cast<const float4 *>(row + tj * kTj);
+                const float x[kTi] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                const float yv[kTj] = {y.x, y.y, y.z, y.w};
 #pragma unroll
-                for (int a = 0; a < kTile; ++a) {
-                    x[a] = row[ti * kTile + a];
-                    y[a] = row[tj * kTile + a];
-                }
+                for (int a = 0; a < kTi; ++a)
 #pragma unroll
-                for (int a = 0; a < kTile; ++a)
-#pragma unroll
-                    for (int b = 0; b < kTile; ++b) df_fma(x[a], y[b], hi[a][b], lo[a][b]);
+                    for (int b = 0; b < kTj; ++b) df_fma(x[a], yv[b], hi[a][b], lo[a][b]);
             }
         }
     }
     if (ti >= 0) {
         double *P = partial + (int64_t)blockIdx.x * l * l;
 #pragma unroll
-        for (int a = 0; a < kTile; ++a)
+        for (int a = 0; a < kTi; ++a)
 #pragma unroll
-            for (int b = 0; b < kTile; ++b) {
-                const int ra = ti * kTile + a, cb = tj * kTile + b;
-                if (ra < l && cb < l) {
+            for (int b = 0; b < kTj; ++b) {
+                const int ra = ti * kTi + a, cb = tj * kTj + b;
+                if (ra <= cb && cb < l) {
                     const double v = (double)hi[a][b] + (double)lo[a][b];
                     P[ra * l + cb] = v;
                     P[cb * l + ra] = v;
@@ -188,8 +198,14 @@ cudaError_t launch_gram(int64_t R, int l, const void *M, int64_t ld, frpca_dtype
     double *partial = (double *)ws;
     cudaError_t e;
     if (dt == FRPCA_F32) {
-        const size_t sm = sizeof(float) * kChunk * lp;
-        gram_partial_df_kernel<<<G, kThreads, sm, s>>>(R, l, (const float *)M, ld, partial); count_launch();
+        const int n8 = (int)ceil_div(l, kTi);
+        const int tiles = n8 * 2 * n8 - n8 * (n8 - 1);
+        const size_t sm = sizeof(float) * kChunk * n8 * kTi;
+        if (tiles <= 256)
+            gram_partial_df_kernel<256><<<G, 256, sm, s>>>(R, l, (const float *)M, ld, partial);
+        else
+            gram_partial_df_kernel<512><<<G, 512, sm, s>>>(R, l, (const float *)M, ld, partial);
+        count_launch();
     } else {
         const size_t sm = sizeof(double) * kChunk * lp;
         gram_partial_kernel<double, double><<<G, kThreads, sm, s>>>(R, l, (const double *)M, ld, partial); count_launch();
