@@ -117,7 +117,8 @@ frpca_status frpca_run_async(frpca_handle h, const frpca_run_opts *opts, void *U
 frpca_status frpca_sync(frpca_handle h);
 
 /* Rebuilds the device CSR of A^T from A (same structure; values may have been
- * changed in place in borrowed arrays).  Synchronizes. */
+ * changed in place in borrowed arrays).  Enqueued on the handle's stream (no
+ * synchronization); runs enqueued after it see the new A^T. */
 frpca_status frpca_refresh(frpca_handle h);
 
 /* ---- instrumentation --------------------------------------------------------- */
@@ -173,6 +174,20 @@ frpca_status frpca_get_transpose(frpca_handle h, int64_t *rowptrT, int32_t *coli
  * magnitudes.  piv (nullable, device, l int64) receives the pivot rows.
  * Synchronizes; FRPCA_ERR_SINGULAR_PIVOT when a column has no nonzero pivot. */
 frpca_status frpca_lu(frpca_handle h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv);
+
+/* lu() of Alg. 5/6 for FP32 blocks with tournament pivoting (the form the
+ * FP32 path of frpca_run uses): P M = L U where the pivot rows of each panel
+ * of 8 columns are chosen by partial pivoting over candidate rows that every
+ * block of rows nominates by partial pivoting on its own rows (communication-
+ * avoiding LU, Grigori, Demmel and Xiang 2011).  Lemma 3 holds for any such
+ * row choice: range(P^T L) = range(M).  Output layout as frpca_lu (the pivot
+ * row of column j: multipliers left of j, 1 at j, 0 right of j); entries of L
+ * are not bounded by 1 as under partial pivoting, but stay small in practice.
+ * M: R x l floats, ld a multiple of 4, 16-byte aligned, device; piv: NULL or
+ * l int64 (device).  Falls back to partial pivoting when a block's rows do
+ * not fit in shared memory.  Synchronizes; FRPCA_ERR_SINGULAR_PIVOT when a
+ * panel column has no nonzero candidate. */
+frpca_status frpca_lu_tournament(frpca_handle h, int64_t R, int l, float *M, int64_t ld, int64_t *piv);
 
 /* frpca_lu without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- for example a

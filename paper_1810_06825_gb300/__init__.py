@@ -28,7 +28,7 @@ EXPORTED = [
     "frpca_create", "frpca_destroy", "frpca_last_error", "frpca_run", "frpca_run_async", "frpca_sync",
     "frpca_refresh", "frpca_set_timing", "frpca_get_stats", "frpca_reset_stats",
     "frpca_gaussian", "frpca_spmm", "frpca_get_transpose", "frpca_lu", "frpca_gram", "frpca_eig",
-    "frpca_eigsvd", "frpca_backward", "frpca_gram_splitbf16",
+    "frpca_eigsvd", "frpca_backward", "frpca_gram_splitbf16", "frpca_lu_tournament",
 ]
 
 
@@ -96,6 +96,7 @@ def library() -> ctypes.CDLL:
         "frpca_eigsvd": [P, I64, I, P, I64, I, P, P],
         "frpca_backward": [P, I, P, P, P, P, P, P, I, P],
         "frpca_gram_splitbf16": [P, I64, I, P, I64, P],
+        "frpca_lu_tournament": [P, I64, I, P, I64, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -194,6 +195,10 @@ def frpca_eigsvd(h, R, l, M, ld, dtype, S, V) -> None:
 
 
 # ---------------------------------------------------------------- torch helpers
+def frpca_lu_tournament(h, R, l, M, ld, piv) -> None:
+    _check(library().frpca_lu_tournament(h, R, l, M, ld, piv), h)
+
+
 def frpca_gram_splitbf16(h, R, l, M, ld, B) -> None:
     _check(library().frpca_gram_splitbf16(h, R, l, M, ld, B), h)
 

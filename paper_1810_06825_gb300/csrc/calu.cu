@@ -1,0 +1,361 @@
+// calu.cu -- lu() of Alg. 5/6 for the FP32 path with tournament pivoting
+// (communication-avoiding LU, Grigori, Demmel and Xiang, SIAM J. Matrix Anal.
+// Appl. 32, 2011): P M = L U with the pivot rows of each panel of kPanel
+// columns chosen by a tournament instead of one column at a time.  Lemma 3
+// only needs P M = L U with L unit lower trapezoidal and U nonsingular, so
+// range(P^T L) = range(M) whatever rows are chosen; the output has exactly the
+// layout of the partial-pivoting kernel (original row order, the pivot row of
+// column j holds its multipliers left of j, 1 at j and 0 right of j).
+//
+// Partial pivoting needs one grid-wide argmax per column, i.e. l grid
+// barriers; here a panel costs one.  One cooperative launch; block b keeps its
+// contiguous row range in shared memory.  Per panel (columns c0 .. c0+w-1):
+//  (1) every block runs partial pivoting on a copy of the panel restricted to
+//      its unpivoted rows (one thread per row) and publishes the w rows it
+//      picked (their current full rows) to a double-buffered candidate area;
+//  (2) grid barrier;
+//  (3) every block replays the same tournament -- partial pivoting over the
+//      G * w candidates' panel entries (largest magnitude, then smallest row
+//      index) -- and eliminates among the w winners in pivot order, which
+//      gives the U rows of the panel and the multipliers between winners;
+//  (4) every block updates its own rows: multipliers by forward substitution
+//      with the panel's U, then the rank-w update of the trailing columns;
+//      winner rows are set to their final P^T L form.
+// Waits are bounded (grid_barrier) and every block takes the same decisions,
+// so they leave the loop together on a singular panel.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace frpca {
+namespace {
+
+constexpr int kCaluThreads = 512;  // also the most rows a block may own
+constexpr int kPanel = 8;
+constexpr int kMaxCaluBlocks = 160;
+constexpr int kMaxCand = kMaxCaluBlocks * kPanel;
+
+__device__ inline unsigned int fkey(float v) {
+    const unsigned int b = __float_as_uint(v) & 0x7fffffffu;
+    return b > 0x7f800000u ? 0u : b;  // NaN never pivots
+}
+
+// Pivot searches compare one 32-bit key: the magnitude's bit pattern with its
+// low `bits` bits replaced by (2^bits - 1 - index), so the maximum is the
+// largest magnitude (to 2^-(23 - bits) relative) and, among equal ones, the
+// smallest index.  Any deterministic choice of large pivots keeps Lemma 3;
+// truncating the magnitude lets one __reduce_max_sync do a warp's search.
+__device__ inline unsigned int pack_key(float v, int index, int bits) {
+    const unsigned int mag = fkey(v) >> bits;
+    return mag ? (mag << bits) | ((1u << bits) - 1u - (unsigned int)index) : 0u;
+}
+__device__ inline int key_index(unsigned int key, int bits) { return (int)((1u << bits) - 1u - (key & ((1u << bits) - 1u))); }
+
+constexpr int kRowBits = 9;    // local row < 512
+constexpr int kSlotBits = 11;  // candidate slot < 2048
+
+constexpr int kCaluWarps = kCaluThreads / 32;
+
+// Block-wide max of a key; every thread gets it.
+__device__ inline unsigned int block_max(unsigned int key, unsigned int *wmax) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    key = __reduce_max_sync(0xffffffffu, key);
+    if (lane == 0) wmax[warp] = key;
+    __syncthreads();
+    unsigned int v = lane < kCaluWarps ? wmax[lane] : 0u;
+    v = __reduce_max_sync(0xffffffffu, v);
+    __syncthreads();  // wmax may be reused right after
+    return v;
+}
+
+// Shared memory after the row cache: tournament panel entries, candidate row
+// ids and chosen flags, the winners' rows, and per-row flags.
+struct CaluLayout {
+    size_t tv, tid, tch, urows, pivd, total;
+};
+
+// Every section starts on a 16-byte boundary (the row cache has an odd
+// stride, so its size is only a multiple of 4 bytes).
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+__host__ __device__ inline CaluLayout calu_layout(int rows_max, int l) {
+    CaluLayout s{};
+    size_t off = align16((size_t)rows_max * (l + 1) * sizeof(float));
+    s.tv = off; off = align16(off + (size_t)kMaxCand * kPanel * sizeof(float));
+    s.tid = off; off = align16(off + (size_t)kMaxCand * sizeof(int));
+    s.tch = off; off = align16(off + (size_t)kMaxCand);
+    s.urows = off; off = align16(off + (size_t)kPanel * FRPCA_MAX_L * sizeof(float));
+    s.pivd = off; off = align16(off + (size_t)rows_max);
+    s.total = off;
+    return s;
+}
+
+// Candidate area, double-buffered by panel parity: per slot (block * kPanel +
+// k) its row id, its 8 panel entries (one 32-byte sector) and its full row.
+struct CandArea {
+    int *ids;        // [2][kMaxCand]
+    float *panel;    // [2][kMaxCand][kPanel]
+    float *rows;     // [2][kMaxCand][ldc]
+};
+
+__global__ void __launch_bounds__(kCaluThreads, 1)
+calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__restrict__ piv_out, CandArea cand,
+            int ldc, GridBarrier *bar, int *status, long long limit_cycles) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int win_row[kPanel];
+    __shared__ int win_slot[kPanel];
+    __shared__ unsigned int wmax[kCaluWarps];
+    __shared__ float pvw[kPanel];  // the local pivot's panel entries
+    const unsigned G = gridDim.x;
+    const int t = threadIdx.x;
+    const int64_t r0 = (int64_t)blockIdx.x * R / G, r1 = (int64_t)(blockIdx.x + 1) * R / G;
+    const int nrows = (int)(r1 - r0);
+    const int rows_max = (int)((R + G - 1) / G);
+    const int cst = l + 1;
+    const CaluLayout L = calu_layout(rows_max, l);
+    float *cache = reinterpret_cast<float *>(smem);
+    float *tv = reinterpret_cast<float *>(smem + L.tv);    // kPanel x candidate (column-major)
+    int *tid = reinterpret_cast<int *>(smem + L.tid);      // candidate row ids (-1: none)
+    unsigned char *tch = smem + L.tch;                      // chosen in the tournament
+    float *U = reinterpret_cast<float *>(smem + L.urows);  // kPanel x FRPCA_MAX_L: winners' rows
+    unsigned char *pivd = smem + L.pivd;
+    const int ncand = (int)G * kPanel;
+
+    for (int i = t; i < nrows; i += kCaluThreads) pivd[i] = 0;
+    for (int idx = t; idx < nrows * l; idx += kCaluThreads) {
+        const int i = idx / l, c = idx - i * l;
+        cache[i * cst + c] = M[(r0 + i) * ld + c];
+    }
+    __syncthreads();
+
+    bool ok = true;
+    for (int c0 = 0, panel = 0; c0 < l && ok; c0 += kPanel, ++panel) {
+        const int w = min(kPanel, l - c0);
+        int *cids = cand.ids + (size_t)(panel & 1) * kMaxCand;
+        float *cpan = cand.panel + (size_t)(panel & 1) * kMaxCand * kPanel;
+        float *crows = cand.rows + (size_t)(panel & 1) * kMaxCand * ldc;
+        // (1) Local partial pivoting on a copy of the panel, one thread per row.
+        float pv[kPanel];
+        const bool mine = t < nrows && !pivd[t];
+        bool picked = false;
+#pragma unroll
+        for (int k = 0; k < kPanel; ++k) pv[k] = (mine && k < w) ? cache[t * cst + c0 + k] : 0.0f;
+        for (int k = 0; k < w; ++k) {
+            float pk = 0.0f;
+#pragma unroll
+            for (int kk = 0; kk < kPanel; ++kk)
+                if (kk == k) pk = pv[kk];
+            const unsigned int key = block_max((mine && !picked) ? pack_key(pk, t, kRowBits) : 0u, wmax);
+            const int slot = blockIdx.x * kPanel + k;
+            if (key == 0u) {  // no nonzero entry left in this block
+                if (t == 0) cids[slot] = -1;
+                continue;
+            }
+            const int wl = key_index(key, kRowBits);
+            if (t == wl) {
+                picked = true;
+#pragma unroll
+                for (int kk = 0; kk < kPanel; ++kk) pvw[kk] = pv[kk];
+                cids[slot] = (int)(r0 + wl);
+            }
+            // Publish the picked row as it is (not the eliminated copy).
+            for (int c = t; c < l; c += kCaluThreads) crows[(size_t)slot * ldc + c] = cache[wl * cst + c];
+            if (t < kPanel) cpan[slot * kPanel + t] = (t < w) ? cache[wl * cst + c0 + t] : 0.0f;
+            __syncthreads();
+            if (mine && !picked) {
+                const float m = pk / pvw[k];
+#pragma unroll
+                for (int kk = 0; kk < kPanel; ++kk)
+                    if (kk > k && kk < w) pv[kk] = fmaf(-m, pvw[kk], pv[kk]);
+            }
+        }
+        for (int k = w + t; k < kPanel; k += kCaluThreads) cids[blockIdx.x * kPanel + k] = -1;
+        ok = grid_barrier(bar, G, status, limit_cycles);
+        if (!ok) break;
+
+        // (3) The tournament, the same in every block.
+        for (int i = t; i < ncand; i += kCaluThreads) {
+            const int id = __ldcg(cids + i);
+            tid[i] = id;
+            tch[i] = 0;
+            const float4 a = id >= 0 ? __ldcg(reinterpret_cast<const float4 *>(cpan + i * kPanel)) : make_float4(0, 0, 0, 0);
+            const float4 b = id >= 0 ? __ldcg(reinterpret_cast<const float4 *>(cpan + i * kPanel + 4)) : make_float4(0, 0, 0, 0);
+            tv[0 * kMaxCand + i] = a.x; tv[1 * kMaxCand + i] = a.y; tv[2 * kMaxCand + i] = a.z; tv[3 * kMaxCand + i] = a.w;
+            tv[4 * kMaxCand + i] = b.x; tv[5 * kMaxCand + i] = b.y; tv[6 * kMaxCand + i] = b.z; tv[7 * kMaxCand + i] = b.w;
+        }
+        __syncthreads();
+        bool singular = false;
+        for (int k = 0; k < w; ++k) {
+            unsigned int key = 0u;
+            for (int i = t; i < ncand; i += kCaluThreads)
+                if (tid[i] >= 0 && !tch[i]) key = max(key, pack_key(tv[k * kMaxCand + i], i, kSlotBits));
+            key = block_max(key, wmax);
+            if (key == 0u) {  // no nonzero pivot left in this column: every block sees it
+                if (t == 0 && blockIdx.x == 0) set_status(status, FRPCA_ERR_SINGULAR_PIVOT);
+                singular = true;
+                break;
+            }
+            const int sw = key_index(key, kSlotBits);
+            if (t == 0) {
+                tch[sw] = 1;
+                win_row[k] = tid[sw];
+                win_slot[k] = sw;
+                if (blockIdx.x == 0 && piv_out) piv_out[c0 + k] = tid[sw];
+            }
+            const float ukk = tv[k * kMaxCand + sw];
+            for (int i = t; i < ncand; i += kCaluThreads) {
+                if (i == sw || tid[i] < 0 || tch[i]) continue;
+                const float m = tv[k * kMaxCand + i] / ukk;
+                for (int kk = k + 1; kk < w; ++kk) tv[kk * kMaxCand + i] = fmaf(-m, tv[kk * kMaxCand + sw], tv[kk * kMaxCand + i]);
+            }
+            __syncthreads();
+        }
+        if (singular) { ok = false; break; }
+        // The winners' full rows, eliminated among themselves in pivot order:
+        // U row k, and the multipliers L11(k, k') (kept left of the diagonal).
+        for (int idx = t; idx < w * l; idx += kCaluThreads) {
+            const int k = idx / l, c = idx - k * l;
+            U[k * FRPCA_MAX_L + c] = __ldcg(crows + (size_t)win_slot[k] * ldc + c);
+        }
+        __syncthreads();
+        for (int k = 0; k < w; ++k) {
+            const float ukk = U[k * FRPCA_MAX_L + c0 + k];
+            const int span = l - c0 - k - 1;  // columns right of the pivot
+            for (int idx = t; idx < (w - 1 - k) * span; idx += kCaluThreads) {
+                const int k2 = k + 1 + idx / span, c = c0 + k + 1 + idx % span;
+                const float m = U[k2 * FRPCA_MAX_L + c0 + k] / ukk;
+                U[k2 * FRPCA_MAX_L + c] = fmaf(-m, U[k * FRPCA_MAX_L + c], U[k2 * FRPCA_MAX_L + c]);
+            }
+            __syncthreads();
+            for (int k2 = k + 1 + t; k2 < w; k2 += kCaluThreads)
+                U[k2 * FRPCA_MAX_L + c0 + k] = U[k2 * FRPCA_MAX_L + c0 + k] / ukk;  // L11(k2, k)
+            __syncthreads();
+        }
+
+        // (4) Own rows.  Winners take their final form; the others get their
+        // multipliers for the panel (forward substitution with U11).
+        if (t < nrows && !pivd[t]) {
+            const int gr = (int)(r0 + t);
+            int wk = -1;
+            for (int k = 0; k < w; ++k)
+                if (win_row[k] == gr) wk = k;
+            float *row = cache + t * cst;
+            if (wk >= 0) {
+                for (int k = 0; k < wk; ++k) row[c0 + k] = U[wk * FRPCA_MAX_L + c0 + k];
+                row[c0 + wk] = 1.0f;
+                for (int c = c0 + wk + 1; c < l; ++c) row[c] = 0.0f;
+                pivd[t] = 1;
+            } else {
+                for (int k = 0; k < w; ++k) {
+                    const float m = row[c0 + k] / U[k * FRPCA_MAX_L + c0 + k];
+                    row[c0 + k] = m;
+                    for (int kk = k + 1; kk < w; ++kk) row[c0 + kk] = fmaf(-m, U[k * FRPCA_MAX_L + c0 + kk], row[c0 + kk]);
+                }
+            }
+        }
+        __syncthreads();
+        // Rank-w update of the trailing columns, 4 rows x 4 columns per item:
+        // per panel column, 4 multipliers and one 16-byte piece of U feed 16 FMAs.
+        const int c1 = c0 + w;
+        if (c1 < l) {
+            const int cg = (l - c1 + 3) / 4, rg = (nrows + 3) / 4;
+            for (int it = t; it < rg * cg; it += kCaluThreads) {
+                const int i0 = 4 * (it / cg), cc = c1 + 4 * (it % cg);
+                float acc[4][4], mu[4][kPanel];
+                bool act[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int i = i0 + a;
+                    act[a] = i < nrows && !pivd[i];
+                    const float *row = cache + (act[a] ? i : 0) * cst;
+#pragma unroll
+                    for (int k = 0; k < kPanel; ++k) mu[a][k] = (act[a] && k < w) ? row[c0 + k] : 0.0f;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = (act[a] && cc + b < l) ? row[cc + b] : 0.0f;
+                }
+#pragma unroll
+                for (int k = 0; k < kPanel; ++k) {
+                    if (k >= w) break;
+                    const float4 u = *reinterpret_cast<const float4 *>(U + k * FRPCA_MAX_L + cc);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        acc[a][0] = fmaf(-mu[a][k], u.x, acc[a][0]);
+                        acc[a][1] = fmaf(-mu[a][k], u.y, acc[a][1]);
+                        acc[a][2] = fmaf(-mu[a][k], u.z, acc[a][2]);
+                        acc[a][3] = fmaf(-mu[a][k], u.w, acc[a][3]);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    if (!act[a]) continue;
+                    float *row = cache + (i0 + a) * cst;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        if (cc + b < l) row[cc + b] = acc[a][b];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int idx = t; idx < nrows * l; idx += kCaluThreads) {
+        const int i = idx / l, c = idx - i * l;
+        M[(r0 + i) * ld + c] = cache[i * cst + c];
+    }
+}
+
+int calu_blocks(int64_t R, int num_sms) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)num_sms, ceil_div(R, 32), (int64_t)kMaxCaluBlocks}));
+}
+
+}  // namespace
+
+size_t calu_workspace_bytes(int l) {
+    const int ldc = (int)round_up(l, 4);
+    return 256 + 2 * (size_t)kMaxCand * (sizeof(int) + sizeof(float) * (kPanel + ldc)) + 256;
+}
+
+cudaError_t launch_calu(int64_t R, int l, float *M, int64_t ld, int64_t *piv, void *ws, int *d_status, int num_sms,
+                        cudaStream_t s) {
+    if (l < 1 || l > FRPCA_MAX_L || R < l) return cudaErrorInvalidValue;
+    if (R >= ((int64_t)1 << 31)) return cudaErrorNotSupported;
+    const int G = calu_blocks(R, num_sms);
+    const int rows_max = (int)ceil_div(R, G);
+    if (rows_max > kCaluThreads) return cudaErrorNotSupported;
+    const CaluLayout L = calu_layout(rows_max, l);
+    int dev = 0, max_optin = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return e;
+    cudaFuncAttributes attr;
+    if ((e = cudaFuncGetAttributes(&attr, calu_kernel)) != cudaSuccess) return e;
+    if (L.total + attr.sharedSizeBytes > (size_t)max_optin) return cudaErrorNotSupported;
+    if ((e = cudaFuncSetAttribute(calu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total)) !=
+        cudaSuccess)
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, calu_kernel, kCaluThreads, L.total)) !=
+        cudaSuccess)
+        return e;
+    if (per_sm < 1 || (int64_t)per_sm * num_sms < G) return cudaErrorNotSupported;
+    char *p = (char *)ws;
+    GridBarrier *bar = (GridBarrier *)p;
+    const int ldc = (int)round_up(l, 4);
+    CandArea cand;
+    cand.panel = (float *)(p + 256);                                // 32-byte aligned sectors
+    cand.rows = cand.panel + 2 * (size_t)kMaxCand * kPanel;
+    cand.ids = (int *)(cand.rows + 2 * (size_t)kMaxCand * ldc);
+    if ((e = cudaMemsetAsync(ws, 0, 256, s)) != cudaSuccess) return e;
+    int64_t Rv = R, ldv = ld;
+    int lv = l, ldcv = ldc;
+    long long lim = kBarrierLimitCycles;
+    void *Mp = M;
+    void *args[] = {&Rv, &lv, &Mp, &ldv, &piv, &cand, &ldcv, &bar, &d_status, &lim};
+    count_launch();
+    return cudaLaunchCooperativeKernel((const void *)calu_kernel, dim3((unsigned)G), dim3(kCaluThreads), args,
+                                       L.total, s);
+}
+
+}  // namespace frpca

@@ -181,10 +181,22 @@ frpca_status spmm_pass(frpca_ctx *h, int trans, int l, const void *X, int64_t ld
     return FRPCA_OK;
 }
 
-frpca_status lu_step(frpca_ctx *h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv) {
-    CK(h->ws_lu.ensure(lu_workspace_bytes(R, l)), "alloc lu workspace");
+// lu() of Alg. 5/6.  FP64: partial pivoting, reproducible bit for bit.  FP32:
+// tournament pivoting (one grid barrier per 8 columns instead of per column)
+// when a block's rows fit in shared memory, partial pivoting otherwise; both
+// return P^T L with range(P^T L) = range(M) (Lemma 3).
+frpca_status lu_step(frpca_ctx *h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv,
+                     bool tournament = true) {
+    CK(h->ws_lu.ensure(std::max(lu_workspace_bytes(R, l), calu_workspace_bytes(l))), "alloc lu workspace");
     PhaseTimer t(h, PH_LU);
-    CK(launch_lu(R, l, M, ld, dt, piv, h->ws_lu.ptr, h->d_status, h->num_sms, h->stream), "lu launch");
+    cudaError_t e = cudaErrorNotSupported;
+    if (dt == FRPCA_F32 && tournament)
+        e = launch_calu(R, l, (float *)M, ld, piv, h->ws_lu.ptr, h->d_status, h->num_sms, h->stream);
+    if (e == cudaErrorNotSupported) {
+        (void)cudaGetLastError();
+        e = launch_lu(R, l, M, ld, dt, piv, h->ws_lu.ptr, h->d_status, h->num_sms, h->stream);
+    }
+    CK(e, "lu launch");
     h->acc.lu_calls += 1;
     return FRPCA_OK;
 }
@@ -581,7 +593,17 @@ frpca_status frpca_lu(frpca_handle h, int64_t R, int l, void *M, int64_t ld, frp
     if (l > FRPCA_MAX_L) return fail(h, FRPCA_ERR_UNSUPPORTED, "l > 160 is not supported");
     frpca_status st = reset_status(h);
     if (st != FRPCA_OK) return st;
-    if ((st = lu_step(h, R, l, M, ld, dt, piv)) != FRPCA_OK) return st;
+    if ((st = lu_step(h, R, l, M, ld, dt, piv, /*tournament=*/false)) != FRPCA_OK) return st;
+    return read_status(h);
+}
+
+frpca_status frpca_lu_tournament(frpca_handle h, int64_t R, int l, float *M, int64_t ld, int64_t *piv) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    if (l < 1 || R < l || !ld_ok(ld, l, FRPCA_F32) || !M) return fail(h, FRPCA_ERR_INVALID_ARG, "need R >= l >= 1 and ld >= l");
+    if (l > FRPCA_MAX_L) return fail(h, FRPCA_ERR_UNSUPPORTED, "l > 160 is not supported");
+    frpca_status st = reset_status(h);
+    if (st != FRPCA_OK) return st;
+    if ((st = lu_step(h, R, l, M, ld, FRPCA_F32, piv, /*tournament=*/true)) != FRPCA_OK) return st;
     return read_status(h);
 }
 

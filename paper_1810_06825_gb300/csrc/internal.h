@@ -110,6 +110,12 @@ cudaError_t launch_column_signs(int64_t R, int k, const void *X, int64_t ld, frp
 cudaError_t launch_scale_columns(int64_t R, int k, void *X, int64_t ld, frpca_dtype dt, const double *sign,
                                  cudaStream_t s);
 
+// ---- calu.cu (FP32 LU with tournament pivoting; cudaErrorNotSupported when
+// a block's rows do not fit in shared memory)
+size_t calu_workspace_bytes(int l);
+cudaError_t launch_calu(int64_t R, int l, float *M, int64_t ld, int64_t *piv, void *ws, int *d_status, int num_sms,
+                        cudaStream_t s);
+
 // ---- gram_tc.cu (split-BF16 Gram on the tcgen05 tensor cores, FP32 input)
 int gram_tc_max_l();
 size_t gram_tc_workspace_bytes(int64_t R, int l, int sms);

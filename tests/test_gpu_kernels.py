@@ -247,3 +247,48 @@ def test_invalid_csr_rejected_on_device():
     with pytest.raises(frpca.FrpcaError):
         frpca.FrPCA(torch.from_numpy(A.indptr).to(DEV), torch.from_numpy(bad).to(DEV),
                     torch.from_numpy(A.data).to(DEV), (A.m, A.n))
+
+
+# ---------------------------------------------------------------- LU, tournament pivoting (FP32 path)
+def _lu_tournament(M):
+    R, l = M.shape
+    A = frpca.empty_block(R, l, torch.float32, DEV)
+    A.copy_(torch.from_numpy(M).to(DEV))
+    piv = torch.empty(l, dtype=torch.int64, device=DEV)
+    frpca.frpca_lu_tournament(frpca._Context.get(), R, l, A.data_ptr(), A.stride(0), piv.data_ptr())
+    return _cpu(A), piv.cpu().numpy()
+
+
+@pytest.mark.parametrize("R,l", [(50, 8), (300, 45), (4099, 48), (20_000, 120), (50_000, 120), (9_000, 160),
+                                 (1000, 1), (33, 33)])
+def test_lu_tournament_structure_and_range(R, l):
+    """Lemma 3 for any pivot rows: range(P^T L) = range(M); the pivot row of
+    column j holds 1 at j and 0 right of j; the unit lower factor stays
+    moderate (tournament pivoting does not bound it by 1)."""
+    M = np.random.default_rng(R + 7 * l).standard_normal((R, l)).astype(np.float32)
+    P, piv = _lu_tournament(M)
+    assert len(set(piv.tolist())) == l and piv.min() >= 0 and piv.max() < R
+    for j, p in enumerate(piv):
+        assert P[p, j] == 1.0 and np.all(P[p, j + 1:] == 0.0)
+    assert np.all(np.isfinite(P)) and np.max(np.abs(P)) <= 16.0
+    assert max_principal_sine(P, M.astype(np.float64)) < 1e-4
+
+
+def test_lu_tournament_matches_partial_pivoting_range():
+    """Same range as the partial-pivoting factor of the same block, on an ill-
+    conditioned block like the power iteration's (columns nearly aligned)."""
+    rng = np.random.default_rng(5)
+    base = rng.standard_normal((30_000, 1))
+    M = (base + 1e-3 * rng.standard_normal((30_000, 96))) * np.logspace(0, -2, 96)
+    M = M.astype(np.float32)
+    P_t, _ = _lu_tournament(M)
+    P_p, _ = frpca.lu(torch.from_numpy(M).to(DEV))
+    assert max_principal_sine(P_t, _cpu(P_p)) < 1e-3
+
+
+def test_lu_tournament_singular_pivot_reports():
+    M = np.random.default_rng(1).standard_normal((500, 20)).astype(np.float32)
+    M[:, 11] = 0.0
+    with pytest.raises(frpca.FrpcaError) as ei:
+        _lu_tournament(M)
+    assert ei.value.status == 5
