@@ -9,7 +9,7 @@
 // carries each entry's row and value along.  Each pass is a stable counting
 // sort over CTA tiles of 8192 entries: a tile's digit counts come from a
 // digit-major scan of all tiles' histograms; inside the tile, warps rank equal
-// digits with __match_any_sync in entry order, the tile is reordered by digit
+// digits (eight ballots per 32-entry chunk) in entry order, the tile is reordered by digit
 // in shared memory, and each digit's run is written out contiguously.  The
 // row pointers of A^T are read off the sorted column indices.
 #include <algorithm>
@@ -149,6 +149,21 @@ __global__ void validate_kernel(int64_t m, int64_t n, int64_t nnz, const int64_t
 // ------------------------------------------------------------------ radix passes
 __device__ inline int digit_of(uint32_t key, int shift) { return (int)((key >> shift) & (kRadix - 1)); }
 
+// Lanes of the warp holding the same 8-bit digit as this lane (all lanes must
+// call it; lanes with valid == false get an empty mask and match nobody).
+// Eight ballots, one per digit bit, instead of __match_any_sync, whose
+// throughput bounded the sort.
+__device__ inline unsigned int digit_peers(int d, bool valid) {
+    unsigned int peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1;
+        const unsigned int bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return valid ? peers : 0u;
+}
+
 // Entry e of tile t, chunk c of warp w, lane: tiles are contiguous ranges and
 // so are a warp's chunks, so ranks follow entry order.
 __device__ inline int64_t entry_of(int64_t t, int warp, int c, int lane) {
@@ -168,8 +183,8 @@ radix_hist_kernel(const uint32_t *__restrict__ keys, int64_t nnz, int shift, int
     for (int c = 0; c < kChunks; ++c) {
         const int64_t e = entry_of(t, warp, c, lane);
         const bool valid = e < nnz;
-        const int d = valid ? digit_of(keys[e], shift) : kRadix;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int d = valid ? digit_of(keys[e], shift) : 0;
+        const unsigned peers = digit_peers(d, valid);
         if (valid && lane == 31 - __clz(peers)) atomicAdd(&cnt[d], __popc(peers));
     }
     __syncthreads();
@@ -206,8 +221,8 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const int32_t *__rest
         const int64_t e = entry_of(t, warp, c, lane);
         const bool valid = e < nnz;
         key[c] = valid ? keys_in[e] : 0u;
-        dig[c] = valid ? digit_of(key[c], shift) : kRadix;
-        peer[c] = __match_any_sync(0xffffffffu, dig[c]);
+        dig[c] = valid ? digit_of(key[c], shift) : 0;
+        peer[c] = digit_peers(dig[c], valid);
         if (valid && lane == 31 - __clz(peer[c])) wrun[warp * kRadix + dig[c]] += __popc(peer[c]);
         __syncwarp();
     }
