@@ -7,7 +7,7 @@
 // rows ascending, and the result is unique (bit-exact whatever the schedule).
 // The sort is an LSD radix sort over 8-bit digits of the column index that
 // carries each entry's row and value along.  Each pass is a stable counting
-// sort over CTA tiles of 8192 entries: a tile's digit counts come from a
+// sort over CTA tiles of 4096 entries: a tile's digit counts come from a
 // digit-major scan of all tiles' histograms; inside the tile, warps rank equal
 // digits (eight ballots per 32-entry chunk) in entry order, the tile is reordered by digit
 // in shared memory, and each digit's run is written out contiguously.  The
@@ -23,8 +23,8 @@ namespace {
 constexpr int kRadix = 256;
 constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kChunks = 16;                        // 32-entry chunks per warp
-constexpr int kSortTile = kSortWarps * kChunks * 32;  // 8192 entries per CTA tile
+constexpr int kChunks = 8;                         // 32-entry chunks per warp
+constexpr int kSortTile = kSortWarps * kChunks * 32;  // 4096 entries per CTA tile
 
 // ------------------------------------------------------------------ scan
 constexpr int kScanThreads = 1024;
