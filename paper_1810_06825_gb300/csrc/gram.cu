@@ -44,7 +44,7 @@ __device__ inline void df_fma(float x, float y, float &hi, float &lo) {
 constexpr int kTi = 8, kTj = 4;
 
 template <int MAXT>
-__global__ void __launch_bounds__(MAXT)
+__global__ void __launch_bounds__(MAXT, 512 / MAXT)
 gram_partial_df_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, double *__restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *Ms = reinterpret_cast<float *>(smem_raw);
