@@ -252,6 +252,21 @@ __device__ inline double block_sum(double v, double *red) {
 }
 
 
+__device__ inline double block_max_d(double v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+    __syncthreads();
+    if (threadIdx.x == 0) red[0] = t;
+    __syncthreads();
+    return red[0];
+}
+
 // 1/g to double accuracy: float reciprocal, one Newton step in double.
 __device__ inline double recip(double g) {
     const double ag = fabs(g);
@@ -261,28 +276,40 @@ __device__ inline double recip(double g) {
     return fma(r0, e, r0);
 }
 
-// One 16 x 16 tile (ti, tj) of C = op(A) Bm (+ Cadd) for b x b blocks with
-// leading dimension ld; op(A) = A^T when TA.  Operands written by other CTAs
-// of the same launch are read past L1 (__ldcg).
+// One 4 x 8 tile (rows 4 ti .., columns 8 tj ..) of C = op(A) Bm (+ Cadd)
+// for b x b blocks: the 256 threads take 32 outputs x 8 slices of the inner
+// index, and each output's eight partial sums are added by shuffles in a fixed
+// order (deterministic).  Small tiles spread the double-precision work over
+// every SM of the cooperative launch (GB300 issues ~2 DFMA per clock per SM,
+// so that rate, not memory, bounds these products).  Operands written by
+// other CTAs of the launch are read past L1.
+constexpr int kTm = 4, kTn = 8, kKs = 8;
+
 template <bool TA>
-__device__ void tile_gemm(int b, int ld, int ti, int tj, const double *A, const double *Bm, const double *Cadd,
-                          double *C, double (*As)[17], double (*Bs)[17]) {
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int i = ti * 16 + ty, j = tj * 16 + tx;
+__device__ void tile_gemm_small(int b, int ld, int ti, int tj, const double *A, const double *Bm, const double *Cadd,
+                                double *C) {
+    const int o = threadIdx.x / kKs, sl = threadIdx.x % kKs;
+    const int i = ti * kTm + o / kTn, j = tj * kTn + o % kTn;
+    constexpr int kMaxSlice = (FRPCA_MAX_L + kKs - 1) / kKs;
+    const int klen = (b + kKs - 1) / kKs, k0 = sl * klen, k1 = min(b, k0 + klen);
     double acc = 0.0;
-    for (int k0 = 0; k0 < b; k0 += 16) {
-        const int ka = k0 + tx, kb = k0 + ty;
-        if (TA)
-            As[ty][tx] = (i < b && ka < b) ? __ldcg(A + ka * ld + i) : 0.0;
-        else
-            As[ty][tx] = (i < b && ka < b) ? __ldcg(A + i * ld + ka) : 0.0;
-        Bs[ty][tx] = (kb < b && j < b) ? __ldcg(Bm + kb * ld + j) : 0.0;
-        __syncthreads();
+    if (i < b && j < b) {
+        // All operands first (they come from L2: one round trip, not one per term).
+        double av[kMaxSlice], bv[kMaxSlice];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) acc = fma(As[ty][k], Bs[k][tx], acc);
-        __syncthreads();
+        for (int kk = 0; kk < kMaxSlice; ++kk) {
+            const int k = k0 + kk;
+            const bool in = k < k1;
+            av[kk] = in ? (TA ? __ldcg(A + k * ld + i) : __ldcg(A + i * ld + k)) : 0.0;
+            bv[kk] = in ? __ldcg(Bm + k * ld + j) : 0.0;
+        }
+#pragma unroll
+        for (int kk = 0; kk < kMaxSlice; ++kk) acc = fma(av[kk], bv[kk], acc);
     }
-    if (i < b && j < b) C[i * ld + j] = acc + (Cadd ? __ldcg(Cadd + i * ld + j) : 0.0);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    if (sl == 0 && i < b && j < b) C[i * ld + j] = acc + (Cadd ? __ldcg(Cadd + i * ld + j) : 0.0);
 }
 
 // The Ogita-Aishima refinement of one level (see the header), all steps in
@@ -304,13 +331,12 @@ oa_refine_kernel(const int *dn, int ld, const double *__restrict__ Cm, double *Z
                  int *status, long long limit_cycles) {
     const int b = *dn;
     if (b < 1) return;
-    __shared__ double As[16][17], Bs[16][17];
     __shared__ double red[32];
     __shared__ double lam_s[FRPCA_MAX_L];
     __shared__ double s_delta, s_low;
     __shared__ unsigned long long emax_s;
     const int G = gridDim.x;
-    const int tb = (b + 15) / 16, ntiles = tb * tb;
+    const int tbn = (b + kTn - 1) / kTn, ntiles = ((b + kTm - 1) / kTm) * tbn;
     const int rows = (b + G - 1) / G;
     const int r0 = min(b, (int)blockIdx.x * rows), r1 = min(b, r0 + rows);
     double *Zc = Z, *Zn = Z2;
@@ -318,12 +344,12 @@ oa_refine_kernel(const int *dn, int ld, const double *__restrict__ Cm, double *Z
         if (blockIdx.x == 0 && threadIdx.x == 0) emax[it] = 0ull;
         // (1) G = Z^T Z, T = C Z
         for (int t = blockIdx.x; t < ntiles; t += G) {
-            tile_gemm<true>(b, ld, t / tb, t % tb, Zc, Zc, nullptr, Gm, As, Bs);
-            tile_gemm<false>(b, ld, t / tb, t % tb, Cm, Zc, nullptr, T, As, Bs);
+            tile_gemm_small<true>(b, ld, t / tbn, t % tbn, Zc, Zc, nullptr, Gm);
+            tile_gemm_small<false>(b, ld, t / tbn, t % tbn, Cm, Zc, nullptr, T);
         }
         if (!grid_barrier(bar, G, status, limit_cycles)) return;
         // (2) S = Z^T C Z
-        for (int t = blockIdx.x; t < ntiles; t += G) tile_gemm<true>(b, ld, t / tb, t % tb, Zc, T, nullptr, S, As, Bs);
+        for (int t = blockIdx.x; t < ntiles; t += G) tile_gemm_small<true>(b, ld, t / tbn, t % tbn, Zc, T, nullptr, S);
         if (!grid_barrier(bar, G, status, limit_cycles)) return;
         // (3) partial norms over rows r0 .. r1 - 1
         {
@@ -349,19 +375,29 @@ oa_refine_kernel(const int *dn, int ld, const double *__restrict__ Cm, double *Z
         }
         if (!grid_barrier(bar, G, status, limit_cycles)) return;
         // (4) lambda_i = S_ii / (1 - R_ii) = S_ii / G_ii, delta, E on rows r0 .. r1 - 1
-        for (int i = threadIdx.x; i < b; i += blockDim.x) lam_s[i] = __ldcg(S + i * ld + i) / __ldcg(Gm + i * ld + i);
-        if (threadIdx.x == 0) emax_s = 0ull;
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        // The partial norms of all CTAs and max |lambda|, reduced by the whole
+        // block (one L2 round trip instead of one per partial).
+        {
             double sS = 0.0, sB = 0.0, sR = 0.0, top = 0.0;
-            for (int p = 0; p < G; ++p) {
+            for (int p = threadIdx.x; p < G; p += blockDim.x) {
                 sS += __ldcg(part + 3 * p);
                 sB += __ldcg(part + 3 * p + 1);
                 sR += __ldcg(part + 3 * p + 2);
             }
-            for (int i = 0; i < b; ++i) top = fmax(top, fabs(lam_s[i]));
-            s_delta = 2.0 * (sqrt(sS) + sqrt(sB) * sqrt(sR));
-            s_low = kTau * top;
+            for (int i = threadIdx.x; i < b; i += blockDim.x) {
+                const double li = __ldcg(S + i * ld + i) / __ldcg(Gm + i * ld + i);
+                lam_s[i] = li;
+                top = fmax(top, fabs(li));
+            }
+            sS = block_sum(sS, red);
+            sB = block_sum(sB, red);
+            sR = block_sum(sR, red);
+            top = block_max_d(top, red);
+            if (threadIdx.x == 0) {
+                emax_s = 0ull;
+                s_delta = 2.0 * (sqrt(sS) + sqrt(sB) * sqrt(sR));
+                s_low = kTau * top;
+            }
         }
         __syncthreads();
         {
@@ -384,7 +420,7 @@ oa_refine_kernel(const int *dn, int ld, const double *__restrict__ Cm, double *Z
         }
         if (!grid_barrier(bar, G, status, limit_cycles)) return;
         // (5) Z' = Z + Z E
-        for (int t = blockIdx.x; t < ntiles; t += G) tile_gemm<false>(b, ld, t / tb, t % tb, Zc, E, Zc, Zn, As, Bs);
+        for (int t = blockIdx.x; t < ntiles; t += G) tile_gemm_small<false>(b, ld, t / tbn, t % tbn, Zc, E, Zc, Zn);
         if (!grid_barrier(bar, G, status, limit_cycles)) return;
         double *tmp = Zc;
         Zc = Zn;
@@ -393,9 +429,9 @@ oa_refine_kernel(const int *dn, int ld, const double *__restrict__ Cm, double *Z
         if (m <= (unsigned long long)__double_as_longlong(kRefineDone)) break;
     }
     if (Zc != Z)  // leave the result in Z
-        for (int t = blockIdx.x; t < ntiles; t += G) {
-            const int i = (t / tb) * 16 + (threadIdx.x >> 4), j = (t % tb) * 16 + (threadIdx.x & 15);
-            if (i < b && j < b) Z[i * ld + j] = __ldcg(Zc + i * ld + j);
+        for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < b * b; idx += G * blockDim.x) {
+            const int r = idx / b, c = idx - r * b;
+            Z[r * ld + c] = __ldcg(Zc + r * ld + c);
         }
 }
 
@@ -528,7 +564,7 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
             long long lim = kBarrierLimitCycles;
             void *args[] = {(void *)&dn, &ldv, (void *)&cm, &Z, &Z2, &G, &T, &S, &E, &Pn, &lam_b, &em, &bar,
                             &d_status, &lim};
-            const int grid = std::min(refine_ctas, (int)((n + 15) / 16) * (int)((n + 15) / 16));
+            const int grid = std::min({refine_ctas, sms, FRPCA_MAX_L});  // 3 norm partials per CTA fit in Pn
             e = cudaLaunchCooperativeKernel((const void *)oa_refine_kernel, grid, 256, args, 0, s);
             if (e != cudaSuccess) return e;
             count_launch();
