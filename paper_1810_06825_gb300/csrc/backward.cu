@@ -188,32 +188,45 @@ sddmm_kernel(int64_t m, const int64_t *__restrict__ rowptr, const int32_t *__res
         lr[t] = vi < nvec ? Lv[vi] : Vec<T>::zero();
     }
     const int64_t start = rowptr[i], end = rowptr[i + 1];
-    for (int64_t base = start; base < end; base += 4) {
-        const int64_t e = base + sub;
-        const bool ok = e < end;
-        const int64_t j = ok ? colidx[e] : 0;
-        const V *rj = Rv + j * (ldf / W);
-        T dot = T(0);
+    // kBatch groups of four nonzeros per iteration: their column indices and R
+    // rows are all requested before any product, so the gathers overlap.
+    constexpr int kBatch = NV <= 2 ? 4 : NV <= 4 ? 2 : 1;
+    for (int64_t base = start; base < end; base += 4 * kBatch) {
+        int64_t e[kBatch];
+        const V *rj[kBatch];
 #pragma unroll
-        for (int t = 0; t < NV; ++t) {
-            const int vi = g + 8 * t;
-            if (vi < nvec) {
-                const V x = __ldg(rj + vi);
+        for (int u = 0; u < kBatch; ++u) {
+            e[u] = base + 4 * u + sub;
+            rj[u] = Rv + (int64_t)(e[u] < end ? colidx[e[u]] : 0) * (ldf / W);
+        }
+        V x[kBatch][NV];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+#pragma unroll
+            for (int t = 0; t < NV; ++t) {
+                const int vi = g + 8 * t;
+                x[u][t] = (vi < nvec && e[u] < end) ? __ldg(rj[u] + vi) : Vec<T>::zero();
+            }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            T dot = T(0);
+#pragma unroll
+            for (int t = 0; t < NV; ++t) {
                 if constexpr (W == 4) {
-                    dot = fma(lr[t].x, x.x, dot);
-                    dot = fma(lr[t].y, x.y, dot);
-                    dot = fma(lr[t].z, x.z, dot);
-                    dot = fma(lr[t].w, x.w, dot);
+                    dot = fma(lr[t].x, x[u][t].x, dot);
+                    dot = fma(lr[t].y, x[u][t].y, dot);
+                    dot = fma(lr[t].z, x[u][t].z, dot);
+                    dot = fma(lr[t].w, x[u][t].w, dot);
                 } else {
-                    dot = fma(lr[t].x, x.x, dot);
-                    dot = fma(lr[t].y, x.y, dot);
+                    dot = fma(lr[t].x, x[u][t].x, dot);
+                    dot = fma(lr[t].y, x[u][t].y, dot);
                 }
             }
+            dot += __shfl_xor_sync(0xffffffffu, dot, 1);
+            dot += __shfl_xor_sync(0xffffffffu, dot, 2);
+            dot += __shfl_xor_sync(0xffffffffu, dot, 4);
+            if (e[u] < end && g == 0) out[e[u]] = dot;
         }
-        dot += __shfl_xor_sync(0xffffffffu, dot, 1);
-        dot += __shfl_xor_sync(0xffffffffu, dot, 2);
-        dot += __shfl_xor_sync(0xffffffffu, dot, 4);
-        if (ok && g == 0) out[e] = dot;
     }
 }
 
