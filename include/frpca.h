@@ -77,6 +77,11 @@ typedef struct frpca_create_opts {
     int borrow;               /* on_device only: 1 = use the caller's arrays in place (they
                                  must stay valid until frpca_destroy); 0 = copy them        */
     int validate;             /* 1 = check the CSR structure (on the device), 0 = trust it  */
+    int hot_columns;          /* FP32 values only: the densest columns of A kept as a dense
+                                 block whose part of every pass runs on the tensor cores.
+                                 0 = automatic (columns holding >= 5% of the rows, up to
+                                 256, in multiples of 128), -1 = off, > 0 = that many
+                                 (rounded down to 128, at most 256)                       */
 } frpca_create_opts;
 
 /* Creates a handle.  csr may be NULL: the handle then serves only the

@@ -45,7 +45,8 @@ class frpca_csr(ctypes.Structure):
 
 
 class frpca_create_opts(ctypes.Structure):
-    _fields_ = [("stream", ctypes.c_void_p), ("borrow", ctypes.c_int), ("validate", ctypes.c_int)]
+    _fields_ = [("stream", ctypes.c_void_p), ("borrow", ctypes.c_int), ("validate", ctypes.c_int),
+                ("hot_columns", ctypes.c_int)]
 
 
 class frpca_run_opts(ctypes.Structure):
@@ -269,7 +270,7 @@ class FrPCA:
     are borrowed (kept alive by this object) and A^T is built on the device.
     """
 
-    def __init__(self, indptr, indices, values, shape, stream=None, borrow=True, validate=True):
+    def __init__(self, indptr, indices, values, shape, stream=None, borrow=True, validate=True, hot_columns=0):
         torch = _torch()
         _need_cuda(indptr, indices, values)
         self.m, self.n = int(shape[0]), int(shape[1])
@@ -283,7 +284,7 @@ class FrPCA:
                         values=self.values.data_ptr() if self.values.numel() else None,
                         dtype=_dtype_code(self.values), on_device=1)
         opts = frpca_create_opts(stream=self.stream.cuda_stream, borrow=1 if borrow else 0,
-                                 validate=1 if validate else 0)
+                                 validate=1 if validate else 0, hot_columns=int(hot_columns))
         self.handle = frpca_create(csr, opts)
 
     @classmethod

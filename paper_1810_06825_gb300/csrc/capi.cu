@@ -27,7 +27,8 @@ struct frpca_ctx {
     DevBuf alt_A, alt_AT;                        // values converted to the other dtype
     bool alt_ready = false;
     SpmmPlan planA, planAT;
-    DevBuf ws_q, ws_w, ws_spmm, ws_gram, ws_eig, ws_lu, ws_small, ws_sign, ws_scratch, ws_scan, ws_bwd;
+    DevBuf ws_q, ws_w, ws_spmm, ws_gram, ws_eig, ws_lu, ws_small, ws_sign, ws_scratch, ws_scan, ws_bwd, ws_hot;
+    HybridCSR hy;  // the densest columns of A as a dense block (FP32 SpMM on the tensor cores)
     std::string err;
     // instrumentation
     bool timing = false;
@@ -168,10 +169,29 @@ frpca_status spmm_pass(frpca_ctx *h, int trans, int l, const void *X, int64_t ld
     if (st != FRPCA_OK) return st;
     const DeviceCSR &C = trans ? h->AT : h->A;
     const SpmmPlan &P = trans ? h->planAT : h->planA;
-    CK(h->ws_spmm.ensure(std::max<size_t>(256, spmm_scratch_bytes(P, l, dt))), "alloc spmm scratch");
-    PhaseTimer t(h, PH_SPMM);
-    CK(launch_spmm(C, trans ? vat : va, P, l, X, ldx, Y, ldy, dt, h->ws_spmm.ptr, h->stream), "spmm launch");
-    t.done();
+    const bool hybrid = dt == FRPCA_F32 && h->hy.h > 0 && l <= 128;
+    if (hybrid) {
+        const SpmmPlan &Pc = trans ? h->hy.plan_t_cold : h->hy.plan_cold;
+        CK(h->ws_spmm.ensure(std::max<size_t>(256, spmm_scratch_bytes(Pc, l, dt))), "alloc spmm scratch");
+        CK(h->ws_hot.ensure(hybrid_workspace_bytes(h->A.rows, h->hy.h, h->num_sms)), "alloc hybrid workspace");
+        PhaseTimer t(h, PH_SPMM);
+        if (!trans) {  // A X = A_H X_H + A_cold X
+            CK(launch_hot_ax(h->hy, h->A.rows, l, (const float *)X, ldx, (float *)Y, ldy, h->ws_hot.ptr, h->num_sms,
+                             h->d_status, h->stream), "hot-column spmm launch");
+            CK(launch_spmm(h->hy.cold, h->hy.cold.vals, Pc, l, X, ldx, Y, ldy, dt, h->ws_spmm.ptr, h->stream,
+                           /*accumulate=*/true), "spmm launch");
+        } else {       // A^T X: rows of cold columns from the CSR of A^T, hot rows from A_H^T X
+            CK(launch_spmm(C, vat, Pc, l, X, ldx, Y, ldy, dt, h->ws_spmm.ptr, h->stream), "spmm launch");
+            CK(launch_hot_aty(h->hy, h->A.rows, l, (const float *)X, ldx, (float *)Y, ldy, h->ws_hot.ptr, h->num_sms,
+                              h->d_status, h->stream), "hot-column spmm launch");
+        }
+        t.done();
+    } else {
+        CK(h->ws_spmm.ensure(std::max<size_t>(256, spmm_scratch_bytes(P, l, dt))), "alloc spmm scratch");
+        PhaseTimer t(h, PH_SPMM);
+        CK(launch_spmm(C, trans ? vat : va, P, l, X, ldx, Y, ldy, dt, h->ws_spmm.ptr, h->stream), "spmm launch");
+        t.done();
+    }
     // Algorithmic bytes: CSR arrays once, input and output blocks once each.
     const double sv = (double)dsize(dt);
     h->acc.spmm_passes += 1;
@@ -457,6 +477,12 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
     if ((e = build_spmm_plan(h->A, h->planA, h->stream, perr)) != cudaSuccess ||
         (e = build_spmm_plan(h->AT, h->planAT, h->stream, perr)) != cudaSuccess)
         return bail(cuda_fail(h, e, perr.c_str()));
+    {
+        const int hc = opts ? opts->hot_columns : 0;
+        const int want = hc == 0 ? -1 : hc < 0 ? 0 : hc;
+        if ((e = build_hybrid(h->A, h->AT, want, h->hy, h->ws_scan, h->stream, perr)) != cudaSuccess)
+            return bail(cuda_fail(h, e, perr.empty() ? "hot-column block" : perr.c_str()));
+    }
     h->has_matrix = true;
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "synchronize"));
     *out = h;
@@ -469,9 +495,10 @@ frpca_status frpca_destroy(frpca_handle h) {
     else cudaDeviceSynchronize();
     h->planA.free_all();
     h->planAT.free_all();
+    h->hy.free_all();
     for (DevBuf *b : {&h->own_rowptr, &h->own_colidx, &h->own_vals, &h->t_rowptr, &h->t_colidx, &h->t_vals,
                       &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
-                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd})
+                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot})
         b->release();
     for (auto &mk : h->marks) {
         cudaEventDestroy(mk.a);
@@ -490,6 +517,7 @@ frpca_status frpca_refresh(frpca_handle h) {
     if (!h->has_matrix) return fail(h, FRPCA_ERR_INVALID_ARG, "handle has no matrix");
     PhaseTimer t(h, PH_TRANSPOSE);
     CK(csr_transpose(h->A, h->AT, h->ws_scratch, h->ws_scan, h->stream), "transpose");
+    CK(refresh_hybrid(h->A, h->hy, h->stream), "hot-column block");
     t.done();
     h->alt_ready = false;
     return FRPCA_OK;

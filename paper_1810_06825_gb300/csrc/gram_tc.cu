@@ -28,9 +28,12 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace frpca {
 namespace {
+
+using namespace tc;
 
 constexpr int kTcThreads = 256;
 constexpr int kTile = 128;                         // l padded to 128; rows per chunk
@@ -39,77 +42,6 @@ constexpr int kAccStride = kTile + 1;              // FP64 accumulator row strid
 constexpr int kAccBytes = kTile * kAccStride * 8;  // 132,096 bytes
 constexpr int kSmemBytes = 3 * kOpBytes + kAccBytes + 64;
 constexpr uint32_t kTmemCols = 256;                // two 128-column FP32 accumulators
-constexpr int kLbo = 2048, kSbo = 128;
-
-__device__ inline uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ inline uint64_t make_desc(uint32_t addr) {
-    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((kLbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((kSbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version of tcgen05; base offset 0, no swizzle
-    return d;
-}
-
-// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major,
-// N = 128 (bits 17-22 hold N >> 3), M = 128 (bits 24-28 hold M >> 4).
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTile >> 3) << 17) |
-                            ((uint32_t)(kTile >> 4) << 24);
-
-__device__ inline void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
-}
-
-__device__ inline void mma_commit(uint32_t mbar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                 : "memory");
-}
-
-__device__ inline bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ inline void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ inline void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ inline void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Byte offset of element (column j, row r) of a chunk in an operand buffer.
-__device__ inline int op_offset(int j, int r) { return (r >> 3) * kLbo + (j >> 3) * kSbo + (j & 7) * 16 + (r & 7) * 2; }
-
-// Splits x into three BF16 terms h + m + s == x.
-__device__ inline void split3(float x, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &s) {
-    h = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(h);
-    m = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(m);
-    s = __float2bfloat16_rn(r2);
-}
-
 // Thread t loads column group j4 = t % 32 (4 columns) of the 8-row groups
 // rg = t / 32 and rg + 8 of a chunk: 16 float4 loads, rows coalesced per warp.
 struct ChunkRegs {
@@ -209,12 +141,7 @@ gram_tc_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, double
             for (int ks = 0; ks < kTile / 16; ++ks) {
                 const uint32_t koff = (uint32_t)(2 * ks * kLbo);  // two core matrices per K-step of 16
                 const uint64_t h = make_desc(aH + koff), m = make_desc(aM + koff), s = make_desc(aS + koff);
-                mma_bf16(d_main, h, h, ks > 0);
-                mma_bf16(d_corr, h, m, ks > 0);
-                mma_bf16(d_corr, m, h, 1);
-                mma_bf16(d_corr, m, m, 1);
-                mma_bf16(d_corr, h, s, 1);
-                mma_bf16(d_corr, s, h, 1);
+                mma_split6(d_main, d_corr, h, m, s, h, m, s, ks > 0);
             }
             mma_commit(mb);
         }

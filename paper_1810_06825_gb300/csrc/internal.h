@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "frpca.h"
 
@@ -67,10 +68,13 @@ cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n
                                       cudaStream_t s);
 
 // ---- spmm.cu
-cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, std::string &err);
+// skip (optional, one flag per row): rows left out of the plan (their output
+// rows are not written).
+cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, std::string &err,
+                            const std::vector<char> *skip = nullptr);
 size_t spmm_scratch_bytes(const SpmmPlan &plan, int l, frpca_dtype dt);
 cudaError_t launch_spmm(const DeviceCSR &A, const void *vals, const SpmmPlan &plan, int l, const void *X,
-                        int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *scratch, cudaStream_t s);
+                        int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *scratch, cudaStream_t s, bool accumulate = false);
 
 // ---- capi.cu: message returned by frpca_last_error(NULL) on this thread
 void set_thread_error(const std::string &msg);
@@ -115,6 +119,30 @@ cudaError_t launch_scale_columns(int64_t R, int k, void *X, int64_t ld, frpca_dt
 size_t calu_workspace_bytes(int l);
 cudaError_t launch_calu(int64_t R, int l, float *M, int64_t ld, int64_t *piv, void *ws, int *d_status, int num_sms,
                         cudaStream_t s);
+
+// ---- spmm_tc.cu: the densest columns of A as a dense block on the tensor cores
+struct HybridCSR {
+    int h = 0;                     // hot columns (0: off), a multiple of 128
+    int32_t *hot_cols = nullptr;   // h column ids, densest first
+    int32_t *slot = nullptr;       // per column of A: its index among the hot columns, -1 if cold
+    float *dense = nullptr;        // m x h row-major: A on the hot columns (zeros kept)
+    DeviceCSR cold;                // A without the hot columns
+    SpmmPlan plan_cold;            // work list of the cold CSR
+    SpmmPlan plan_t_cold;          // work list of A^T without the rows of hot columns
+    DevBuf b_hot, b_slot, b_dense, b_crow, b_ccol, b_cval;
+    void free_all();
+};
+// want: -1 automatic, 0 off, > 0 that many columns (rounded down to 128).
+cudaError_t build_hybrid(const DeviceCSR &A, const DeviceCSR &AT, int want, HybridCSR &hy, DevBuf &scan_scratch,
+                         cudaStream_t s, std::string &err);
+cudaError_t refresh_hybrid(const DeviceCSR &A, HybridCSR &hy, cudaStream_t s);  // values changed, same structure
+size_t hybrid_workspace_bytes(int64_t m, int h, int sms);
+// Y = A_H X_H (overwrites Y's first round_up(l, 4) columns); l <= 128.
+cudaError_t launch_hot_ax(const HybridCSR &hy, int64_t m, int l, const float *X, int64_t ldx, float *Y, int64_t ldy,
+                          void *ws, int sms, int *d_status, cudaStream_t s);
+// Z[hot rows] = A_H^T Y; l <= 128.
+cudaError_t launch_hot_aty(const HybridCSR &hy, int64_t m, int l, const float *Y, int64_t ldy, float *Z, int64_t ldz,
+                           void *ws, int sms, int *d_status, cudaStream_t s);
 
 // ---- gram_tc.cu (split-BF16 Gram on the tcgen05 tensor cores, FP32 input)
 int gram_tc_max_l();

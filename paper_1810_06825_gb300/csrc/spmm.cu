@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(kThreads)
 spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, const T *__restrict__ vals,
             const int32_t *__restrict__ short_rows, int64_t n_short, const int64_t *__restrict__ seg_start,
             const int32_t *__restrict__ seg_len, int64_t n_segs, int nvec, const T *__restrict__ X, int64_t ldx,
-            T *__restrict__ Y, int64_t ldy, T *__restrict__ partial) {
+            T *__restrict__ Y, int64_t ldy, T *__restrict__ partial, int accumulate) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::width;
     const int lane = threadIdx.x & 31;
@@ -50,8 +50,14 @@ spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ coli
     const V *Xv = reinterpret_cast<const V *>(X);
     const int64_t ldxv = ldx / W;
     V acc[NV];
+    // accumulate: add to the row already in Y (whole rows only; segments of
+    // long rows are added to Y by the fix-up).
+    const bool add_y = accumulate && w < n_short;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = Vec<T>::zero();
+    for (int k = 0; k < NV; ++k) {
+        const int vi = lane + 32 * k;
+        acc[k] = (add_y && vi < nvec) ? out[vi] : Vec<T>::zero();
+    }
 
     for (int base = 0; base < len; base += 32) {
         const int cnt = min(32, len - base);
@@ -105,7 +111,7 @@ spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ coli
 template <typename T>
 __global__ void spmm_fixup_kernel(int64_t n_long, const int32_t *__restrict__ long_rows,
                                   const int64_t *__restrict__ long_first, int nvec, const T *__restrict__ partial,
-                                  T *__restrict__ Y, int64_t ldy) {
+                                  T *__restrict__ Y, int64_t ldy, int accumulate) {
     using V = typename Vec<T>::type;
     const int lane = threadIdx.x & 31;
     const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -114,15 +120,15 @@ __global__ void spmm_fixup_kernel(int64_t n_long, const int32_t *__restrict__ lo
     const V *P = reinterpret_cast<const V *>(partial);
     V *out = reinterpret_cast<V *>(Y + (int64_t)long_rows[r] * ldy);
     for (int vi = lane; vi < nvec; vi += 32) {
-        V acc = P[s0 * nvec + vi];
-        for (int64_t s = s0 + 1; s < s1; ++s) Vec<T>::add(acc, P[s * nvec + vi]);
+        V acc = accumulate ? out[vi] : Vec<T>::zero();
+        for (int64_t s = s0; s < s1; ++s) Vec<T>::add(acc, P[s * nvec + vi]);
         out[vi] = acc;
     }
 }
 
 template <typename T>
 cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmPlan &p, int l, const T *X, int64_t ldx, T *Y,
-                         int64_t ldy, T *partial, cudaStream_t s) {
+                         int64_t ldy, T *partial, bool accumulate, cudaStream_t s) {
     constexpr int W = Vec<T>::width;
     const int nvec = (int)ceil_div(l, W);
     const int nv = (int)ceil_div(nvec, 32);
@@ -133,7 +139,7 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmPlan &p, i
     case NVV:                                                                                                 \
         spmm_kernel<T, NVV><<<(unsigned)blocks, kThreads, 0, s>>>(A.rowptr, A.colidx, vals, p.short_rows,     \
                                                                   p.n_short, p.seg_start, p.seg_len,          \
-                                                                  p.n_segs, nvec, X, ldx, Y, ldy, partial); count_launch();   \
+                                                                  p.n_segs, nvec, X, ldx, Y, ldy, partial, accumulate); count_launch();   \
         break;
         switch (nv) {
             FRPCA_SPMM_CASE(1)
@@ -149,7 +155,7 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmPlan &p, i
     if (p.n_long > 0) {
         spmm_fixup_kernel<T><<<(unsigned)ceil_div(p.n_long * 32, 256), 256, 0, s>>>(p.n_long, p.long_rows,
                                                                                    p.long_first, nvec, partial,
-                                                                                   Y, ldy); count_launch();
+                                                                                   Y, ldy, accumulate); count_launch();
         return cudaGetLastError();
     }
     return cudaSuccess;
@@ -171,7 +177,8 @@ void SpmmPlan::free_all() {
     n_short = n_segs = n_long = 0;
 }
 
-cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, std::string &err) {
+cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, std::string &err,
+                            const std::vector<char> *skip) {
     plan.free_all();
     plan.seg = kDefaultSeg;
     std::vector<int64_t> rp((size_t)A.rows + 1);
@@ -185,6 +192,7 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
     std::vector<int64_t> sstart, lfirst;
     shorts.reserve((size_t)A.rows);
     for (int64_t i = 0; i < A.rows; ++i) {
+        if (skip && (*skip)[(size_t)i]) continue;
         const int64_t len = rp[i + 1] - rp[i];
         if (len <= plan.seg) {
             shorts.push_back((int32_t)i);
@@ -224,12 +232,13 @@ size_t spmm_scratch_bytes(const SpmmPlan &plan, int l, frpca_dtype dt) {
 }
 
 cudaError_t launch_spmm(const DeviceCSR &A, const void *vals, const SpmmPlan &plan, int l, const void *X,
-                        int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *scratch, cudaStream_t s) {
+                        int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *scratch, cudaStream_t s,
+                        bool accumulate) {
     if (dt == FRPCA_F32)
         return launch_typed<float>(A, (const float *)vals, plan, l, (const float *)X, ldx, (float *)Y, ldy,
-                                   (float *)scratch, s);
+                                   (float *)scratch, accumulate, s);
     return launch_typed<double>(A, (const double *)vals, plan, l, (const double *)X, ldx, (double *)Y, ldy,
-                                (double *)scratch, s);
+                                (double *)scratch, accumulate, s);
 }
 
 }  // namespace frpca

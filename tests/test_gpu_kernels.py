@@ -98,6 +98,13 @@ def _spmm_bound(A, X, trans, eps):
     f = oracle.spmm_t if trans else oracle.spmm
     mag = f(Aabs.m, Aabs.n, Aabs.indptr, Aabs.indices, Aabs.data, np.abs(X))
     deg = np.diff(A.indptr) if not trans else np.bincount(A.indices, minlength=A.n)
+    if eps == EPS32:
+        # FP32 matrices keep their densest columns as a dense block on the
+        # tensor cores: FP32 accumulation rounds once per 16-column K-step with
+        # a nonzero product (at most once per entry) on top of the CSR order's
+        # rounding, plus the split remainder (< 2^-26 per product) and the sums
+        # of the correction accumulator and of the cold part.
+        return (2 * deg[:, None] + 8) * eps * mag + 1e-300
     return (deg[:, None] + 2) * eps * mag + 1e-300
 
 
@@ -118,6 +125,49 @@ def test_spmm_matches_oracle(idx, l, dtype, trans):
     eps = EPS64 if dtype == np.float64 else EPS32
     bound = _spmm_bound(A, X.astype(np.float64), trans, eps)
     assert np.all(np.abs(Y - ref) <= bound)
+    mat.close()
+
+
+def _hot_matrix(m, n, seed):
+    """Power-law CSR whose densest columns hold 5-60 % of the rows."""
+    return synthetic.powerlaw_csr(m, n, 40, 1.1, "tfidf", seed=seed, dtype=np.float32)
+
+
+@pytest.mark.parametrize("hot", [-1, 0, 128, 256])
+@pytest.mark.parametrize("l", [1, 48, 120, 128])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_spmm_hot_columns_match_oracle(hot, l, trans):
+    """A X and A^T X with the densest columns on the tensor cores (forced
+    block sizes, automatic, and off) against the oracle; rows of A^T at hot
+    columns come from the dense block, the rest from the CSR of A^T."""
+    A = _hot_matrix(9000, 2500, 3)
+    mat = frpca.FrPCA.from_csr(A, device=DEV, hot_columns=hot)
+    X = np.random.default_rng(l + trans).standard_normal((A.m if trans else A.n, l)).astype(np.float32)
+    Xg = frpca.empty_block(X.shape[0], l, torch.float32, DEV)
+    Xg.copy_(torch.from_numpy(X))
+    Y = _cpu(mat.spmm(Xg, trans=bool(trans)))
+    f = oracle.spmm_t if trans else oracle.spmm
+    ref = f(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64), X.astype(np.float64))
+    assert np.all(np.abs(Y - ref) <= _spmm_bound(A, X.astype(np.float64), trans, EPS32))
+    mat.close()
+
+
+def test_spmm_hot_columns_refresh_and_determinism():
+    """After the values change in place, frpca_refresh rebuilds the dense block
+    and the cold values; results stay deterministic."""
+    A = _hot_matrix(6000, 1200, 4)
+    vals = torch.tensor(A.data, device=DEV)
+    mat = frpca.FrPCA(torch.tensor(A.indptr, device=DEV), torch.tensor(A.indices, device=DEV), vals, (A.m, A.n),
+                      hot_columns=128)
+    X = frpca.empty_block(A.n, 64, torch.float32, DEV)
+    X.copy_(torch.randn(A.n, 64, generator=torch.Generator().manual_seed(0)))
+    Y1 = mat.spmm(X).clone()
+    with torch.no_grad():
+        vals.mul_(3.0)
+    mat.refresh()
+    Y3 = mat.spmm(X).clone()
+    assert torch.allclose(Y3, 3.0 * Y1, rtol=1e-5, atol=1e-5 * float(Y1.abs().max()))
+    assert torch.equal(mat.spmm(X), Y3)
     mat.close()
 
 
