@@ -78,10 +78,12 @@ typedef struct frpca_create_opts {
                                  must stay valid until frpca_destroy); 0 = copy them        */
     int validate;             /* 1 = check the CSR structure (on the device), 0 = trust it  */
     int hot_columns;          /* FP32 values only: the densest columns of A kept as a dense
-                                 block whose part of every pass runs on the tensor cores.
-                                 0 = automatic (columns holding >= 5% of the rows, up to
-                                 256, in multiples of 128), -1 = off, > 0 = that many
-                                 (rounded down to 128, at most 256)                       */
+                                 block whose part of every pass runs on the tensor cores
+                                 (split-BF16) while the rest stays on the CSR kernel.
+                                 0 = off (the default: on the power-law workloads the CSR
+                                 kernel alone is faster), -1 = automatic (columns holding
+                                 >= 5% of the rows, up to 256, in multiples of 128), > 0 =
+                                 that many (rounded down to 128, at most 256)              */
 } frpca_create_opts;
 
 /* Creates a handle.  csr may be NULL: the handle then serves only the

@@ -268,6 +268,9 @@ class FrPCA:
     ``indptr`` (int64, m+1), ``indices`` (int32, nnz, sorted and unique per
     row) and ``values`` (float32/float64, nnz) are CUDA tensors; by default they
     are borrowed (kept alive by this object) and A^T is built on the device.
+    ``hot_columns``: 0 keeps every nonzero on the CSR kernel; -1 picks the
+    densest columns automatically and > 0 that many (multiples of 128, at most
+    256) for a dense block whose share of each pass runs on the tensor cores.
     """
 
     def __init__(self, indptr, indices, values, shape, stream=None, borrow=True, validate=True, hot_columns=0):

@@ -479,7 +479,7 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
         return bail(cuda_fail(h, e, perr.c_str()));
     {
         const int hc = opts ? opts->hot_columns : 0;
-        const int want = hc == 0 ? -1 : hc < 0 ? 0 : hc;
+        const int want = hc < 0 ? -1 : hc;  // -1 automatic, 0 off, > 0 a count
         if ((e = build_hybrid(h->A, h->AT, want, h->hy, h->ws_scan, h->stream, perr)) != cudaSuccess)
             return bail(cuda_fail(h, e, perr.empty() ? "hot-column block" : perr.c_str()));
     }

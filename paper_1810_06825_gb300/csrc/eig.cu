@@ -54,17 +54,78 @@ __device__ inline int dim_of(const int *dn, int n_static) { return dn ? *dn : n_
 // convergent, and its orthogonality error (a few ulps) is removed by the
 // double-precision refinement that follows.
 //
-// The round is bound by shared-memory traffic and instruction issue in one
-// SM, so the work is split over gridDim.x CTAs without any communication:
-// every CTA runs the same deterministic sequence of rotations on its own copy
-// of A (only the upper triangle is updated) and accumulates only its own
-// slice of the rows of V (one or two rows each with 60 CTAs).  Each thread's
-// items (2 x 2 blocks of A, entries of V) are fixed for the whole kernel and
-// kept in registers; NI = items per thread.
+// Systolic layout (Brent and Luk's array for the round-robin ordering): the
+// n_p = n + (n odd) indices sit in slots, and in every round pair k rotates
+// slots (2k, 2k+1).  After the round the slots move one step along the cycle
+// top_1 .. top_{nb-1}, bottom_{nb-1} .. bottom_0 (top_k = slot 2k, bottom_k =
+// slot 2k + 1; slot 0 stays), which pairs every two indices once per sweep of
+// n_p - 1 rounds and brings every index back to its own slot at the end of a
+// sweep.  A thread keeps its 2 x 2 blocks (ka, kb), ka <= kb, of the upper
+// triangle in registers; the update J^T A J is register arithmetic and the
+// move goes through four shared-memory planes (entry (x, y) of every block)
+// that each thread writes at its own block and reads where its entries come
+// from.  Blocks are numbered along the diagonals d = kb - ka, so the stores
+// of a warp are contiguous and the moves along the diagonal are shifts by one.
+//
+// The rotations come from the diagonal blocks, whose next values depend only
+// on the blocks of diagonals 0, 1 and 2: dedicated warps own the diagonal
+// blocks, the blocks of diagonals 1 and 2 are the first items of the warps
+// after them, and named barriers let the diagonal warps collect their entries
+// and compute the next round's rotations (into the other half of a
+// double-buffered table) while the remaining warps still move theirs.
+//
+// The work is split over gridDim.x CTAs without any communication: every CTA
+// runs the same deterministic sequence of rotations on its own copy of A and
+// accumulates only its own slice of the rows of V (one or two rows each with
+// 60 CTAs), whose (row, pair) entries move through two more planes.  NI =
+// items (blocks of A, entries of V) per thread outside the diagonal warps.
+constexpr int kJacobiMaxNb = FRPCA_MAX_L / 2;
+constexpr int kJacobiPlane = kJacobiMaxNb * (kJacobiMaxNb + 1) / 2;  // one plane: an entry of every block
+
+// Slot whose content moves into slot s at the end of a round.
+__device__ inline int jacobi_src_slot(int s, int nb) {
+    if (nb == 1) return s;
+    const int k = s >> 1;
+    if ((s & 1) == 0) return k == 0 ? 0 : k == 1 ? 1 : 2 * (k - 1);
+    return k == nb - 1 ? 2 * (nb - 1) : 2 * (k + 1) + 1;
+}
+
+// Position of block (a, b), a <= b, in a plane: diagonal-major.
+__device__ inline int jacobi_block_index(int a, int b, int nb) {
+    const int d = b - a;
+    return d * nb - d * (d - 1) / 2 + a;
+}
+
+__device__ inline void bar_sync_named(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ inline void bar_arrive_named(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Rotation (c, s) that annihilates a_pq of a diagonal block; 1 when it rotates.
+__device__ inline int jacobi_rotation(float app, float apq, float aqq, float2 &out) {
+    float c = 1.0f, sn = 0.0f;
+    int did = 0;
+    if (apq != 0.0f && apq * apq > 0x1p-46f * fabsf(app * aqq)) {
+        const float tau = __fdividef(aqq - app, 2.0f * apq);
+        const float at = fabsf(tau);
+        const float h = fmaf(tau, tau, 1.0f);
+        const float t = at < 1e18f ? copysignf(__fdividef(1.0f, at + h * rsqrtf(h)), tau) : __fdividef(0.5f, tau);
+        c = rsqrtf(fmaf(t, t, 1.0f));
+        sn = t * c;
+        did = 1;
+    }
+    out = make_float2(c, sn);
+    return did;
+}
+
+__host__ __device__ inline int jacobi_diag_threads(int nb) { return 32 * ((nb + 31) / 32); }
+
 template <int NI>
 __global__ void __launch_bounds__(kJacobiThreads, 1)
 jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int ld, double *__restrict__ X) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) float smem_f[];
     const int n = dim_of(dn, n_static);
     if (n < 1) return;
     const int np = n + (n & 1);
@@ -73,139 +134,192 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
     const int vrows = (np + gridDim.x - 1) / gridDim.x;
     const int v0 = blockIdx.x * vrows;
     const int vcnt = max(0, min(vrows, np - v0));
-    const int lda = np + 1;  // odd row strides: fewer shared-memory bank conflicts
-    float *A = reinterpret_cast<float *>(smem_raw);
-    float *V = A + np * lda;  // rows v0 .. v0 + vcnt - 1 of V, stride lda
-    __shared__ float4 rot[FRPCA_MAX_L / 2];  // (c, s, p, q) of each pair, one 16-byte load
-    __shared__ unsigned long long maxdiag;   // bit pattern of max |B_ii| (monotone)
+    const int vpl = vrows * nb;   // one plane of V: entry (row, pair k)
+    float *P = smem_f;            // planes (x, y) at P + (2x + y) kJacobiPlane
+    float *VP = P + 4 * kJacobiPlane;  // V planes top / bottom at VP + x vpl
+    __shared__ float2 rot[2][FRPCA_MAX_L / 2];  // (c, s) per pair, by round parity
+    __shared__ unsigned long long maxdiag;      // bit pattern of max |B_ii| (monotone)
     __shared__ double scale;
+    const int t = threadIdx.x;
+    // Threads [0, dthreads) own the diagonal blocks, one each; the others own
+    // the off-diagonal blocks in diagonal-major order, then the V entries.
+    // The "producer" warps hold the blocks of diagonals 1 and 2.
+    const int dthreads = jacobi_diag_threads(nb);
+    const int othreads = kJacobiThreads - dthreads;
+    const bool dwarp = t < dthreads;
+    const int prod_threads = 32 * ((min(max(0, 2 * nb - 3), othreads) + 31) / 32);
+    const int xcount = dthreads + prod_threads;
+    const bool producer = !dwarp && t - dthreads < prod_threads;
 
-    if (threadIdx.x == 0) maxdiag = 0ull;
+    if (t == 0) maxdiag = 0ull;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += kJacobiThreads)
+    for (int i = t; i < n; i += kJacobiThreads)
         atomicMax(&maxdiag, (unsigned long long)__double_as_longlong(B[i * ld + i]) & 0x7fffffffffffffffull);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (t == 0) {
         const double m = __longlong_as_double((long long)maxdiag);
         scale = (m > 0.0 && isfinite(m)) ? 1.0 / m : 1.0;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < np * np; idx += kJacobiThreads) {
-        const int i = idx / np, j = idx - i * np;
-        A[i * lda + j] = (i < n && j < n) ? (float)(B[i * ld + j] * scale) : 0.0f;
-    }
-    for (int idx = threadIdx.x; idx < vcnt * np; idx += kJacobiThreads) {
-        const int i = v0 + idx / np, j = idx % np;
-        V[(idx / np) * lda + j] = (i == j) ? 1.0f : 0.0f;
-    }
-    // This thread's items: kind 0 = block (ka, kb) of pairs, ka <= kb;
-    // kind 1 = entry (row, pair k) of the V slice; -1 = none.
-    int kind[NI], ia[NI], ib[NI];
+    const double sc = scale;
+    // Items: kind 0 = off-diagonal block, 1 = diagonal block (entries 00, 01,
+    // 11), 2 = (row, pair) of the V slice, 3 = none.  own = offset in its
+    // planes; g = where each entry comes from after the move.
+    int kind[NI], own[NI], ra[NI], rb[NI], g[NI][4];
+    float v[NI][4];
 #pragma unroll
     for (int u = 0; u < NI; ++u) {
-        int idx = threadIdx.x + u * kJacobiThreads;
-        kind[u] = -1;
-        ia[u] = 0;
-        ib[u] = 0;
-        if (idx < nblk) {
-            int a = 0;
-            while (idx >= nb - a) {
-                idx -= nb - a;
-                ++a;
+        kind[u] = 3;
+        own[u] = 0;
+        ra[u] = rb[u] = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            g[u][e] = 0;
+            v[u][e] = 0.0f;
+        }
+        int a = -1, b = -1, vidx = -1;
+        if (dwarp) {
+            if (u == 0 && t < nb) {
+                a = b = t;
+                kind[u] = 1;
             }
-            kind[u] = 0;
-            ia[u] = a;
-            ib[u] = a + idx;
-        } else if (idx < nblk + vcnt * nb) {
-            const int v = idx - nblk;
-            kind[u] = 1;
-            ia[u] = v / nb;
-            ib[u] = v - (v / nb) * nb;
+        } else {
+            const int j = (t - dthreads) + u * othreads;
+            if (j < nblk - nb) {
+                int w = j, d = 1;
+                while (w >= nb - d) {
+                    w -= nb - d;
+                    ++d;
+                }
+                a = w;
+                b = w + d;
+                kind[u] = 0;
+            } else if (j < nblk - nb + vcnt * nb) {
+                vidx = j - (nblk - nb);
+            }
+        }
+        if (a >= 0) {
+            ra[u] = a;
+            rb[u] = b;
+            own[u] = jacobi_block_index(a, b, nb);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int x = e >> 1, y = e & 1;
+                const int i2 = 2 * a + x, j2 = 2 * b + y;
+                if (i2 < n && j2 < n) v[u][e] = (float)(B[i2 * ld + j2] * sc);
+                const int si = jacobi_src_slot(i2, nb), sj = jacobi_src_slot(j2, nb);
+                const int lo = min(si, sj), hi = max(si, sj);
+                g[u][e] = (2 * (lo & 1) + (hi & 1)) * kJacobiPlane + jacobi_block_index(lo >> 1, hi >> 1, nb);
+            }
+        } else if (vidx >= 0) {
+            const int row = vidx / nb, k = vidx - row * nb;
+            kind[u] = 2;
+            ra[u] = rb[u] = k;
+            own[u] = row * nb + k;
+            v[u][0] = (v0 + row == 2 * k) ? 1.0f : 0.0f;
+            v[u][1] = (v0 + row == 2 * k + 1) ? 1.0f : 0.0f;
+            const int s0 = jacobi_src_slot(2 * k, nb), s1 = jacobi_src_slot(2 * k + 1, nb);
+            g[u][0] = (s0 & 1) * vpl + row * nb + (s0 >> 1);
+            g[u][1] = (s1 & 1) * vpl + row * nb + (s1 >> 1);
         }
     }
-
+    if (kind[0] == 1) {
+        float2 o;
+        jacobi_rotation(v[0][0], v[0][1], v[0][3], o);
+        rot[0][ra[0]] = o;
+    }
+    __syncthreads();
+    // The rotations of round r + 1 are computed during round r, so the
+    // convergence test looks at the rounds 1 .. n_p - 1 of each sweep plus
+    // round 0 of the next: any n_p - 1 consecutive rounds visit every pair once.
+    int cur = 0;
     for (int sweep = 0; sweep < kJacobiMaxSweeps; ++sweep) {
         int rotated = 0;
         for (int r = 0; r < m1; ++r) {
-            __syncthreads();
-            if ((int)threadIdx.x < nb) {
-                // Pair k of round r of the round-robin ordering.
-                const int k = threadIdx.x;
-                int a = m1, b = r;
-                if (k > 0) {
-                    a = r + k;
-                    if (a >= m1) a -= m1;
-                    b = r - k;
-                    if (b < 0) b += m1;
-                }
-                const int p = min(a, b), q = max(a, b);
-                float c = 1.0f, sn = 0.0f;
-                if (q < n) {
-                    const float apq = A[p * lda + q], app = A[p * lda + p], aqq = A[q * lda + q];
-                    if (apq != 0.0f && apq * apq > 0x1p-46f * fabsf(app * aqq)) {
-                        const float tau = __fdividef(aqq - app, 2.0f * apq);
-                        const float at = fabsf(tau);
-                        const float h = fmaf(tau, tau, 1.0f);
-                        const float t = at < 1e18f ? copysignf(__fdividef(1.0f, at + h * rsqrtf(h)), tau)
-                                                   : __fdividef(0.5f, tau);
-                        c = rsqrtf(fmaf(t, t, 1.0f));
-                        sn = t * c;
-                        rotated = 1;
-                    }
-                }
-                rot[k] = make_float4(c, sn, __int_as_float(p), __int_as_float(q));
-            }
-            __syncthreads();
+            const float2 *R = rot[cur];
 #pragma unroll
             for (int u = 0; u < NI; ++u) {
                 if (kind[u] == 0) {
-                    // A <- J^T A J on the 2x2 block of pairs (ka, kb), upper triangle.
-                    const int ka = ia[u], kb = ib[u];
-                    const float4 ra = rot[ka], rb = rot[kb];
-                    const float ca = ra.x, sa = ra.y, cb = rb.x, sb = rb.y;
-                    if (sa == 0.0f && sb == 0.0f) continue;
-                    const int pa = __float_as_int(ra.z), qa = __float_as_int(ra.w);
-                    const int pb = __float_as_int(rb.z), qb = __float_as_int(rb.w);
-                    const int i11 = min(pa, pb) * lda + max(pa, pb), i12 = min(pa, qb) * lda + max(pa, qb);
-                    const int i21 = min(qa, pb) * lda + max(qa, pb), i22 = min(qa, qb) * lda + max(qa, qb);
-                    const float a11 = A[i11], a12 = A[i12], a21 = A[i21], a22 = A[i22];
+                    // A <- J^T A J on the 2 x 2 block of pairs (ka, kb).
+                    const float2 rA = R[ra[u]], rB = R[rb[u]];
+                    const float ca = rA.x, sa = rA.y, cb = rB.x, sb = rB.y;
+                    const float a11 = v[u][0], a12 = v[u][1], a21 = v[u][2], a22 = v[u][3];
                     const float t11 = ca * a11 - sa * a21, t12 = ca * a12 - sa * a22;
                     const float t21 = sa * a11 + ca * a21, t22 = sa * a12 + ca * a22;
-                    A[i11] = t11 * cb - t12 * sb;
-                    A[i22] = t21 * sb + t22 * cb;
-                    if (ka == kb) {
-                        A[i12] = 0.0f;  // (pa, qa): the rotation annihilates it
-                    } else {
-                        A[i12] = t11 * sb + t12 * cb;
-                        A[i21] = t21 * cb - t22 * sb;
-                    }
+                    float *q = P + own[u];
+                    q[0] = t11 * cb - t12 * sb;
+                    q[kJacobiPlane] = t11 * sb + t12 * cb;
+                    q[2 * kJacobiPlane] = t21 * cb - t22 * sb;
+                    q[3 * kJacobiPlane] = t21 * sb + t22 * cb;
                 } else if (kind[u] == 1) {
-                    // V <- V J, one row of this CTA's slice and one pair.
-                    const float4 rk = rot[ib[u]];
-                    const float c = rk.x, sn = rk.y;
-                    if (sn == 0.0f) continue;
-                    const int p = __float_as_int(rk.z), q = __float_as_int(rk.w);
-                    float *vr = V + ia[u] * lda;
-                    const float x = vr[p], y = vr[q];
-                    vr[p] = c * x - sn * y;
-                    vr[q] = sn * x + c * y;
+                    const float2 rA = R[ra[u]];
+                    const float ca = rA.x, sa = rA.y;
+                    const float a11 = v[u][0], a12 = v[u][1], a22 = v[u][3];
+                    const float t11 = ca * a11 - sa * a12, t12 = ca * a12 - sa * a22;
+                    const float t21 = sa * a11 + ca * a12, t22 = sa * a12 + ca * a22;
+                    float *q = P + own[u];
+                    q[0] = t11 * ca - t12 * sa;
+                    q[kJacobiPlane] = 0.0f;  // (p, q): the rotation annihilates it
+                    q[3 * kJacobiPlane] = t21 * sa + t22 * ca;
+                } else if (kind[u] == 2) {
+                    // V <- V J for one row of this CTA's slice and one pair.
+                    const float2 rk = R[ra[u]];
+                    const float x = v[u][0], y = v[u][1];
+                    VP[own[u]] = rk.x * x - rk.y * y;
+                    VP[vpl + own[u]] = rk.y * x + rk.x * y;
                 }
             }
+            if (dwarp) {
+                bar_arrive_named(1, kJacobiThreads);  // this warp's entries are written
+                bar_sync_named(2, xcount);            // and so are the producers'
+                if (kind[0] == 1) {
+                    v[0][0] = P[g[0][0]];
+                    v[0][1] = P[g[0][1]];
+                    v[0][3] = P[g[0][3]];
+                    float2 o;
+                    rotated |= jacobi_rotation(v[0][0], v[0][1], v[0][3], o);
+                    rot[cur ^ 1][ra[0]] = o;
+                }
+            } else {
+                if (producer) bar_arrive_named(2, xcount);
+                bar_sync_named(1, kJacobiThreads);
+                // The move: every entry to its slot of the next round.
+#pragma unroll
+                for (int u = 0; u < NI; ++u) {
+                    if (kind[u] == 0) {
+                        v[u][0] = P[g[u][0]];
+                        v[u][1] = P[g[u][1]];
+                        v[u][2] = P[g[u][2]];
+                        v[u][3] = P[g[u][3]];
+                    } else if (kind[u] == 2) {
+                        v[u][0] = VP[g[u][0]];
+                        v[u][1] = VP[g[u][1]];
+                    }
+                }
+            }
+            bar_sync_named(3, kJacobiThreads);
+            cur ^= 1;
         }
+        // After a whole sweep every index is back in its own slot.
         if (!__syncthreads_or(rotated)) break;
     }
-    for (int idx = threadIdx.x; idx < vcnt * n; idx += kJacobiThreads) {
-        const int r = idx / n, j = idx - r * n;
-        if (v0 + r < n) X[(v0 + r) * ld + j] = (double)V[r * lda + j];
+#pragma unroll
+    for (int u = 0; u < NI; ++u) {
+        if (kind[u] != 2) continue;
+        const int row = own[u] / nb, k = ra[u], i = v0 + row;
+        if (i >= n) continue;
+        if (2 * k < n) X[i * ld + 2 * k] = (double)v[u][0];
+        if (2 * k + 1 < n) X[i * ld + 2 * k + 1] = (double)v[u][1];
     }
 }
 
-// Items per thread for a Jacobi launch on blocks of at most n (the deflated
-// levels are smaller), and the matching kernel.
+// Items per thread outside the diagonal warps for a Jacobi launch on blocks
+// of at most n (the deflated levels are smaller), and the matching kernel.
 int jacobi_items(int n) {
     const int np = n + (n & 1), nb = np / 2;
     const int vrows = (np + kJacobiCtas - 1) / kJacobiCtas;
-    return (int)ceil_div(nb * (nb + 1) / 2 + vrows * nb, kJacobiThreads);
+    const int othreads = kJacobiThreads - jacobi_diag_threads(nb);
+    return (int)ceil_div(nb * (nb + 1) / 2 - nb + vrows * nb, othreads);
 }
 
 // C (M x N) = op(A) (M x K) * Bm (K x N) (+ Cadd); all row-major with leading
@@ -532,7 +646,7 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
     if (e != cudaSuccess) return e;
     const int np = n + (n & 1);
     const int vrows = (np + kJacobiCtas - 1) / kJacobiCtas;
-    const size_t smem = sizeof(float) * ((size_t)np * (np + 1) + (size_t)vrows * (np + 1));
+    const size_t smem = sizeof(float) * (4 * (size_t)kJacobiPlane + 2 * (size_t)vrows * (np / 2));
     const int items = jacobi_items(n);
     void (*jacobi)(const int *, int, const double *, int, double *) =
         items <= 2 ? jacobi_f32_kernel<2> : items <= 3 ? jacobi_f32_kernel<3> : jacobi_f32_kernel<4>;

@@ -107,17 +107,67 @@ __global__ void xhot_prep_kernel(int h, int l, const float *__restrict__ X, int6
     *reinterpret_cast<uint4 *>(xs + (3 * c + 2) * kOpAx + off) = *reinterpret_cast<const uint4 *>(ss);
 }
 
+// Registers holding one A_H chunk for a thread: items (row, 8-slot group)
+// t, t + 256, t + 512, t + 768 of the 128 x 64 chunk.
+struct AxRegs {
+    float4 v[4][2];
+};
+
+__device__ inline void load_ax(const float *__restrict__ dense, int64_t m, int h, int64_t row0, int c, AxRegs &a) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int it = t + u * kHotThreads;
+        const int r = it / (kKc / 8), g = it % (kKc / 8);
+        const int64_t row = row0 + r;
+        float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+        if (row < m) {
+            const float4 *src = reinterpret_cast<const float4 *>(dense + row * h + c * kKc + 8 * g);
+            x0 = __ldcs(src);
+            x1 = __ldcs(src + 1);
+        }
+        a.v[u][0] = x0;
+        a.v[u][1] = x1;
+    }
+}
+
+__device__ inline void store_ax(const AxRegs &a, unsigned char *stage) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int it = t + u * kHotThreads;
+        const int r = it / (kKc / 8), g = it % (kKc / 8);
+        const float4 x0 = a.v[u][0], x1 = a.v[u][1];
+        const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        __align__(16) __nv_bfloat16 hh[8], mm[8], ss[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) split3(xv[k], hh[k], mm[k], ss[k]);
+        const int off = op_offset(r, 8 * g);
+        *reinterpret_cast<uint4 *>(stage + 0 * kOpAx + off) = *reinterpret_cast<const uint4 *>(hh);
+        *reinterpret_cast<uint4 *>(stage + 1 * kOpAx + off) = *reinterpret_cast<const uint4 *>(mm);
+        *reinterpret_cast<uint4 *>(stage + 2 * kOpAx + off) = *reinterpret_cast<const uint4 *>(ss);
+    }
+}
+
+__device__ inline void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
 // Y[rows of tile] = A_H[rows, :] X_H for 128-row tiles (persistent CTAs).  The
-// A operand (M = row, K = slot) is K-major as stored; per chunk of 64 slots a
+// A operand (M = row, K = slot) is K-major as stored: per chunk of 64 slots a
 // thread turns 8 consecutive floats of a row into three 16-byte core-matrix
-// rows.  Chunks are double-buffered: the staging of chunk c+1 overlaps the
-// MMAs of chunk c.  Columns l .. round_up(l, 4) - 1 of Y receive zeros.
+// rows.  The next chunk of A_H is loaded into registers while the current one
+// is split, X_H's chunk (already split) is copied with cp.async, and stages
+// are double-buffered, so loads overlap the MMAs.  The tile's result goes
+// through shared memory to coalesced row writes.  Columns l ..
+// round_up(l, 4) - 1 of Y receive zeros.
 __global__ void __launch_bounds__(kHotThreads, 1)
 hot_ax_kernel(int64_t m, int h, const float *__restrict__ dense, const unsigned char *__restrict__ xs, int l,
               float *__restrict__ Y, int64_t ldy, int *status, long long limit_cycles) {
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 2 * kStageAx);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
+    float *otile = reinterpret_cast<float *>(smem);  // 128 x 129 floats, over stage 0 after the MMAs
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
     if (warp == 0) tmem_alloc(tmem_slot, 256);
     if (t == 0) {
@@ -134,6 +184,8 @@ hot_ax_kernel(int64_t m, int h, const float *__restrict__ dense, const unsigned 
     const int lcols = (int)round_up(l, 4);
     uint32_t uses[2] = {0u, 0u};  // commits to each buffer's mbarrier so far
     bool ok = true;
+    AxRegs areg;
+    if ((int64_t)blockIdx.x < ntiles) load_ax(dense, m, h, (int64_t)blockIdx.x * kRowsTile, 0, areg);
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const int64_t row0 = tile * kRowsTile;
         int last = 0;
@@ -145,31 +197,16 @@ hot_ax_kernel(int64_t m, int h, const float *__restrict__ dense, const unsigned 
                 const bool done = mbar_wait_bounded(smem_u32(mbar + b), (uses[b] - 1) & 1, limit_cycles);
                 if (!__syncthreads_and(done)) { ok = false; break; }
             }
-            // A_H chunk: 128 rows x 64 slots; item = (row, 8-slot group).
-            for (int it = t; it < kRowsTile * (kKc / 8); it += kHotThreads) {
-                const int r = it / (kKc / 8), g = it % (kKc / 8);
-                const int64_t row = row0 + r;
-                float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-                if (row < m) {
-                    const float4 *src = reinterpret_cast<const float4 *>(dense + row * h + c * kKc + 8 * g);
-                    x0 = __ldcs(src);
-                    x1 = __ldcs(src + 1);
-                }
-                const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-                __align__(16) __nv_bfloat16 hh[8], mm[8], ss[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) split3(xv[k], hh[k], mm[k], ss[k]);
-                const int off = op_offset(r, 8 * g);
-                *reinterpret_cast<uint4 *>(stage + 0 * kOpAx + off) = *reinterpret_cast<const uint4 *>(hh);
-                *reinterpret_cast<uint4 *>(stage + 1 * kOpAx + off) = *reinterpret_cast<const uint4 *>(mm);
-                *reinterpret_cast<uint4 *>(stage + 2 * kOpAx + off) = *reinterpret_cast<const uint4 *>(ss);
+            {  // X_H chunk: already split and laid out, copied asynchronously.
+                const unsigned char *src = xs + (size_t)3 * c * kOpAx;
+                for (int i = t; i < 3 * kOpAx / 16; i += kHotThreads) cp_async16(stage + 3 * kOpAx + 16 * i, src + 16 * i);
+                asm volatile("cp.async.commit_group;" ::: "memory");
             }
-            // X_H chunk: already split and laid out; a straight copy.
-            {
-                const uint4 *src = reinterpret_cast<const uint4 *>(xs + (size_t)3 * c * kOpAx);
-                uint4 *dst = reinterpret_cast<uint4 *>(stage + 3 * kOpAx);
-                for (int i = t; i < 3 * kOpAx / 16; i += kHotThreads) dst[i] = __ldg(src + i);
-            }
+            store_ax(areg, stage);
+            // Prefetch the next chunk of A_H (of this tile or of the next one).
+            if (c + 1 < nchunks) load_ax(dense, m, h, row0, c + 1, areg);
+            else if (tile + gridDim.x < ntiles) load_ax(dense, m, h, row0 + (int64_t)gridDim.x * kRowsTile, 0, areg);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
             fence_async_smem();
             fence_before();
             __syncthreads();
@@ -190,7 +227,7 @@ hot_ax_kernel(int64_t m, int h, const float *__restrict__ dense, const unsigned 
             last = b;
         }
         if (!ok) break;
-        // The last commit covers every MMA of the tile.
+        // The last commit covers every MMA of the tile; both stages are free.
         const bool done = mbar_wait_bounded(smem_u32(mbar + last), (uses[last] - 1) & 1, limit_cycles);
         if (!__syncthreads_and(done)) { ok = false; break; }
         fence_after();
@@ -202,17 +239,21 @@ hot_ax_kernel(int64_t m, int h, const float *__restrict__ dense, const unsigned 
             float vm[32], vc[32];
             tmem_ld32(d_main + lane_addr + col0 + 32 * q, vm);
             tmem_ld32(d_corr + lane_addr + col0 + 32 * q, vc);
-            if (row0 + row < m) {
-                float *yr = Y + (row0 + row) * ldy + col0 + 32 * q;
+            float *orow = otile + row * (kRowsTile + 1) + col0 + 32 * q;
 #pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    if (col0 + 32 * q + i < lcols) yr[i] = vm[i] + vc[i];
-            }
+            for (int i = 0; i < 32; ++i) orow[i] = vm[i] + vc[i];
         }
         fence_before();
         __syncthreads();
+        // Coalesced rows: consecutive threads write consecutive columns.
+        for (int idx = t; idx < kRowsTile * lcols; idx += kHotThreads) {
+            const int r = idx / lcols, cc = idx - r * lcols;
+            if (row0 + r < m) Y[(row0 + r) * ldy + cc] = otile[r * (kRowsTile + 1) + cc];
+        }
+        __syncthreads();
     }
     if (!ok && t == 0) set_status(status, FRPCA_ERR_TIMEOUT);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     fence_before();
     __syncthreads();
     fence_after();

@@ -138,7 +138,7 @@ def _hot_matrix(m, n, seed):
 @pytest.mark.parametrize("trans", [0, 1])
 def test_spmm_hot_columns_match_oracle(hot, l, trans):
     """A X and A^T X with the densest columns on the tensor cores (forced
-    block sizes, automatic, and off) against the oracle; rows of A^T at hot
+    block sizes, automatic (-1), and off (0)) against the oracle; rows of A^T at hot
     columns come from the dense block, the rest from the CSR of A^T."""
     A = _hot_matrix(9000, 2500, 3)
     mat = frpca.FrPCA.from_csr(A, device=DEV, hot_columns=hot)
