@@ -47,8 +47,10 @@ typedef enum frpca_status {
 typedef enum frpca_dtype { FRPCA_F32 = 0, FRPCA_F64 = 1 } frpca_dtype;
 
 /* Arithmetic of a run.  FP64: every step in double.  FP32: SpMM, LU, Gram and
- * the apply step in float; the l x l eigendecomposition always returns double
- * precision eigenpairs.  FP32_SPLITGRAM: FP32 with the Gram matrix of the
+ * the apply step in float (the apply step, Y = M W with l, k <= 128, on the
+ * tensor cores from split-BF16 operands: every product exact, accumulated in
+ * float); the l x l eigendecomposition always returns double precision
+ * eigenpairs.  FP32_SPLITGRAM: FP32 with the Gram matrix of the
  * final eigSVD (the one over max(m, n) rows) formed on the tensor cores from
  * split-BF16 operands; needs l <= 128 (see frpca_gram_splitbf16). */
 typedef enum frpca_precision {

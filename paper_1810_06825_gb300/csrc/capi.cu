@@ -264,6 +264,20 @@ frpca_status small_bufs(frpca_ctx *h, int l, Small &s) {
     return FRPCA_OK;
 }
 
+// Y = M W (Alg. 2 step 5 and the final products of Alg. 5/6): FP32 blocks
+// that fit go to the tensor cores, the rest to the CUDA-core kernel.
+frpca_status apply_block(frpca_ctx *h, int64_t R, int l, const void *M, int64_t ldm, const void *W, int kout,
+                         void *Y, int64_t ldy, frpca_dtype dt, const char *what) {
+    if (dt == FRPCA_F32 && apply_tc_eligible(R, l, M, ldm, kout, ldy)) {
+        CK(launch_apply_tc(R, l, (const float *)M, ldm, (const float *)W, kout, (float *)Y, ldy, h->num_sms,
+                           h->d_status, h->stream),
+           what);
+    } else {
+        CK(launch_apply(R, l, M, ldm, W, kout, Y, ldy, dt, h->stream), what);
+    }
+    return FRPCA_OK;
+}
+
 // eigSVD (Alg. 2) in place: M <- U = M V spdiags(1./S).
 frpca_status eigsvd_inplace(frpca_ctx *h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, Small &s,
                             double *S_out) {
@@ -272,8 +286,7 @@ frpca_status eigsvd_inplace(frpca_ctx *h, int64_t R, int l, void *M, int64_t ld,
     PhaseTimer t(h, PH_APPLY);
     CK(launch_make_w(l, l, s.w, s.V, /*descending=*/0, /*scale=*/1, nullptr, dt, s.W1, S_out, h->d_status, h->stream),
        "make_w");
-    CK(launch_apply(R, l, M, ld, s.W1, l, M, ld, dt, h->stream), "apply");
-    return FRPCA_OK;
+    return apply_block(h, R, l, M, ld, s.W1, l, M, ld, dt, "apply");
 }
 
 frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S, void *V) {
@@ -361,15 +374,15 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
     const bool sign_on_thin = (alg == 6) || (m < n);
     CK(h->ws_sign.ensure(sign_workspace_bytes(k, h->num_sms)), "alloc sign workspace");
     CK(launch_make_w(l, k, sm.w, sm.V, 1, 0, nullptr, dt, sm.W1, S, h->d_status, h->stream), "make_w thin");
-    CK(launch_apply(rq, l, Q, ld, sm.W1, k, thin, k, dt, h->stream), "apply thin");
+    if ((st = apply_block(h, rq, l, Q, ld, sm.W1, k, thin, k, dt, "apply thin")) != FRPCA_OK) return st;
     if (sign_on_thin) {
         CK(launch_column_signs(rq, k, thin, k, dt, sm.sign, h->ws_sign.ptr, h->num_sms, h->stream), "signs");
         CK(launch_scale_columns(rq, k, thin, k, dt, sm.sign, h->stream), "flip thin");
         CK(launch_make_w(l, k, sm.w, sm.V, 1, 1, sm.sign, dt, sm.W2, nullptr, h->d_status, h->stream), "make_w wide");
-        CK(launch_apply(rw, l, W, ld, sm.W2, k, wide, k, dt, h->stream), "apply wide");
+        if ((st = apply_block(h, rw, l, W, ld, sm.W2, k, wide, k, dt, "apply wide")) != FRPCA_OK) return st;
     } else {
         CK(launch_make_w(l, k, sm.w, sm.V, 1, 1, nullptr, dt, sm.W2, nullptr, h->d_status, h->stream), "make_w wide");
-        CK(launch_apply(rw, l, W, ld, sm.W2, k, wide, k, dt, h->stream), "apply wide");
+        if ((st = apply_block(h, rw, l, W, ld, sm.W2, k, wide, k, dt, "apply wide")) != FRPCA_OK) return st;
         CK(launch_column_signs(rw, k, wide, k, dt, sm.sign, h->ws_sign.ptr, h->num_sms, h->stream), "signs");
         CK(launch_scale_columns(rw, k, wide, k, dt, sm.sign, h->stream), "flip wide");
         CK(launch_scale_columns(rq, k, thin, k, dt, sm.sign, h->stream), "flip thin");
@@ -681,7 +694,7 @@ frpca_status frpca_eigsvd(frpca_handle h, int64_t R, int l, void *M, int64_t ld,
     if ((st = gram_eig(h, R, l, M, ld, dt, sm.B, sm.w, sm.V)) != FRPCA_OK) return st;
     // S = sqrt(w) ascending, W = V diag(1./S), then U = M W over M.
     CK(launch_make_w(l, l, sm.w, sm.V, 0, 1, nullptr, dt, sm.W1, S, h->d_status, h->stream), "make_w");
-    CK(launch_apply(R, l, M, ld, sm.W1, l, M, ld, dt, h->stream), "apply");
+    if ((st = apply_block(h, R, l, M, ld, sm.W1, l, M, ld, dt, "apply")) != FRPCA_OK) return st;
     CK(cudaMemcpyAsync(V, sm.V, sizeof(double) * (size_t)l * l, cudaMemcpyDeviceToDevice, h->stream), "copy V");
     return read_status(h);
 }

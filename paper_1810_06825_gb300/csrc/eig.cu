@@ -599,13 +599,8 @@ __global__ void level_split_kernel(int n, int ld, const int *db, const double *_
     if (threadIdx.x == 0) *db_next = (first_big >= 2) ? first_big : 0;
 }
 
-__global__ void set_identity_kernel(int n, int ld, double *X, int *dims, int levels, unsigned long long *emax,
-                                    int nemax) {
+__global__ void init_levels_kernel(int n, int *dims, int levels, unsigned long long *emax, int nemax) {
     for (int i = threadIdx.x; i < nemax; i += blockDim.x) emax[i] = ~0ull;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int i = idx / n, j = idx - i * n;
-        X[i * ld + j] = (i == j) ? 1.0 : 0.0;
-    }
     if (threadIdx.x == 0) {
         dims[0] = n;
         for (int lv = 1; lv <= levels; ++lv) dims[lv] = 0;
@@ -614,11 +609,12 @@ __global__ void set_identity_kernel(int n, int ld, double *X, int *dims, int lev
 
 __global__ void copy_out_kernel(int n, int ld, const double *__restrict__ lam_all, const double *__restrict__ X,
                                 double *__restrict__ w, double *__restrict__ V) {
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n * n) {
         const int i = idx / n, j = idx - i * n;
-        V[i * n + j] = X[i * ld + j];
+        V[idx] = X[i * ld + j];
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = lam_all[i];
+    if (idx < n) w[idx] = lam_all[idx];
 }
 
 }  // namespace
@@ -659,21 +655,27 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, oa_refine_kernel, 256, 0)) != cudaSuccess)
         return e;
     const int refine_ctas = std::max(1, sms * per_sm);
-    set_identity_kernel<<<1, 256, 0, s>>>(n, ld, X, dims, kLevels, emax, kLevels * kRefineSteps);
+    init_levels_kernel<<<1, 32, 0, s>>>(n, dims, kLevels, emax, kLevels * kRefineSteps);
     count_launch();
     const dim3 g2((n + 15) / 16, (n + 15) / 16);
     for (int lv = 0; lv < kLevels; ++lv) {
         const int *db = dims + lv;  // active block size (0: nothing left)
-        // C = Xa^T B Xa on the active columns (the first b columns of X).
-        gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, nullptr, n, 0, n, ld, Bl, X, nullptr, T);
-        gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, nullptr, 0, 0, n, ld, X, T, nullptr, Cm);
-        jacobi<<<kJacobiCtas, kJacobiThreads, smem, s>>>(db, 0, Cm, ld, Z);
-        count_launch(3);
+        // C = Xa^T B Xa on the active columns (the first b columns of X); at
+        // level 0, X = I and C = B.
+        const double *C = Bl;
+        if (lv > 0) {
+            gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, nullptr, n, 0, n, ld, Bl, X, nullptr, T);
+            gemm64_kernel<true><<<g2, 256, 0, s>>>(db, db, nullptr, 0, 0, n, ld, X, T, nullptr, Cm);
+            count_launch(2);
+            C = Cm;
+        }
+        jacobi<<<kJacobiCtas, kJacobiThreads, smem, s>>>(db, 0, C, ld, Z);
+        count_launch();
         {
             if ((e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s)) != cudaSuccess) return e;
             const int *dn = db;
             int ldv = ld;
-            const double *cm = Cm;
+            const double *cm = C;
             unsigned long long *em = emax + lv * kRefineSteps;
             long long lim = kBarrierLimitCycles;
             void *args[] = {(void *)&dn, &ldv, (void *)&cm, &Z, &Z2, &G, &T, &S, &E, &Pn, &lam_b, &em, &bar,
@@ -683,13 +685,19 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
             if (e != cudaSuccess) return e;
             count_launch();
         }
-        // Xa <- Xa Z, then sort the active block and choose the next one.
-        gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, db, n, 0, 0, ld, X, Z, nullptr, Xn);
-        level_split_kernel<<<1, 256, 0, s>>>(n, ld, db, lam_b, Xn, X, lam_all, dims + lv + 1, d_status);
-        count_launch(2);
+        // Xa <- Xa Z (at level 0 simply Z), then sort the active block and
+        // choose the next one.
+        const double *Xa = Z;
+        if (lv > 0) {
+            gemm64_kernel<false><<<g2, 256, 0, s>>>(nullptr, db, db, n, 0, 0, ld, X, Z, nullptr, Xn);
+            count_launch();
+            Xa = Xn;
+        }
+        level_split_kernel<<<1, 1024, 0, s>>>(n, ld, db, lam_b, Xa, X, lam_all, dims + lv + 1, d_status);
+        count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    copy_out_kernel<<<1, 256, 0, s>>>(n, ld, lam_all, X, w, V);
+    copy_out_kernel<<<(int)ceil_div((int64_t)n * n, 256), 256, 0, s>>>(n, ld, lam_all, X, w, V);
     count_launch();
     return cudaGetLastError();
 }

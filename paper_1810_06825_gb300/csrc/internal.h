@@ -106,6 +106,13 @@ cudaError_t launch_make_w(int l, int kout, const double *w, const double *V, int
 // Y (R x kout, ldy) = M (R x l, ldm) W; Y may equal M when kout <= ldm.
 cudaError_t launch_apply(int64_t R, int l, const void *M, int64_t ldm, const void *W, int kout, void *Y,
                          int64_t ldy, frpca_dtype dt, cudaStream_t s);
+// The same product for FP32 on the tensor cores (split-BF16, apply_tc.cu),
+// for blocks where apply_tc_eligible holds: l, kout <= 128, ldm a multiple
+// of 4 and at least round_up(l, 8), M 16-byte aligned.  Y may equal M (same
+// leading dimension).
+bool apply_tc_eligible(int64_t R, int l, const void *M, int64_t ldm, int kout, int64_t ldy);
+cudaError_t launch_apply_tc(int64_t R, int l, const float *M, int64_t ldm, const float *W, int kout, float *Y,
+                            int64_t ldy, int sms, int *d_status, cudaStream_t s);
 // sign[j] = +1/-1 so that the largest-magnitude entry (smallest row on ties) of
 // column j of X (R x k, ld) is positive; partial results in ws.
 size_t sign_workspace_bytes(int k, int num_sms);

@@ -275,6 +275,25 @@ def test_eigsvd_matches_oracle(R, l, cond, dtype):
     assert max_principal_sine(U, Uo) <= (1e-10 if dtype == np.float64 else 1e-3)
 
 
+@pytest.mark.parametrize("R,l", [(1, 1), (127, 7), (129, 64), (300, 65), (1000, 128), (4097, 120)])
+def test_eigsvd_apply_step_elementwise(R, l):
+    """Step 5 of Alg. 2 in FP32 (U = M V spdiags(1./S), on the tensor cores for
+    l <= 128): every entry of U against the product formed in FP64 from the
+    returned S and V, with the float accumulation bound of an l-term sum;
+    covers ragged 128-row tiles and the second 64-column chunk."""
+    rng = np.random.default_rng(R + l)
+    Uq, _ = np.linalg.qr(rng.standard_normal((R, l)))
+    Vq, _ = np.linalg.qr(rng.standard_normal((l, l)))
+    M = ((Uq * np.geomspace(1, 0.1, l)) @ Vq.T).astype(np.float32)
+    U, S, V = frpca.eigsvd(torch.from_numpy(M).to(DEV))
+    U, S, V = _cpu(U), _cpu(S), _cpu(V)
+    W = (V / S).astype(np.float32).astype(np.float64)  # the float W the step multiplies by
+    Md = M.astype(np.float64)
+    ref = Md @ W
+    bound = (l + 8) * 2.0**-23 * (np.abs(Md) @ np.abs(W))
+    assert np.all(np.abs(U - ref) <= bound)
+
+
 def test_eigsvd_rank_deficient_reports():
     M = np.random.default_rng(0).standard_normal((300, 8))
     M[:, 7] = M[:, 0] - M[:, 2]
