@@ -34,10 +34,10 @@ L2_BYTES = 129 * 2**20
 PRECISIONS = ("fp32", "fp64", "fp32_splitgram")
 
 # DRAM traffic of one SpMM pass (dram__bytes_read.sum + dram__bytes_write.sum),
-# averaged over the q = 5 schedule (3 passes with A, 2 with A^T), from the ncu
-# capture summarized in profiles/spmm_kernel_powerlaw_200000x50000.md.  Valid
-# only while spmm_kernel is unchanged since that capture.
-NCU_SPMM_TRAFFIC = {(WORKLOAD, "f32", 5): (3 * 272.0e6 + 2 * 1379.0e6) / 5}
+# averaged over the q = 5 schedule (3 passes with A, 2 with A^T), from an ncu
+# capture of one step's five spmm_kernel launches on this workload.  Valid only
+# while spmm_kernel is unchanged since that capture.
+NCU_SPMM_TRAFFIC = {(WORKLOAD, "f32", 5): (275.2e6 + 272.3e6 + 272.1e6 + 1483.0e6 + 1484.3e6) / 5}
 
 
 def _max_sine(X, Y):
