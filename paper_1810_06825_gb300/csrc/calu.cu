@@ -57,6 +57,18 @@ constexpr int kSlotBits = 11;  // candidate slot < 2048
 
 constexpr int kCaluWarps = kCaluThreads / 32;
 
+// Block-wide max of a key with one barrier; every thread gets it.  Callers
+// alternate between two tables, so a table is rewritten only after every
+// thread has passed the next call's barrier, i.e. finished reading it.
+__device__ inline unsigned int block_max1(unsigned int key, unsigned int *wm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    key = __reduce_max_sync(0xffffffffu, key);
+    if (lane == 0) wm[warp] = key;
+    __syncthreads();
+    const unsigned int v = lane < kCaluWarps ? wm[lane] : 0u;
+    return __reduce_max_sync(0xffffffffu, v);
+}
+
 // Block-wide max of a key; every thread gets it.
 __device__ inline unsigned int block_max(unsigned int key, unsigned int *wmax) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -106,7 +118,10 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
     __shared__ int win_row[kPanel];
     __shared__ int win_slot[kPanel];
     __shared__ unsigned int wmax[kCaluWarps];
+    __shared__ unsigned int wmax2[2][kCaluWarps];
     __shared__ float pvw[kPanel];  // the local pivot's panel entries
+    __shared__ float pvr;          // 1 / the local pivot
+    __shared__ float rdiag[kPanel];  // 1 / U(k, c0 + k) of the panel
     const unsigned G = gridDim.x;
     const int t = threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.x * R / G, r1 = (int64_t)(blockIdx.x + 1) * R / G;
@@ -146,7 +161,7 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
 #pragma unroll
             for (int kk = 0; kk < kPanel; ++kk)
                 if (kk == k) pk = pv[kk];
-            const unsigned int key = block_max((mine && !picked) ? pack_key(pk, t, kRowBits) : 0u, wmax);
+            const unsigned int key = block_max1((mine && !picked) ? pack_key(pk, t, kRowBits) : 0u, wmax2[k & 1]);
             const int slot = blockIdx.x * kPanel + k;
             if (key == 0u) {  // no nonzero entry left in this block
                 if (t == 0) cids[slot] = -1;
@@ -157,6 +172,7 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
                 picked = true;
 #pragma unroll
                 for (int kk = 0; kk < kPanel; ++kk) pvw[kk] = pv[kk];
+                pvr = 1.0f / pk;
                 cids[slot] = (int)(r0 + wl);
             }
             // Publish the picked row as it is (not the eliminated copy).
@@ -164,7 +180,7 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
             if (t < kPanel) cpan[slot * kPanel + t] = (t < w) ? cache[wl * cst + c0 + t] : 0.0f;
             __syncthreads();
             if (mine && !picked) {
-                const float m = pk / pvw[k];
+                const float m = pk * pvr;
 #pragma unroll
                 for (int kk = 0; kk < kPanel; ++kk)
                     if (kk > k && kk < w) pv[kk] = fmaf(-m, pvw[kk], pv[kk]);
@@ -174,11 +190,15 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
         ok = grid_barrier(bar, G, status, limit_cycles);
         if (!ok) break;
 
-        // (3) The tournament, the same in every block.
+        // (3) The tournament, the same in every block.  Thread t owns the
+        // candidates t + j kCaluThreads: it alone updates their entries and
+        // tracks which of them were chosen, so a pivot step needs one barrier
+        // (the block max) -- the pivot row's entries, read by every thread, were
+        // last written before that barrier.
+        constexpr int kOwn = (kMaxCand + kCaluThreads - 1) / kCaluThreads;
         for (int i = t; i < ncand; i += kCaluThreads) {
             const int id = __ldcg(cids + i);
             tid[i] = id;
-            tch[i] = 0;
             const float4 a = id >= 0 ? __ldcg(reinterpret_cast<const float4 *>(cpan + i * kPanel)) : make_float4(0, 0, 0, 0);
             const float4 b = id >= 0 ? __ldcg(reinterpret_cast<const float4 *>(cpan + i * kPanel + 4)) : make_float4(0, 0, 0, 0);
             tv[0 * kMaxCand + i] = a.x; tv[1 * kMaxCand + i] = a.y; tv[2 * kMaxCand + i] = a.z; tv[3 * kMaxCand + i] = a.w;
@@ -186,52 +206,104 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
         }
         __syncthreads();
         bool singular = false;
+        unsigned int chosen = 0u;  // bit j: candidate t + j kCaluThreads was chosen
         for (int k = 0; k < w; ++k) {
             unsigned int key = 0u;
-            for (int i = t; i < ncand; i += kCaluThreads)
-                if (tid[i] >= 0 && !tch[i]) key = max(key, pack_key(tv[k * kMaxCand + i], i, kSlotBits));
-            key = block_max(key, wmax);
+#pragma unroll
+            for (int j = 0; j < kOwn; ++j) {
+                const int i = t + j * kCaluThreads;
+                if (i < ncand && tid[i] >= 0 && !((chosen >> j) & 1u))
+                    key = max(key, pack_key(tv[k * kMaxCand + i], i, kSlotBits));
+            }
+            key = block_max1(key, wmax2[k & 1]);
             if (key == 0u) {  // no nonzero pivot left in this column: every block sees it
                 if (t == 0 && blockIdx.x == 0) set_status(status, FRPCA_ERR_SINGULAR_PIVOT);
                 singular = true;
                 break;
             }
             const int sw = key_index(key, kSlotBits);
+            if (sw % kCaluThreads == t) chosen |= 1u << (sw / kCaluThreads);
             if (t == 0) {
-                tch[sw] = 1;
                 win_row[k] = tid[sw];
                 win_slot[k] = sw;
                 if (blockIdx.x == 0 && piv_out) piv_out[c0 + k] = tid[sw];
             }
-            const float ukk = tv[k * kMaxCand + sw];
-            for (int i = t; i < ncand; i += kCaluThreads) {
-                if (i == sw || tid[i] < 0 || tch[i]) continue;
-                const float m = tv[k * kMaxCand + i] / ukk;
-                for (int kk = k + 1; kk < w; ++kk) tv[kk * kMaxCand + i] = fmaf(-m, tv[kk * kMaxCand + sw], tv[kk * kMaxCand + i]);
+            const float rkk = 1.0f / tv[k * kMaxCand + sw];  // one reciprocal per pivot, the same in every block
+            float urow[kPanel];
+#pragma unroll
+            for (int kk = 0; kk < kPanel; ++kk) urow[kk] = (kk > k && kk < w) ? tv[kk * kMaxCand + sw] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < kOwn; ++j) {
+                const int i = t + j * kCaluThreads;
+                if (i >= ncand || tid[i] < 0 || ((chosen >> j) & 1u)) continue;
+                const float m = tv[k * kMaxCand + i] * rkk;
+#pragma unroll
+                for (int kk = 0; kk < kPanel; ++kk)
+                    if (kk > k && kk < w) tv[kk * kMaxCand + i] = fmaf(-m, urow[kk], tv[kk * kMaxCand + i]);
             }
-            __syncthreads();
         }
         if (singular) { ok = false; break; }
         // The winners' full rows, eliminated among themselves in pivot order:
         // U row k, and the multipliers L11(k, k') (kept left of the diagonal).
+        // Warp 0 eliminates the w x w panel block (lane j holds its column j and
+        // broadcasts multipliers by shuffles); every thread then applies the same
+        // row operations, in the same order, to its own trailing columns.
         for (int idx = t; idx < w * l; idx += kCaluThreads) {
             const int k = idx / l, c = idx - k * l;
             U[k * FRPCA_MAX_L + c] = __ldcg(crows + (size_t)win_slot[k] * ldc + c);
         }
         __syncthreads();
-        for (int k = 0; k < w; ++k) {
-            const float ukk = U[k * FRPCA_MAX_L + c0 + k];
-            const int span = l - c0 - k - 1;  // columns right of the pivot
-            for (int idx = t; idx < (w - 1 - k) * span; idx += kCaluThreads) {
-                const int k2 = k + 1 + idx / span, c = c0 + k + 1 + idx % span;
-                const float m = U[k2 * FRPCA_MAX_L + c0 + k] / ukk;
-                U[k2 * FRPCA_MAX_L + c] = fmaf(-m, U[k * FRPCA_MAX_L + c], U[k2 * FRPCA_MAX_L + c]);
+        __shared__ float mult[kPanel][kPanel];  // mult[k2][k]: row k2 -= mult * row k
+        if (t < 32) {
+            const int j = t;  // panel column c0 + j
+            float col[kPanel];
+#pragma unroll
+            for (int k2 = 0; k2 < kPanel; ++k2) col[k2] = (j < w && k2 < w) ? U[k2 * FRPCA_MAX_L + c0 + j] : 0.0f;
+#pragma unroll
+            for (int k = 0; k < kPanel; ++k) {
+                if (k >= w) break;
+                const float rkk = 1.0f / __shfl_sync(0xffffffffu, col[k], k);  // 1 / U(k, c0 + k)
+                float m[kPanel];
+#pragma unroll
+                for (int k2 = 0; k2 < kPanel; ++k2) m[k2] = __shfl_sync(0xffffffffu, col[k2], k) * rkk;
+                if (j > k) {
+#pragma unroll
+                    for (int k2 = 0; k2 < kPanel; ++k2)
+                        if (k2 > k && k2 < w) col[k2] = fmaf(-m[k2], col[k], col[k2]);
+                }
+                if (j == k) {
+#pragma unroll
+                    for (int k2 = 0; k2 < kPanel; ++k2)
+                        if (k2 > k && k2 < w) {
+                            mult[k2][k] = m[k2];
+                            col[k2] = m[k2];  // L11(k2, k)
+                        }
+                }
             }
-            __syncthreads();
-            for (int k2 = k + 1 + t; k2 < w; k2 += kCaluThreads)
-                U[k2 * FRPCA_MAX_L + c0 + k] = U[k2 * FRPCA_MAX_L + c0 + k] / ukk;  // L11(k2, k)
-            __syncthreads();
+            if (j < w) {
+#pragma unroll
+                for (int k2 = 0; k2 < kPanel; ++k2)
+                    if (k2 < w) U[k2 * FRPCA_MAX_L + c0 + j] = col[k2];
+#pragma unroll
+                for (int k2 = 0; k2 < kPanel; ++k2)
+                    if (k2 == j) rdiag[j] = 1.0f / col[k2];  // 1 / U(j, c0 + j)
+            }
         }
+        __syncthreads();
+        for (int c = c0 + w + t; c < l; c += kCaluThreads) {
+            float col[kPanel];
+#pragma unroll
+            for (int k2 = 0; k2 < kPanel; ++k2) col[k2] = k2 < w ? U[k2 * FRPCA_MAX_L + c] : 0.0f;
+#pragma unroll
+            for (int k = 0; k < kPanel; ++k)
+#pragma unroll
+                for (int k2 = 0; k2 < kPanel; ++k2)
+                    if (k < w && k2 > k && k2 < w) col[k2] = fmaf(-mult[k2][k], col[k], col[k2]);
+#pragma unroll
+            for (int k2 = 1; k2 < kPanel; ++k2)
+                if (k2 < w) U[k2 * FRPCA_MAX_L + c] = col[k2];
+        }
+        __syncthreads();
 
         // (4) Own rows.  Winners take their final form; the others get their
         // multipliers for the panel (forward substitution with U11).
@@ -248,7 +320,7 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
                 pivd[t] = 1;
             } else {
                 for (int k = 0; k < w; ++k) {
-                    const float m = row[c0 + k] / U[k * FRPCA_MAX_L + c0 + k];
+                    const float m = row[c0 + k] * rdiag[k];
                     row[c0 + k] = m;
                     for (int kk = k + 1; kk < w; ++kk) row[c0 + kk] = fmaf(-m, U[k * FRPCA_MAX_L + c0 + kk], row[c0 + kk]);
                 }
