@@ -169,15 +169,14 @@ __global__ void col_sign_kernel(int k, int nparts, const ColBest *__restrict__ p
     if (lane == 0) sign[j] = b.sgn;
 }
 
+// X(:, j) *= sign[j]: a block of rows per CTA row-group, threads along the
+// columns (no per-element index division).
 template <typename T>
 __global__ void scale_columns_kernel(int64_t R, int k, T *X, int64_t ld, const double *__restrict__ sign) {
-    const int64_t total = R * k;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / k;
-        const int j = (int)(idx - i * k);
-        if (sign[j] < 0) X[i * ld + j] = -X[i * ld + j];
-    }
+    const int j = threadIdx.x;
+    if (j >= k || !(sign[j] < 0)) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.y + threadIdx.y; i < R; i += (int64_t)gridDim.x * blockDim.y)
+        X[i * ld + j] = -X[i * ld + j];
 }
 
 int sign_blocks(int num_sms) { return 4 * num_sms; }
@@ -249,13 +248,15 @@ cudaError_t launch_column_signs(int64_t R, int k, const void *X, int64_t ld, frp
 
 cudaError_t launch_scale_columns(int64_t R, int k, void *X, int64_t ld, frpca_dtype dt, const double *sign,
                                  cudaStream_t s) {
-    const int64_t total = R * k;
-    if (total == 0) return cudaSuccess;
-    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(total, 256), 1 << 20);
+    if (R == 0 || k == 0) return cudaSuccess;
+    const int tx = (int)round_up(k, 32);  // k <= FRPCA_MAX_L: one thread per column
+    const int ty = std::max(1, 1024 / tx);
+    const dim3 block(tx, ty);
+    const unsigned g = (unsigned)std::min<int64_t>(ceil_div(R, ty), 4096);
     if (dt == FRPCA_F32)
-        scale_columns_kernel<float><<<g, 256, 0, s>>>(R, k, (float *)X, ld, sign);
+        scale_columns_kernel<float><<<g, block, 0, s>>>(R, k, (float *)X, ld, sign);
     else
-        scale_columns_kernel<double><<<g, 256, 0, s>>>(R, k, (double *)X, ld, sign);
+        scale_columns_kernel<double><<<g, block, 0, s>>>(R, k, (double *)X, ld, sign);
     count_launch();
     return cudaGetLastError();
 }

@@ -37,6 +37,14 @@ __device__ inline void df_fma(float x, float y, float &hi, float &lo) {
     lo = __fadd_rn(lo, __fadd_rn(err, e));
 }
 
+// 16 bytes global -> shared without a register round trip; the bytes past
+// src_bytes (0..16) are filled with zeros.
+__device__ inline void cp_async16_zfill(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
 // FP32 input: each thread accumulates one 8 x 4 tile (rows 8 ti .., columns
 // 4 tj .., tj >= 2 ti, which covers the upper triangle exactly once) in
 // double-float; 240 tiles for l = 120, so 256 (or, for l > 128, 512) threads
@@ -69,17 +77,32 @@ gram_partial_df_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld
         for (int b = 0; b < kTj; ++b) hi[a][b] = lo[a][b] = 0.0f;
     const int64_t G = gridDim.x;
     const int64_t r0 = (int64_t)blockIdx.x * R / G, r1 = (int64_t)(blockIdx.x + 1) * R / G;
-    for (int64_t c0 = r0; c0 < r1; c0 += kChunk) {
+    // Chunks are double-buffered in shared memory and fetched asynchronously
+    // one chunk ahead (ld is a multiple of 4 and M 16-byte aligned, so rows
+    // copy as 16-byte pieces; columns from l on and rows past the range read
+    // as zeros).
+    const int nq = lp / 4;
+    auto fetch = [&](int64_t c0, float *dst) {
         const int rows = (int)std::min<int64_t>(kChunk, r1 - c0);
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < kChunk * lp; idx += blockDim.x) {
-            const int rr = idx / lp, cc = idx - rr * lp;
-            Ms[idx] = (rr < rows && cc < l) ? M[(c0 + rr) * ld + cc] : 0.0f;
+        for (int qi = threadIdx.x; qi < kChunk * nq; qi += blockDim.x) {
+            const int rr = qi / nq, cc = 4 * (qi - rr * nq);
+            const bool in = rr < rows && cc < l;
+            cp_async16_zfill(dst + rr * lp + cc, in ? (const void *)(M + (c0 + rr) * ld + cc) : (const void *)M,
+                             in ? 4 * min(4, l - cc) : 0);
         }
-        __syncthreads();
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    int buf = 0;
+    if (r0 < r1) fetch(r0, Ms);
+    for (int64_t c0 = r0; c0 < r1; c0 += kChunk, buf ^= 1) {
+        const int rows = (int)std::min<int64_t>(kChunk, r1 - c0);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();  // chunk c0 is in buffer buf; buffer buf ^ 1 is no longer read
+        if (c0 + kChunk < r1) fetch(c0 + kChunk, Ms + (buf ^ 1) * kChunk * lp);
+        const float *Mc = Ms + buf * kChunk * lp;
         if (ti >= 0) {
             for (int rr = 0; rr < rows; ++rr) {
-                const float *row = Ms + rr * lp;
+                const float *row = Mc + rr * lp;
                 const float4 x0 = *reinterpret_cast<const float4 *>(row + ti * kTi);
                 const float4 x1 = *reinterpret_cast<const float4 *>(row + ti * kTi + 4);
                 const float4 y = *reinterpret_cast<const float4 *>(row + tj * kTj);
@@ -200,7 +223,7 @@ cudaError_t launch_gram(int64_t R, int l, const void *M, int64_t ld, frpca_dtype
     if (dt == FRPCA_F32) {
         const int n8 = (int)ceil_div(l, kTi);
         const int tiles = n8 * 2 * n8 - n8 * (n8 - 1);
-        const size_t sm = sizeof(float) * kChunk * n8 * kTi;
+        const size_t sm = 2 * sizeof(float) * kChunk * n8 * kTi;  // two chunk buffers
         if (tiles <= 256)
             gram_partial_df_kernel<256><<<G, 256, sm, s>>>(R, l, (const float *)M, ld, partial);
         else
