@@ -407,11 +407,15 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
         return st;
     };
     h->stream = opts ? (cudaStream_t)opts->stream : nullptr;
+    for (DevBuf *b : {&h->own_rowptr, &h->own_colidx, &h->own_vals, &h->t_rowptr, &h->t_colidx, &h->t_vals,
+                      &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
+                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot})
+        b->stream = h->stream;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "device attribute"));
-    e = cudaMalloc(&h->d_status, 256);
+    e = dev_malloc((void **)&h->d_status, 256, h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "alloc status"));
     e = cudaMemsetAsync(h->d_status, 0, 256, h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "clear status"));
@@ -518,7 +522,11 @@ frpca_status frpca_destroy(frpca_handle h) {
         cudaEventDestroy(mk.b);
     }
     for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
-    if (h->d_status) cudaFree(h->d_status);
+    dev_free(h->d_status, h->stream);
+    // The releases above are ordered on the handle's stream; let them retire
+    // before the handle (and possibly the caller's stream) goes away.
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
     delete h;
     return FRPCA_OK;
 }

@@ -40,13 +40,22 @@ struct SpmmPlan {
     int32_t *seg_len = nullptr;
     int32_t *long_rows = nullptr; // row of each long row
     int64_t *long_first = nullptr;// first segment of each long row (n_long + 1 entries)
+    cudaStream_t stream = nullptr;  // stream the arrays were allocated on
     void free_all();
 };
 
 // Grow-only device buffer.
+// Device memory from the stream-ordered pool of the current device, on the
+// stream of its owner: up to 8 GiB of freed blocks stay cached in the pool
+// (its release threshold is raised once per device), so creating and
+// destroying handles neither maps memory again nor synchronizes the device.
+cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
 struct DevBuf {
     void *ptr = nullptr;
     size_t bytes = 0;
+    cudaStream_t stream = nullptr;  // the owner's stream: allocation and release are ordered on it
     cudaError_t ensure(size_t need);
     void release();
 };

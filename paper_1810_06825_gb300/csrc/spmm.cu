@@ -164,11 +164,11 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmPlan &p, i
 }  // namespace
 
 void SpmmPlan::free_all() {
-    cudaFree(short_rows);
-    cudaFree(seg_start);
-    cudaFree(seg_len);
-    cudaFree(long_rows);
-    cudaFree(long_first);
+    dev_free(short_rows, stream);
+    dev_free(seg_start, stream);
+    dev_free(seg_len, stream);
+    dev_free(long_rows, stream);
+    dev_free(long_first, stream);
     short_rows = nullptr;
     seg_start = nullptr;
     seg_len = nullptr;
@@ -180,6 +180,7 @@ void SpmmPlan::free_all() {
 cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, std::string &err,
                             const std::vector<char> *skip) {
     plan.free_all();
+    plan.stream = s;
     plan.seg = kDefaultSeg;
     std::vector<int64_t> rp((size_t)A.rows + 1);
     cudaError_t e = cudaMemcpyAsync(rp.data(), A.rowptr, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost, s);
@@ -211,7 +212,7 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
     plan.n_segs = (int64_t)sstart.size();
     auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
         if (bytes == 0) return cudaSuccess;
-        cudaError_t r = cudaMalloc(dst, bytes);
+        cudaError_t r = dev_malloc(dst, bytes, s);
         if (r != cudaSuccess) return r;
         return cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s);
     };

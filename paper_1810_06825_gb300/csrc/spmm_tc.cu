@@ -422,6 +422,7 @@ void HybridCSR::free_all() {
 cudaError_t build_hybrid(const DeviceCSR &A, const DeviceCSR &AT, int want, HybridCSR &hy, DevBuf &scan_scratch,
                          cudaStream_t s, std::string &err) {
     hy.free_all();
+    for (DevBuf *b : {&hy.b_hot, &hy.b_slot, &hy.b_dense, &hy.b_crow, &hy.b_ccol, &hy.b_cval}) b->stream = s;
     if (want == 0 || A.dtype != FRPCA_F32 || A.nnz == 0) return cudaSuccess;
     // Column counts from the row pointers of A^T.
     std::vector<int64_t> rpt((size_t)AT.rows + 1);

@@ -13,6 +13,7 @@
 // in shared memory, and each digit's run is written out contiguously.  The
 // row pointers of A^T are read off the sorted column indices.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -113,6 +114,7 @@ cudaError_t exclusive_scan(const TIn *in, int64_t *out, int64_t n, DevBuf &scrat
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (nb > kScanChunk) {
         DevBuf inner;
+        inner.stream = s;
         e = exclusive_scan<int64_t>(sums, offs, nb, inner, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         inner.release();
@@ -399,15 +401,37 @@ cudaError_t csr_transpose(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, De
     return transpose_typed<double>(A, AT, scratch, scan_scratch, s);
 }
 
+cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t s) {
+    static std::mutex mu;
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!configured[dev]) {
+            cudaMemPool_t pool;
+            if ((e = cudaDeviceGetDefaultMemPool(&pool, dev)) != cudaSuccess) return e;
+            uint64_t keep = 8ull << 30;  // up to 8 GiB of freed blocks stay cached for reuse
+            if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+            configured[dev] = true;
+        }
+    }
+    return cudaMallocAsync(p, bytes, s);
+}
+
+void dev_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
 cudaError_t DevBuf::ensure(size_t need) {
     if (need <= bytes) return cudaSuccess;
     if (ptr) {
-        cudaError_t e = cudaFree(ptr);
+        dev_free(ptr, stream);
         ptr = nullptr;
         bytes = 0;
-        if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaMalloc(&ptr, need);
+    cudaError_t e = dev_malloc(&ptr, need, stream);
     if (e != cudaSuccess) {
         ptr = nullptr;
         return e;
@@ -417,7 +441,7 @@ cudaError_t DevBuf::ensure(size_t need) {
 }
 
 void DevBuf::release() {
-    if (ptr) cudaFree(ptr);
+    dev_free(ptr, stream);
     ptr = nullptr;
     bytes = 0;
 }
