@@ -27,7 +27,7 @@ struct frpca_ctx {
     DevBuf alt_A, alt_AT;                        // values converted to the other dtype
     bool alt_ready = false;
     SpmmPlan planA, planAT;
-    DevBuf ws_q, ws_w, ws_spmm, ws_gram, ws_eig, ws_lu, ws_small, ws_sign, ws_scratch, ws_scan, ws_bwd, ws_hot;
+    DevBuf ws_q, ws_w, ws_spmm, ws_gram, ws_eig, ws_lu, ws_small, ws_sign, ws_scratch, ws_scan, ws_bwd, ws_hot, ws_plan;
     HybridCSR hy;  // the densest columns of A as a dense block (FP32 SpMM on the tensor cores)
     std::string err;
     // instrumentation
@@ -409,7 +409,7 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
     h->stream = opts ? (cudaStream_t)opts->stream : nullptr;
     for (DevBuf *b : {&h->own_rowptr, &h->own_colidx, &h->own_vals, &h->t_rowptr, &h->t_colidx, &h->t_vals,
                       &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
-                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot})
+                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot, &h->ws_plan})
         b->stream = h->stream;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
@@ -491,9 +491,12 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
     if ((e = csr_transpose(h->A, h->AT, h->ws_scratch, h->ws_scan, h->stream)) != cudaSuccess)
         return bail(cuda_fail(h, e, "transpose"));
     std::string perr;
-    if ((e = build_spmm_plan(h->A, h->planA, h->stream, perr)) != cudaSuccess ||
-        (e = build_spmm_plan(h->AT, h->planAT, h->stream, perr)) != cudaSuccess)
-        return bail(cuda_fail(h, e, perr.c_str()));
+    {
+        const DeviceCSR *mats[2] = {&h->A, &h->AT};
+        SpmmPlan *plans[2] = {&h->planA, &h->planAT};
+        if ((e = build_spmm_plans_device(mats, plans, 2, h->ws_plan, h->ws_scan, h->stream, perr)) != cudaSuccess)
+            return bail(cuda_fail(h, e, perr.c_str()));
+    }
     {
         const int hc = opts ? opts->hot_columns : 0;
         const int want = hc < 0 ? -1 : hc;  // -1 automatic, 0 off, > 0 a count
@@ -515,7 +518,7 @@ frpca_status frpca_destroy(frpca_handle h) {
     h->hy.free_all();
     for (DevBuf *b : {&h->own_rowptr, &h->own_colidx, &h->own_vals, &h->t_rowptr, &h->t_colidx, &h->t_vals,
                       &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
-                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot})
+                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot, &h->ws_plan})
         b->release();
     for (auto &mk : h->marks) {
         cudaEventDestroy(mk.a);

@@ -81,6 +81,11 @@ cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n
 // rows are not written).
 cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, std::string &err,
                             const std::vector<char> *skip = nullptr);
+// The same plans for several matrices, built on the device (one host
+// synchronization for all of them, to read the totals); scratch holds the
+// per-row flags and scans.
+cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *const *plans, int count, DevBuf &scratch,
+                                    DevBuf &scan_scratch, cudaStream_t s, std::string &err);
 size_t spmm_scratch_bytes(const SpmmPlan &plan, int l, frpca_dtype dt);
 cudaError_t launch_spmm(const DeviceCSR &A, const void *vals, const SpmmPlan &plan, int l, const void *X,
                         int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *scratch, cudaStream_t s, bool accumulate = false);

@@ -227,6 +227,122 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
     return cudaStreamSynchronize(s);
 }
 
+// ---- the same plan built on the device (no host pass over the rows)
+namespace {
+
+// Per row: 1 if handled whole (at most seg entries), and its number of
+// segments otherwise.
+__global__ void plan_flags_kernel(int64_t m, const int64_t *__restrict__ rowptr, int seg, int32_t *__restrict__ is_short,
+                                  int32_t *__restrict__ nseg) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t len = rowptr[i + 1] - rowptr[i];
+    is_short[i] = len <= seg ? 1 : 0;
+    nseg[i] = len <= seg ? 0 : (int32_t)((len + seg - 1) / seg);
+}
+
+// Order-preserving compaction from the scans: short rows, long rows with
+// their first segment, and every segment's (start, length).
+__global__ void plan_fill_kernel(int64_t m, const int64_t *__restrict__ rowptr, int seg,
+                                 const int32_t *__restrict__ is_short, const int64_t *__restrict__ short_pos,
+                                 const int64_t *__restrict__ seg_off, int32_t *__restrict__ short_rows,
+                                 int32_t *__restrict__ long_rows, int64_t *__restrict__ long_first,
+                                 int64_t *__restrict__ seg_start, int32_t *__restrict__ seg_len) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0) long_first[m - short_pos[m]] = seg_off[m];
+    if (i >= m) return;
+    if (is_short[i]) {
+        short_rows[short_pos[i]] = (int32_t)i;
+        return;
+    }
+    const int64_t j = i - short_pos[i];  // rank among the long rows
+    const int64_t first = seg_off[i], start = rowptr[i], end = rowptr[i + 1];
+    long_rows[j] = (int32_t)i;
+    long_first[j] = first;
+    for (int64_t p = start, sidx = first; p < end; p += seg, ++sidx) {
+        seg_start[sidx] = p;
+        seg_len[sidx] = (int32_t)min((int64_t)seg, end - p);
+    }
+}
+
+}  // namespace
+
+cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *const *plans, int count, DevBuf &scratch,
+                                    DevBuf &scan_scratch, cudaStream_t s, std::string &err) {
+    // Scratch per matrix: flags (2 x rows int32) and scans (2 x (rows + 1) int64).
+    std::vector<size_t> off((size_t)count + 1, 0);
+    for (int c = 0; c < count; ++c)
+        off[c + 1] = off[c] + round_up(8 * (size_t)mats[c]->rows + 16 * ((size_t)mats[c]->rows + 1), 256);
+    cudaError_t e = scratch.ensure(std::max<size_t>(off[count], 256));
+    if (e != cudaSuccess) {
+        err = "spmm plan: scratch allocation failed";
+        return e;
+    }
+    auto parts = [&](int c, int32_t *&is_short, int32_t *&nseg, int64_t *&short_pos, int64_t *&seg_off) {
+        const int64_t m = mats[c]->rows;
+        char *p = (char *)scratch.ptr + off[c];
+        is_short = (int32_t *)p;
+        nseg = is_short + m;
+        short_pos = (int64_t *)round_up((int64_t)(uintptr_t)(nseg + m), 8);
+        seg_off = short_pos + m + 1;
+    };
+    std::vector<int64_t> totals(2 * (size_t)count, 0);
+    for (int c = 0; c < count; ++c) {
+        const DeviceCSR &A = *mats[c];
+        plans[c]->free_all();
+        plans[c]->stream = s;
+        plans[c]->seg = kDefaultSeg;
+        int32_t *is_short, *nseg;
+        int64_t *short_pos, *seg_off;
+        parts(c, is_short, nseg, short_pos, seg_off);
+        plan_flags_kernel<<<(unsigned)ceil_div(A.rows, 256), 256, 0, s>>>(A.rows, A.rowptr, kDefaultSeg, is_short,
+                                                                         nseg);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess ||
+            (e = exclusive_scan_i32_to_i64(is_short, short_pos, A.rows, scan_scratch, s)) != cudaSuccess ||
+            (e = exclusive_scan_i32_to_i64(nseg, seg_off, A.rows, scan_scratch, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&totals[2 * c], short_pos + A.rows, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&totals[2 * c + 1], seg_off + A.rows, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+            err = "spmm plan: device pass failed";
+            return e;
+        }
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        err = "spmm plan: synchronize failed";
+        return e;
+    }
+    for (int c = 0; c < count; ++c) {
+        const DeviceCSR &A = *mats[c];
+        SpmmPlan &plan = *plans[c];
+        plan.n_short = totals[2 * c];
+        plan.n_long = A.rows - plan.n_short;
+        plan.n_segs = totals[2 * c + 1];
+        auto alloc = [&](void **dst, size_t bytes) -> cudaError_t {
+            return bytes ? dev_malloc(dst, bytes, s) : cudaSuccess;
+        };
+        if ((e = alloc((void **)&plan.short_rows, 4 * (size_t)plan.n_short)) != cudaSuccess ||
+            (e = alloc((void **)&plan.long_rows, 4 * (size_t)plan.n_long)) != cudaSuccess ||
+            (e = alloc((void **)&plan.long_first, 8 * ((size_t)plan.n_long + 1))) != cudaSuccess ||
+            (e = alloc((void **)&plan.seg_start, 8 * (size_t)plan.n_segs)) != cudaSuccess ||
+            (e = alloc((void **)&plan.seg_len, 4 * (size_t)plan.n_segs)) != cudaSuccess) {
+            err = "spmm plan: device allocation failed";
+            return e;
+        }
+        int32_t *is_short, *nseg;
+        int64_t *short_pos, *seg_off;
+        parts(c, is_short, nseg, short_pos, seg_off);
+        plan_fill_kernel<<<(unsigned)ceil_div(A.rows, 256), 256, 0, s>>>(
+            A.rows, A.rowptr, kDefaultSeg, is_short, short_pos, seg_off, plan.short_rows, plan.long_rows,
+            plan.long_first, plan.seg_start, plan.seg_len);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            err = "spmm plan: fill failed";
+            return e;
+        }
+    }
+    return cudaSuccess;
+}
+
 size_t spmm_scratch_bytes(const SpmmPlan &plan, int l, frpca_dtype dt) {
     const int W = dt == FRPCA_F32 ? 4 : 2;
     return (size_t)plan.n_segs * (size_t)ceil_div(l, W) * 16;
