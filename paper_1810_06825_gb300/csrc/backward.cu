@@ -29,7 +29,7 @@ constexpr int kTnTile = 32;      // output tile of the X^T Y partials
 constexpr int kTnRowsPerBlock = 512;
 constexpr size_t kTnPartialBudget = size_t(4) << 20;  // doubles of partial sums
 constexpr int kRowThreads = 256;
-constexpr int kSddmmThreads = 256;
+constexpr int kSddmmThreads = 64;  // a warp per row of A: small blocks free their slots row by row
 
 __host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
