@@ -69,22 +69,10 @@ __device__ inline unsigned int block_max1(unsigned int key, unsigned int *wm) {
     return __reduce_max_sync(0xffffffffu, v);
 }
 
-// Block-wide max of a key; every thread gets it.
-__device__ inline unsigned int block_max(unsigned int key, unsigned int *wmax) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    key = __reduce_max_sync(0xffffffffu, key);
-    if (lane == 0) wmax[warp] = key;
-    __syncthreads();
-    unsigned int v = lane < kCaluWarps ? wmax[lane] : 0u;
-    v = __reduce_max_sync(0xffffffffu, v);
-    __syncthreads();  // wmax may be reused right after
-    return v;
-}
-
 // Shared memory after the row cache: tournament panel entries, candidate row
-// ids and chosen flags, the winners' rows, and per-row flags.
+// ids, the winners' rows, and per-row flags.
 struct CaluLayout {
-    size_t tv, tid, tch, urows, pivd, total;
+    size_t tv, tid, urows, pivd, total;
 };
 
 // Every section starts on a 16-byte boundary (the row cache has an odd
@@ -96,7 +84,6 @@ __host__ __device__ inline CaluLayout calu_layout(int rows_max, int l) {
     size_t off = align16((size_t)rows_max * (l + 1) * sizeof(float));
     s.tv = off; off = align16(off + (size_t)kMaxCand * kPanel * sizeof(float));
     s.tid = off; off = align16(off + (size_t)kMaxCand * sizeof(int));
-    s.tch = off; off = align16(off + (size_t)kMaxCand);
     s.urows = off; off = align16(off + (size_t)kPanel * FRPCA_MAX_L * sizeof(float));
     s.pivd = off; off = align16(off + (size_t)rows_max);
     s.total = off;
@@ -117,8 +104,7 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int win_row[kPanel];
     __shared__ int win_slot[kPanel];
-    __shared__ unsigned int wmax[kCaluWarps];
-    __shared__ unsigned int wmax2[2][kCaluWarps];
+    __shared__ unsigned int wmax2[2][kCaluWarps];  // block-max tables, used alternately
     __shared__ float pvw[kPanel];  // the local pivot's panel entries
     __shared__ float pvr;          // 1 / the local pivot
     __shared__ float rdiag[kPanel];  // 1 / U(k, c0 + k) of the panel
@@ -132,7 +118,6 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
     float *cache = reinterpret_cast<float *>(smem);
     float *tv = reinterpret_cast<float *>(smem + L.tv);    // kPanel x candidate (column-major)
     int *tid = reinterpret_cast<int *>(smem + L.tid);      // candidate row ids (-1: none)
-    unsigned char *tch = smem + L.tch;                      // chosen in the tournament
     float *U = reinterpret_cast<float *>(smem + L.urows);  // kPanel x FRPCA_MAX_L: winners' rows
     unsigned char *pivd = smem + L.pivd;
     const int ncand = (int)G * kPanel;
