@@ -238,8 +238,10 @@ frpca_status frpca_gram_splitbf16(frpca_handle h, int64_t R, int l, const float 
 frpca_status frpca_eig(frpca_handle h, int n, const double *B, double *w, double *V);
 
 /* eigSVD (Alg. 2) of the R x l block M, R >= l: S ascending (l doubles),
- * V (l x l doubles), and U = M V diag(1./S) written over M.  Synchronizes;
- * FRPCA_ERR_RANK_DEFICIENT as in Sec. 3.1. */
+ * V (l x l doubles), and U = M V diag(1./S) written over M (for FP32 blocks
+ * with l <= 128, ld a multiple of 4 and M 16-byte aligned, that product runs
+ * on the tensor cores from split-BF16 operands with float accuracy).
+ * Synchronizes; FRPCA_ERR_RANK_DEFICIENT as in Sec. 3.1. */
 frpca_status frpca_eigsvd(frpca_handle h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt,
                           double *S, double *V);
 
