@@ -48,8 +48,8 @@ __device__ inline int dim_of(const int *dn, int n_static) { return dn ? *dn : n_
 // largest diagonal magnitude.  Writes the eigenvectors (columns) into X (ld).
 // A pair is rotated while |a_pq| > 2^-23 sqrt(|a_pp a_qq|) (the relative test
 // that lets Jacobi resolve small eigenvalues of a definite matrix to float
-// accuracy); the sweep loop stops at the first sweep without rotations or
-// after kJacobiMaxSweeps.  Rotations use the fast reciprocal and reciprocal
+// accuracy); the sweep loop stops when no pair passes that test at the start
+// of a sweep (the sweep would rotate nothing) or after kJacobiMaxSweeps.  Rotations use the fast reciprocal and reciprocal
 // square root: any rotation close to the exact one keeps the iteration
 // convergent, and its orthogonality error (a few ulps) is removed by the
 // double-precision refinement that follows.
@@ -138,6 +138,7 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
     float *P = smem_f;            // planes (x, y) at P + (2x + y) kJacobiPlane
     float *VP = P + 4 * kJacobiPlane;  // V planes top / bottom at VP + x vpl
     __shared__ float2 rot[2][FRPCA_MAX_L / 2];  // (c, s) per pair, by round parity
+    __shared__ float diagv[FRPCA_MAX_L];        // the diagonal, at the start of a sweep
     __shared__ unsigned long long maxdiag;      // bit pattern of max |B_ii| (monotone)
     __shared__ double scale;
     const int t = threadIdx.x;
@@ -229,12 +230,36 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
         rot[0][ra[0]] = o;
     }
     __syncthreads();
-    // The rotations of round r + 1 are computed during round r, so the
-    // convergence test looks at the rounds 1 .. n_p - 1 of each sweep plus
-    // round 0 of the next: any n_p - 1 consecutive rounds visit every pair once.
+    // The rotations of round r + 1 are computed during round r (round 0 of a
+    // sweep during the last round of the previous one).
     int cur = 0;
     for (int sweep = 0; sweep < kJacobiMaxSweeps; ++sweep) {
-        int rotated = 0;
+        // Every index is in its own slot here.  A sweep changes A only if some
+        // pair passes the rotation test now: until the first such pair comes up
+        // nothing has rotated, so it sees the values tested here.  Testing every
+        // pair once is therefore the same as running a sweep that rotates
+        // nothing, and the loop stops without it.
+        if (kind[0] == 1) {
+            diagv[2 * ra[0]] = v[0][0];
+            diagv[2 * ra[0] + 1] = v[0][3];
+        }
+        __syncthreads();
+        int need = 0;
+#pragma unroll
+        for (int u = 0; u < NI; ++u) {
+            if (kind[u] == 0) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float apq = v[u][e];
+                    const float app = diagv[2 * ra[u] + (e >> 1)], aqq = diagv[2 * rb[u] + (e & 1)];
+                    if (apq != 0.0f && apq * apq > 0x1p-46f * fabsf(app * aqq)) need = 1;
+                }
+            } else if (kind[u] == 1) {
+                const float apq = v[u][1];
+                if (apq != 0.0f && apq * apq > 0x1p-46f * fabsf(v[u][0] * v[u][3])) need = 1;
+            }
+        }
+        if (!__syncthreads_or(need)) break;
         for (int r = 0; r < m1; ++r) {
             const float2 *R = rot[cur];
 #pragma unroll
@@ -277,7 +302,7 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
                     v[0][1] = P[g[0][1]];
                     v[0][3] = P[g[0][3]];
                     float2 o;
-                    rotated |= jacobi_rotation(v[0][0], v[0][1], v[0][3], o);
+                    jacobi_rotation(v[0][0], v[0][1], v[0][3], o);
                     rot[cur ^ 1][ra[0]] = o;
                 }
             } else {
@@ -301,7 +326,6 @@ jacobi_f32_kernel(const int *dn, int n_static, const double *__restrict__ B, int
             cur ^= 1;
         }
         // After a whole sweep every index is back in its own slot.
-        if (!__syncthreads_or(rotated)) break;
     }
 #pragma unroll
     for (int u = 0; u < NI; ++u) {
