@@ -4,11 +4,12 @@
 //
 // GB300 has little double-precision throughput, so the result is reached in
 // stages that keep double-precision work in GEMMs spread over many SMs.
-//  (1) Cyclic Jacobi in float on the (scaled, rounded) matrix, resident in
-//      shared memory; each sweep visits all pairs in the round-robin order, so
-//      every round applies n/2 disjoint rotations at once (Golub and Van Loan,
-//      Matrix Computations, Sec. 8.5, parallel Jacobi).  A few CTAs repeat the
-//      same rotations and split the rows of the eigenvector accumulator.
+//  (1) Cyclic Jacobi in float on the (scaled, rounded) matrix, held in
+//      registers as a systolic array whose entries move through shared memory;
+//      each sweep visits all pairs in the round-robin order, so every round
+//      applies n/2 disjoint rotations at once (Golub and Van Loan, Matrix
+//      Computations, Sec. 8.5, parallel Jacobi).  Several CTAs repeat the same
+//      rotations and split the rows of the eigenvector accumulator.
 //  (2) The float eigenvectors X are refined in double by the iteration of
 //      Ogita and Aishima ("Iterative refinement for symmetric eigenvalue
 //      decomposition", Japan J. Indust. Appl. Math. 35, 2018): with

@@ -9,7 +9,8 @@
 // loads through the read-only path, accumulating in registers in CSR order.
 // Rows longer than `seg` entries are cut into segments whose partial rows are
 // summed in segment order by a fix-up kernel, so the result is deterministic
-// and no float atomics are used.
+// and no float atomics are used.  The lists of whole rows and segments (the
+// plan) are built once per matrix, on the device.
 #include <vector>
 
 #include "common.cuh"
