@@ -135,28 +135,21 @@ int or_spmm(int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
     return OR_OK;
 }
 
-/* A^T X by scattering row i of A: y_j += a_ij x_i, rows in ascending order, so
- * every output entry is summed over ascending i.  Threads own disjoint column
- * ranges of the l-wide block, never a shared output entry.                  */
+/* A^T X: row j of the result is the sum over the entries of column j of A,
+ * which the transpose lists in ascending row order, so every output entry is
+ * summed over ascending i.                                                   */
 int or_spmm_t(int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
               const double *vals, int64_t l, const double *X, int64_t ldx, double *Y, int64_t ldy) {
     if (m < 0 || n < 0 || l < 0 || ldx < l || ldy < l) return OR_ERR_INVALID_ARG;
-    for (int64_t j = 0; j < n; ++j)
-        for (int64_t c = 0; c < l; ++c) Y[j * ldy + c] = 0.0;
-    const int64_t chunk = 8;
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t c0 = 0; c0 < l; c0 += chunk) {
-        const int64_t c1 = c0 + chunk < l ? c0 + chunk : l;
-        for (int64_t i = 0; i < m; ++i) {
-            const double *x = X + i * ldx;
-            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-                const double a = vals[e];
-                double *y = Y + (int64_t)colidx[e] * ldy;
-                for (int64_t c = c0; c < c1; ++c) y[c] += a * x[c];
-            }
-        }
-    }
-    return OR_OK;
+    const int64_t nnz = rowptr[m];
+    int64_t *rowptrT = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int32_t *colidxT = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    double *valsT = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    int st = (rowptrT && colidxT && valsT) ? OR_OK : OR_ERR_OOM;
+    if (st == OR_OK) st = or_csr_transpose(m, n, rowptr, colidx, vals, rowptrT, colidxT, valsT);
+    if (st == OR_OK) st = or_spmm(n, m, rowptrT, colidxT, valsT, l, X, ldx, Y, ldy);
+    free(rowptrT); free(colidxT); free(valsT);
+    return st;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -284,18 +277,28 @@ int or_eig_sym(int64_t n, const double *B, double *w, double *V, int *sweeps_out
 }
 
 /* ------------------------------------------------------------------------ */
-/* Step 1 of Alg. 2: B = M^T M, each entry summed over ascending rows. */
+/* Step 1 of Alg. 2: B = M^T M, each entry summed over ascending rows.  The
+ * rows are visited in blocks small enough to stay in cache while every entry
+ * of a row of B takes its running sum through them; the order of the terms of
+ * each entry is unchanged.                                                   */
 int or_gram(int64_t R, int64_t l, const double *M, int64_t ld, double *B) {
     if (R < 0 || l < 0 || ld < l) return OR_ERR_INVALID_ARG;
+    const int64_t blk = 256;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t a = 0; a < l; ++a) {
-        for (int64_t b = a; b < l; ++b) {
-            double acc = 0.0;
-            for (int64_t i = 0; i < R; ++i) acc += M[i * ld + a] * M[i * ld + b];
-            B[a * l + b] = acc;
-            B[b * l + a] = acc;
+        double *acc = B + a * l;
+        for (int64_t b = a; b < l; ++b) acc[b] = 0.0;
+        for (int64_t i0 = 0; i0 < R; i0 += blk) {
+            const int64_t i1 = i0 + blk < R ? i0 + blk : R;
+            for (int64_t b = a; b < l; ++b) {
+                double s = acc[b];
+                for (int64_t i = i0; i < i1; ++i) s += M[i * ld + a] * M[i * ld + b];
+                acc[b] = s;
+            }
         }
     }
+    for (int64_t a = 0; a < l; ++a)
+        for (int64_t b = a + 1; b < l; ++b) B[b * l + a] = B[a * l + b];
     return OR_OK;
 }
 
@@ -408,11 +411,17 @@ int or_frpca_ex(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int3
     double *W = (double *)malloc(sizeof(double) * (size_t)(rw * l));
     double *Sh = (double *)malloc(sizeof(double) * (size_t)l);
     double *Vh = (double *)malloc(sizeof(double) * (size_t)(l * l));
-    int st = (Q && W && Sh && Vh) ? OR_OK : OR_ERR_OOM;
+    /* A^T, built once: A^T X is the row-by-row product with it (or_spmm_t). */
+    const int64_t nnz = rowptr[m];
+    int64_t *rowptrT = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int32_t *colidxT = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    double *valsT = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    int st = (Q && W && Sh && Vh && rowptrT && colidxT && valsT) ? OR_OK : OR_ERR_OOM;
+    if (st == OR_OK) st = or_csr_transpose(m, n, rowptr, colidx, vals, rowptrT, colidxT, valsT);
     /* "forward" product: A X for Alg. 6, A^T X for Alg. 5 (and the reverse). */
 #define FWD(Xin, Yout) ((alg == 6) ? or_spmm(m, n, rowptr, colidx, vals, l, Xin, l, Yout, l) \
-                                   : or_spmm_t(m, n, rowptr, colidx, vals, l, Xin, l, Yout, l))
-#define BWD(Xin, Yout) ((alg == 6) ? or_spmm_t(m, n, rowptr, colidx, vals, l, Xin, l, Yout, l) \
+                                   : or_spmm(n, m, rowptrT, colidxT, valsT, l, Xin, l, Yout, l))
+#define BWD(Xin, Yout) ((alg == 6) ? or_spmm(n, m, rowptrT, colidxT, valsT, l, Xin, l, Yout, l) \
                                    : or_spmm(m, n, rowptr, colidx, vals, l, Xin, l, Yout, l))
     if (st == OR_OK) {
         if (q % 2 == 0) {
@@ -459,7 +468,7 @@ int or_frpca_ex(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int3
     }
 #undef FWD
 #undef BWD
-    free(Q); free(W); free(Sh); free(Vh);
+    free(Q); free(W); free(Sh); free(Vh); free(rowptrT); free(colidxT); free(valsT);
     return st;
 }
 
