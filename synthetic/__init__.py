@@ -12,7 +12,9 @@ Recipe of ``powerlaw_csr(m, n, deg_mean, zipf_s, values, seed)``:
   2. column ranks drawn from P(r) proportional to (r+1)^-s, r in [0, n), without
      replacement inside a row (duplicates redrawn), then mapped through a
      seeded random permutation of [0, n) so hot columns are scattered; rows
-     are sorted;
+     are sorted; rows are drawn in blocks of 65,536, each block from its own
+     Philox stream (threads build blocks in parallel; the matrix does not
+     depend on their number);
   3. values: "tfidf": log(1 + c) * log(m / df_j), c ~ Poisson(2) conditioned on
      c >= 1, df_j the column count; "binary_tfidf": log(m / df_j); "uniform":
      U(0, 1).  A column present in every row gets value 0 (kept as a
@@ -88,51 +90,84 @@ def _zipf_cdf(n: int, s: float) -> np.ndarray:
     return c / c[-1]
 
 
+# Rows are generated in fixed blocks, each from its own Philox stream, so the
+# matrix does not depend on how many threads build it.
+_ROW_BLOCK = 1 << 16
+
+
+def _block_rng(seed: int, purpose: int, block: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=np.array([seed, (purpose << 32) | block], dtype=np.uint64)))
+
+
+def _powerlaw_block(b, r0, r1, indptr, n, cdf, perm, seed, cols_out):
+    """Columns of rows r0 .. r1-1: Zipf ranks without repeats inside a row,
+    mapped through perm, sorted within each row; written into cols_out."""
+    rng = _block_rng(seed, 11, b)
+    p0, p1 = int(indptr[r0]), int(indptr[r1])
+    cnt = p1 - p0
+    if cnt == 0:
+        return
+
+    def draw(k):
+        r = np.searchsorted(cdf, rng.random(k), side="right")
+        return np.minimum(r, n - 1).astype(np.int64)
+
+    rows = np.repeat(np.arange(r1 - r0, dtype=np.int64), np.diff(indptr[r0:r1 + 1]))
+    key = rows * n + draw(cnt)
+    # Redraw repeated (row, rank) pairs until every row's ranks are distinct.
+    while True:
+        key.sort()
+        dup = np.flatnonzero(key[1:] == key[:-1]) + 1
+        if dup.size == 0:
+            break
+        key[dup] = (key[dup] // n) * n + draw(dup.size)
+    key = rows * n + perm[key % n]
+    key.sort()
+    cols_out[p0:p1] = (key % n).astype(np.int32)
+
+
 def powerlaw_csr(m: int, n: int, deg_mean: float, zipf_s: float, values: str = "tfidf",
-                 seed: int = 1, dtype=np.float32, sigma_ln: float = 1.0) -> CSR:
-    rng_deg, rng_col, rng_perm, rng_val = (_rng(seed, p) for p in (10, 11, 12, 13))
+                 seed: int = 1, dtype=np.float32, sigma_ln: float = 1.0, threads: int | None = None) -> CSR:
+    import concurrent.futures
+    import os
+
+    rng_deg, rng_perm = _rng(seed, 10), _rng(seed, 12)
     mu = np.log(deg_mean) - 0.5 * sigma_ln ** 2
     deg = np.clip(np.rint(rng_deg.lognormal(mu, sigma_ln, size=m)), 1, n).astype(np.int64)
     indptr = np.zeros(m + 1, dtype=np.int64)
     np.cumsum(deg, out=indptr[1:])
     nnz = int(indptr[-1])
-    rows = np.repeat(np.arange(m, dtype=np.int64), deg)
     cdf = _zipf_cdf(n, zipf_s)
-
-    def draw(count):
-        r = np.searchsorted(cdf, rng_col.random(count), side="right")
-        return np.minimum(r, n - 1).astype(np.int64)
-
-    ranks = draw(nnz)
-    # Redraw repeated (row, rank) pairs until every row's ranks are distinct.
-    key = rows * n + ranks
-    while True:
-        order = np.argsort(key, kind="stable")
-        key = key[order]
-        dup = np.flatnonzero(key[1:] == key[:-1]) + 1
-        if dup.size == 0:
-            break
-        r_dup = key[dup] // n
-        key[dup] = r_dup * n + draw(dup.size)
-    ranks = key % n
     perm = rng_perm.permutation(n).astype(np.int64)
-    cols = perm[ranks]
-    key = rows * n + cols
-    key.sort()
-    cols = (key % n).astype(np.int32)
+    cols = np.empty(nnz, dtype=np.int32)
+    blocks = [(b, r0, min(m, r0 + _ROW_BLOCK)) for b, r0 in enumerate(range(0, m, _ROW_BLOCK))]
+    workers = threads or min(16, os.cpu_count() or 1)
+    if workers > 1 and len(blocks) > 1:
+        with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+            list(ex.map(lambda t: _powerlaw_block(*t, indptr, n, cdf, perm, seed, cols), blocks))
+    else:
+        for t in blocks:
+            _powerlaw_block(*t, indptr, n, cdf, perm, seed, cols)
     df = np.bincount(cols, minlength=n).astype(np.float64)
     idf = np.log(m / np.maximum(df, 1.0))
     if values == "tfidf":
-        c = rng_val.poisson(2.0, size=nnz)
-        zero = np.flatnonzero(c == 0)
-        while zero.size:
-            c[zero] = rng_val.poisson(2.0, size=zero.size)
-            zero = zero[c[zero] == 0]
-        vals = np.log1p(c.astype(np.float64)) * idf[cols]
+        vals = np.empty(nnz, dtype=np.float64)
+        for b, r0, r1 in blocks:
+            p0, p1 = int(indptr[r0]), int(indptr[r1])
+            rng_val = _block_rng(seed, 13, b)
+            c = rng_val.poisson(2.0, size=p1 - p0)
+            zero = np.flatnonzero(c == 0)
+            while zero.size:
+                c[zero] = rng_val.poisson(2.0, size=zero.size)
+                zero = zero[c[zero] == 0]
+            vals[p0:p1] = np.log1p(c.astype(np.float64)) * idf[cols[p0:p1]]
     elif values == "binary_tfidf":
         vals = idf[cols]
     elif values == "uniform":
-        vals = rng_val.random(nnz)
+        vals = np.empty(nnz, dtype=np.float64)
+        for b, r0, r1 in blocks:
+            p0, p1 = int(indptr[r0]), int(indptr[r1])
+            vals[p0:p1] = _block_rng(seed, 13, b).random(p1 - p0)
     else:
         raise ValueError(values)
     return CSR(m, n, indptr, cols, vals.astype(dtype))
