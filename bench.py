@@ -1,14 +1,17 @@
 #!/usr/bin/env python
 """Benchmark of the frPCA hot path on GB300.
 
-One step = one pass of the whole method over the resident 200,000 x 50,000
-power-law CSR (~20M nnz, tf-idf-like FP32 values): the device A^T rebuild, the
-Gaussian test matrix, q = 5 SpMM passes with A and A^T, LU, two eigSVDs and the
-final products (k = 100, l = 120, FP32 path, Alg. 6).  Metric: seconds per
-rank-k frPCA run (lower is better), device-timed with CUDA events.  The JSON
-line also carries the SpMM passes' HBM roofline (algorithmic bytes over their
-measured device time), an end-to-end time through the public API with host
-buffers, and the FP64 CPU oracle timed on the host cores.
+One step = one pass of the whole method over the resident 12,000,000 x 320,000
+power-law CSR (~480M nnz, binary tf-idf FP32 values, int32 column indices, A
+and A^T resident): the device A^T rebuild, the Gaussian test matrix, q = 5
+SpMM passes with A and A^T, LU, two eigSVDs and the final products (k = 100,
+l = 120, FP32 path, Alg. 6).  Metric: seconds per rank-k frPCA run (lower is
+better), device-timed with CUDA events.  The JSON line also carries the SpMM
+passes' HBM roofline (algorithmic bytes over their measured device time), an
+end-to-end time through the C ABI's host-array path (the library copies the
+CSR to the device itself; U, S, V are read back), the FP64 CPU oracle timed on
+the host cores over a bounded row sample, and the 200,000 x 50,000 workload
+with every precision form and its errors against the oracle.
 
 Multi-GPU (torchrun): every rank runs its own independent problem (weak
 scaling, no collective on the data path); the time is the max over ranks.
@@ -28,16 +31,19 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "powerlaw_200000x50000_deg100"
+WORKLOAD = "powerlaw_12000000x320000_deg40"
+SIDE_WORKLOAD = "powerlaw_200000x50000_deg100"
 BWD_WORKLOAD = "powerlaw_100000x20000_deg50"
 L2_BYTES = 129 * 2**20
 PRECISIONS = ("fp32", "fp64", "fp32_splitgram")
 
 # DRAM traffic of one SpMM pass (dram__bytes_read.sum + dram__bytes_write.sum),
 # averaged over the q = 5 schedule (3 passes with A, 2 with A^T), from an ncu
-# capture of one step's five spmm_kernel launches on this workload.  Valid only
-# while spmm_kernel is unchanged since that capture.
-NCU_SPMM_TRAFFIC = {(WORKLOAD, "f32", 5): (275.9e6 + 1486.6e6 + 272.7e6 + 1486.6e6 + 272.5e6) / 5}
+# capture of one step's SpMM launches on the workload.  An entry is valid only
+# while the SpMM kernels are unchanged since that capture.
+NCU_SPMM_TRAFFIC = {}
+# Rows of the headline workload the oracle runs on for the CPU baseline.
+ORACLE_SAMPLE_ROWS = {WORKLOAD: 500_000}
 
 
 def _max_sine(X, Y):
@@ -139,23 +145,54 @@ def _max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def _row_sample(A, rows):
+    """The first `rows` rows of a CSR (all columns): the bounded sample of the
+    workload that the oracle runs on."""
+    import synthetic
+    r = min(rows, A.m)
+    p = int(A.indptr[r])
+    return synthetic.CSR(r, A.n, A.indptr[:r + 1].copy(), A.indices[:p], A.data[:p])
+
+
+def _oracle_sample_run(A, k, l, q):
+    """One FP64 oracle frPCA run on the workload, or on its leading row block
+    when the workload is large; returns (seconds scaled to the whole workload,
+    description).  The scaling is linear in rows: every pass, Gram and apply
+    over the m side grows with the rows, while the n-side LU and the l x l eig
+    do not, so the scaled figure slightly overstates the oracle's time."""
+    import oracle
+    rows = ORACLE_SAMPLE_ROWS.get(_CURRENT_WORKLOAD[0])
+    B = A if not rows or rows >= A.m else _row_sample(A, rows)
+    t0 = time.perf_counter()
+    oracle.frpca(B.m, B.n, B.indptr, B.indices, B.data.astype(np.float64), k, l, q, 0)
+    dt = time.perf_counter() - t0
+    if B is A:
+        return dt, {"sample": f"the whole workload, one FP64 frPCA run (q={q})", "sample_s": dt, "scale": 1.0}
+    scale = A.m / B.m
+    return dt * scale, {"sample": (f"one FP64 frPCA run (q={q}) on the first {B.m:,} of {A.m:,} rows "
+                                   f"({B.nnz:,} of {A.nnz:,} nnz, all {A.n:,} columns), time scaled by "
+                                   f"the row ratio {scale:.2f}"), "sample_s": dt, "scale": scale}
+
+
+_CURRENT_WORKLOAD = [WORKLOAD]
+
+
 def run_reference(args, world, rank):
-    """The FP64 CPU oracle as it stands, on the host cores, same workload."""
+    """The FP64 CPU oracle as it stands, on the host cores, same workload
+    (each step one bounded sample of it, scaled to the whole workload)."""
     if rank != 0:
         return 0
     import oracle
     import synthetic
     oracle.build()
+    _CURRENT_WORKLOAD[0] = args.workload
     w = synthetic.WORKLOADS[args.workload]
     A = synthetic.make_workload(args.workload, seed=1)
-    vals = A.data.astype(np.float64)
-    times = []
+    times, info = [], None
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        oracle.frpca(A.m, A.n, A.indptr, A.indices, vals, w["k"], w["l"], args.q, 0)
-        dt = time.perf_counter() - t0
+        v, info = _oracle_sample_run(A, w["k"], w["l"], args.q)
         if i >= args.warmup:
-            times.append(dt)
+            times.append(v)
     v = float(np.mean(times))
     cores = oracle.num_threads()
     line = {
@@ -163,8 +200,8 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(args, w),
-        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
-                         "sample": f"the whole workload, one frPCA run per step (q={args.q})"},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": info["sample"],
+                         "sample_s": info["sample_s"]},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -242,6 +279,87 @@ def _fwd_bwd(dev, with_ref: bool) -> dict:
     return out
 
 
+def _roofline(st, peak, peak_kind, traffic):
+    passes = max(st["spmm_passes"], 1)
+    ms_pass = st["spmm_ms"] / passes
+    bytes_pass = st["spmm_bytes"] / passes
+    achieved = bytes_pass / (ms_pass * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "spmm_kernel (+ fix-up), one SpMM pass", "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "ms_per_pass": ms_pass, "bytes_per_pass": bytes_pass,
+            "fp32_tflops": st["spmm_flops"] / max(st["spmm_ms"], 1e-9) / 1e9}
+
+
+def _timed_steps(mat, k, l, q, precision, steps, warmup, stream, U, S, V):
+    """warmup untimed steps, then `steps` timed ones (A^T rebuild + run), CUDA
+    events on the handle's stream; returns (ms per step, library stats)."""
+    import torch
+
+    import paper_1810_06825_gb300 as frpca
+
+    def step():
+        mat.refresh()
+        mat.run(k, l, q, seed=0, precision=precision, out=(U, S, V), sync=False)
+
+    for _ in range(warmup):
+        step()
+    frpca.frpca_sync(mat.handle)
+    mat.set_timing(True)
+    mat.reset_stats()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    frpca.frpca_sync(mat.handle)
+    st = mat.stats()
+    mat.set_timing(False)
+    return e0.elapsed_time(e1) / steps, st
+
+
+PHASES = ("spmm_ms", "lu_ms", "gram_ms", "eig_ms", "apply_ms", "gaussian_ms", "transpose_ms", "finish_ms")
+
+
+def _side_workload(dev, stream, args, peak, peak_kind, with_ref: bool) -> dict:
+    """The 200,000 x 50,000 workload (~20M nnz): every precision form's device
+    time per step and, when the oracle runs, its errors against the FP64
+    oracle on the same Gaussian test matrix; the FP32 form's phases and SpMM
+    roofline."""
+    import torch
+
+    import paper_1810_06825_gb300 as frpca
+    import synthetic
+
+    w = synthetic.WORKLOADS[SIDE_WORKLOAD]
+    k, l, q = w["k"], w["l"], 5
+    A = synthetic.make_workload(SIDE_WORKLOAD, seed=1, dtype=np.float32)
+    mat = frpca.FrPCA.from_csr(A, device=dev, stream=stream)
+    ref = None
+    if with_ref:
+        import oracle
+        oracle.build()
+        ref = oracle.frpca(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64), k, l, q, 0)
+    out = {"workload": SIDE_WORKLOAD, "m": A.m, "n": A.n, "nnz": int(A.nnz), "k": k, "l": l, "q": q}
+    S = torch.empty((k,), dtype=torch.float64, device=dev)
+    for prec in PRECISIONS:
+        pdt = torch.float64 if prec == "fp64" else torch.float32
+        Up = torch.empty((A.m, k), dtype=pdt, device=dev)
+        Vp = torch.empty((A.n, k), dtype=pdt, device=dev)
+        ms, st = _timed_steps(mat, k, l, q, prec, 10 if prec != "fp64" else 5, 3, stream, Up, S, Vp)
+        entry = {"ms_per_step": ms}
+        if prec == "fp32":
+            entry["phases_ms_per_step"] = {key: st[key] / 10 for key in PHASES}
+            entry["roofline"] = _roofline(st, peak, peak_kind, NCU_SPMM_TRAFFIC.get((SIDE_WORKLOAD, "f32", q)))
+        if ref is not None:
+            entry.update(_errors(Up.double().cpu().numpy(), S.cpu().numpy(), Vp.double().cpu().numpy(), ref))
+        out[prec] = entry
+    out["errors_vs"] = "FP64 CPU oracle, same Philox Omega" if ref is not None else None
+    mat.close()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -250,49 +368,36 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    _CURRENT_WORKLOAD[0] = args.workload
     w = synthetic.WORKLOADS[args.workload]
     k, l, q = w["k"], w["l"], args.q
-    dt_np = np.float32  # the workload's values are FP32; the FP64 path converts them once
-    A = synthetic.make_workload(args.workload, seed=1 + rank, dtype=dt_np)
-    indptr = torch.from_numpy(A.indptr).to(dev)
-    indices = torch.from_numpy(A.indices).to(dev)
-    values = torch.from_numpy(A.data).to(dev)
+    A = synthetic.make_workload(args.workload, seed=1 + rank, dtype=np.float32)
     stream = torch.cuda.current_stream()
-    mat = frpca.FrPCA(indptr, indices, values, (A.m, A.n), stream=stream)
     tdt = torch.float64 if args.precision == "fp64" else torch.float32
+    peak, peak_kind = _peaks()
+
+    # Device-resident run: the CSR is copied to the device before the timed
+    # region; every timed step rebuilds A^T and runs the whole method.
+    mat = frpca.FrPCA.from_csr(A, device=dev, stream=stream)
     U = torch.empty((A.m, k), dtype=tdt, device=dev)
     S = torch.empty((k,), dtype=torch.float64, device=dev)
     V = torch.empty((A.n, k), dtype=tdt, device=dev)
-
-    def step():
-        mat.refresh()
-        mat.run(k, l, q, seed=0, precision=args.precision, out=(U, S, V), sync=False)
-
-    for _ in range(args.warmup):
-        step()
-    frpca.frpca_sync(mat.handle)
-    mat.set_timing(True)
-    mat.reset_stats()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     _barrier(world)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms, st = _timed_steps(mat, k, l, q, args.precision, args.steps, args.warmup, stream, U, S, V)
     _barrier(world)
     clk = clocks.stop()
-    frpca.frpca_sync(mat.handle)
-    ms = e0.elapsed_time(e1) / args.steps
-    st = mat.stats()
     ms_max = _max_over_ranks(ms, world)
+    mat.close()
+    del mat, U, V
+    torch.cuda.empty_cache()
 
-    # End to end through the public API: pinned host CSR -> device, create the
-    # handle (validation + A^T + plan), run, read U, S, V back.
+    # End to end through the C ABI's host-array path: pinned host CSR handed to
+    # frpca_create (the library copies it to the device, validates it there,
+    # builds A^T and the SpMM plans), frpca_run, U, S, V read back into pinned
+    # host buffers, frpca_destroy.
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
@@ -300,18 +405,18 @@ def run_ours(args, world, rank, local):
         h_U = torch.empty((A.m, k), dtype=tdt).pin_memory()
         h_S = torch.empty((k,), dtype=torch.float64).pin_memory()
         h_V = torch.empty((A.n, k), dtype=tdt).pin_memory()
+        d_U = torch.empty((A.m, k), dtype=tdt, device=dev)
+        d_S = torch.empty((k,), dtype=torch.float64, device=dev)
+        d_V = torch.empty((A.n, k), dtype=tdt, device=dev)
         h2d = h_ip.numel() * 8 + h_ix.numel() * 4 + h_v.numel() * h_v.element_size()
         d2h = h_U.numel() * h_U.element_size() + h_S.numel() * 8 + h_V.numel() * h_V.element_size()
 
         def e2e_step():
-            d_ip = h_ip.to(dev, non_blocking=True)
-            d_ix = h_ix.to(dev, non_blocking=True)
-            d_v = h_v.to(dev, non_blocking=True)
-            m2 = frpca.FrPCA(d_ip, d_ix, d_v, (A.m, A.n), stream=stream)
-            Ud, Sd, Vd = m2.run(k, l, q, seed=0, precision=args.precision, sync=False)
-            h_U.copy_(Ud, non_blocking=True)
-            h_S.copy_(Sd, non_blocking=True)
-            h_V.copy_(Vd, non_blocking=True)
+            m2 = frpca.FrPCA.from_host(h_ip, h_ix, h_v, (A.m, A.n), device=dev, stream=stream)
+            m2.run(k, l, q, seed=0, precision=args.precision, out=(d_U, d_S, d_V), sync=False)
+            h_U.copy_(d_U, non_blocking=True)
+            h_S.copy_(d_S, non_blocking=True)
+            h_V.copy_(d_V, non_blocking=True)
             frpca.frpca_sync(m2.handle)
             m2.close()
 
@@ -325,71 +430,38 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         e2e_s = _max_over_ranks((time.perf_counter() - t0) / n_e2e, world)
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "steps": n_e2e}
+               "steps": n_e2e, "path": "frpca_create from pinned host arrays (on_device = 0), frpca_run, "
+                                       "U, S, V to pinned host, frpca_destroy"}
+        del h_ip, h_ix, h_v, h_U, h_V, d_U, d_V
+        torch.cuda.empty_cache()
 
-    peak, peak_kind = _peaks()
-    spmm_ms_per_pass = st["spmm_ms"] / max(st["spmm_passes"], 1)
-    achieved = (st["spmm_bytes"] / max(st["spmm_passes"], 1)) / (spmm_ms_per_pass * 1e-3) / 1e9
-    dtype_tag = "f64" if args.precision == "fp64" else "f32"
-    roofline = {"bound": "hbm", "kernel": "spmm_kernel (+ fix-up), one SpMM pass", "achieved": achieved,
-                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": NCU_SPMM_TRAFFIC.get((args.workload, dtype_tag, args.q)), "ms_per_pass": spmm_ms_per_pass,
-                "bytes_per_pass": st["spmm_bytes"] / max(st["spmm_passes"], 1),
-                "fp32_tflops": st["spmm_flops"] / max(st["spmm_ms"], 1e-9) / 1e9}
-    # What bounds the pass on this workload: every nonzero brings one l-wide row
-    # of the dense block from L1/L2 into registers, and the L1 load path moves
-    # at most 128 bytes per clock per SM.
+    roofline = _roofline(st, peak, peak_kind, NCU_SPMM_TRAFFIC.get((args.workload, "f32", q)))
+    # What bounds the pass: every nonzero brings one l-wide row of the dense
+    # block from L1/L2 into registers, and the L1 load path moves at most 128
+    # bytes per clock per SM.
     vsize = 8 if args.precision == "fp64" else 4
     gathered = A.nnz * l * vsize
     sm_clock = (clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0) * 1e6
     l1_peak = torch.cuda.get_device_properties(local).multi_processor_count * 128 * sm_clock / 1e9
-    gather_achieved = gathered / (spmm_ms_per_pass * 1e-3) / 1e9
+    gather_achieved = gathered / (roofline["ms_per_pass"] * 1e-3) / 1e9
     gather_roofline = {"bound": "l1_load_path", "kernel": "spmm_kernel, one SpMM pass",
                        "gathered_bytes_per_pass": gathered, "achieved": gather_achieved, "peak": l1_peak,
                        "unit": "GB/s", "frac": gather_achieved / l1_peak,
                        "peak_basis": "SMs x 128 B per clock x median SM clock under load"}
-    phases = {key: st[key] / args.steps for key in ("spmm_ms", "lu_ms", "gram_ms", "eig_ms", "apply_ms",
-                                                    "gaussian_ms", "transpose_ms", "finish_ms")}
+    phases = {key: st[key] / args.steps for key in PHASES}
 
-    cpu, ref = None, None
+    cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        vals = A.data.astype(np.float64)
-        t0 = time.perf_counter()
-        ref = oracle.frpca(A.m, A.n, A.indptr, A.indices, vals, k, l, q, 0)
-        cpu_s = time.perf_counter() - t0
-        cpu = {"value": cpu_s, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": f"the whole workload, one FP64 frPCA run (q={q})"}
+        v, info = _oracle_sample_run(A, k, l, q)
+        cpu = {"value": v, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle", "sample": info["sample"],
+               "sample_s": info["sample_s"]}
+    del A
 
-    # The precision forms side by side on the same matrix: device time of one
-    # step (A^T rebuild + run) and, when the oracle ran, the error against it.
-    forms = None
+    side = None
     if rank == 0 and not args.no_forms:
-        forms = {}
-        for prec in PRECISIONS:
-            pdt = torch.float64 if prec == "fp64" else torch.float32
-            Up = torch.empty((A.m, k), dtype=pdt, device=dev)
-            Vp = torch.empty((A.n, k), dtype=pdt, device=dev)
-
-            def pstep():
-                mat.refresh()
-                mat.run(k, l, q, seed=0, precision=prec, out=(Up, S, Vp), sync=False)
-
-            for _ in range(3):
-                pstep()
-            frpca.frpca_sync(mat.handle)
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            for _ in range(5):
-                pstep()
-            a1.record(stream)
-            frpca.frpca_sync(mat.handle)
-            entry = {"ms_per_step": a0.elapsed_time(a1) / 5}
-            if ref is not None:
-                entry.update(_errors(Up.double().cpu().numpy(), S.cpu().numpy(), Vp.double().cpu().numpy(), ref))
-            forms[prec] = entry
-        forms["errors_vs"] = "FP64 CPU oracle, same Philox Omega" if ref is not None else None
+        side = _side_workload(dev, stream, args, peak, peak_kind, with_ref=not args.no_cpu_baseline)
 
     fwd_bwd = None
     if rank == 0 and not args.no_fwd_bwd:
@@ -403,10 +475,9 @@ def run_ours(args, world, rank, local):
             "config": _config(args, w), "roofline": roofline, "gather_roofline": gather_roofline,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(st["kernel_launches"]), "clocks": clk, "phases_ms_per_step": phases,
-            "nnz": int(A.nnz), "precision_forms": forms, "fwd_bwd": fwd_bwd,
+            "nnz": int(gathered // (l * vsize)), "workload_200000x50000": side, "fwd_bwd": fwd_bwd,
         }
         print(json.dumps(line), flush=True)
-    mat.close()
     return 0
 
 

@@ -46,6 +46,10 @@ typedef enum frpca_status {
 
 typedef enum frpca_dtype { FRPCA_F32 = 0, FRPCA_F64 = 1 } frpca_dtype;
 
+/* Element type of the CSR row pointers.  Either way nnz < 2^31; the library
+ * keeps its own int64 copy of int32 row pointers. */
+typedef enum frpca_index { FRPCA_I64 = 0, FRPCA_I32 = 1 } frpca_index;
+
 /* Arithmetic of a run.  FP64: every step in double.  FP32: SpMM, LU, Gram and
  * the apply step in float (the apply step, Y = M W with l, k <= 128, on the
  * tensor cores from split-BF16 operands: every product exact, accumulated in
@@ -67,11 +71,13 @@ typedef struct frpca_ctx *frpca_handle;
  * transpose that Alg. 5/6 multiply by is built on the device. */
 typedef struct frpca_csr {
     int64_t m, n, nnz;        /* 1 <= m, n < 2^31; 0 <= nnz < 2^31                         */
-    const int64_t *rowptr;    /* m + 1 entries                                              */
+    const void *rowptr;       /* m + 1 entries of type rowptr_type                          */
     const int32_t *colidx;    /* nnz entries                                                */
     const void *values;       /* nnz entries of type dtype                                  */
     frpca_dtype dtype;
-    int on_device;            /* 1: the three arrays are device pointers; 0: host pointers  */
+    int on_device;            /* 1: the three arrays are device pointers; 0: host pointers
+                                 (copied to the device at create, then validated there)     */
+    frpca_index rowptr_type;  /* FRPCA_I64 (0, the default) or FRPCA_I32                    */
 } frpca_csr;
 
 typedef struct frpca_create_opts {
@@ -86,13 +92,21 @@ typedef struct frpca_create_opts {
                                  kernel alone is faster), -1 = automatic (columns holding
                                  >= 5% of the rows, up to 256, in multiples of 128), > 0 =
                                  that many (rounded down to 128, at most 256)              */
+    int64_t max_device_bytes; /* 0 = no cap; otherwise the most device memory the handle
+                                 may allocate for itself (copies of A, A^T, work blocks,
+                                 workspaces; the caller's buffers are not counted).  An
+                                 allocation that would pass it fails with FRPCA_ERR_OOM,
+                                 as a failed cudaMallocAsync does                          */
 } frpca_create_opts;
 
 /* Creates a handle.  csr may be NULL: the handle then serves only the
  * step-level entry points below that take no matrix.  With a matrix, the
- * structure is validated (FRPCA_ERR_INVALID_CSR), values are copied or borrowed,
+ * arrays are copied (host arrays always; device arrays unless borrowed) or
+ * borrowed, the structure is validated on the device (FRPCA_ERR_INVALID_CSR),
  * and the CSR of A^T is built on the device (stable: each row of A^T lists the
- * rows of A in ascending order).  Synchronizes the stream. */
+ * rows of A in ascending order).  int32 row pointers are widened into a
+ * handle-owned int64 copy even when the other arrays are borrowed.
+ * Synchronizes the stream. */
 frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, frpca_handle *out);
 
 /* Frees every device buffer the handle owns.  Accepts NULL. */
@@ -155,6 +169,17 @@ frpca_status frpca_set_timing(frpca_handle h, int enable);
 frpca_status frpca_get_stats(frpca_handle h, frpca_stats *out);
 frpca_status frpca_reset_stats(frpca_handle h);
 
+/* Limit, in SM clock cycles, of each bounded device-side wait in the grid-wide
+ * barriers of the LU kernels (frpca_lu, frpca_lu_tournament and the LU steps of
+ * frpca_run) and of the eigensolver's refinement.  A wait that runs out makes
+ * its block record FRPCA_ERR_TIMEOUT and leave the kernel, so a block that
+ * never arrives cannot hang the GPU; the call then returns FRPCA_ERR_TIMEOUT
+ * and the handle stays usable.  cycles <= 0 restores the default (about one
+ * second at GB300 clocks).  The tensor-core kernels' waits on their MMA
+ * completion keep the default: ending one early could leave tensor-core work
+ * in flight. */
+frpca_status frpca_set_wait_limit(frpca_handle h, int64_t cycles);
+
 /* ---- step-level entry points (device pointers, handle's stream) ------------ */
 
 /* Gaussian test matrix randn (Sec. 2.2; drawn as in Alg. 5/6 steps 2 and 6):
@@ -208,13 +233,16 @@ frpca_status frpca_lu_tournament(frpca_handle h, int64_t R, int l, float *M, int
  * caller's; the result is exactly that of frpca_lu.  The kernel's scratch (grid
  * barrier, pivot candidates, status word) lives in one static 64 KiB device
  * array that every GPU loading this library holds until the process exits.
- * Limits: 1 <= l <= 160 and R <= 8192 times the number of SMs; larger sizes
- * return FRPCA_ERR_INVALID_ARG with a message from frpca_last_error(NULL).
- * The first call on each device looks up the array's device address once
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call shares the one array and clears the parts that must start at
- * zero, so calls that overlap on the GPU (other streams, other host threads)
- * race: serialize them.  Synchronizes the stream to read the status. */
+ * Limits: 1 <= l <= 160 and R <= 8192 times the number of SMs; l > 160
+ * returns FRPCA_ERR_UNSUPPORTED (as frpca_lu does) and a larger R
+ * FRPCA_ERR_INVALID_ARG, with a message from frpca_last_error(NULL).
+ * Every call looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, a host-side query that allocates nothing), so a
+ * context that was reset and created again is handled; the first call in a
+ * context loads the library's device code, so make it before any stream
+ * capture.  Every call shares the one array and clears the parts that must
+ * start at zero, so calls that overlap on the GPU (other streams, other host
+ * threads) race: serialize them.  Synchronizes the stream to read the status. */
 frpca_status frpca_lu_noalloc(int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv, void *stream);
 
 /* Step 1 of eigSVD (Alg. 2): B = M^T M, l x l double (ld l), M R x l.  FP32

@@ -22,13 +22,14 @@ STATUS_NAMES = {
     6: "RANK_DEFICIENT", 7: "TIMEOUT", 8: "NOT_CONVERGED", 9: "UNSUPPORTED",
 }
 FRPCA_F32, FRPCA_F64 = 0, 1
+FRPCA_I64, FRPCA_I32 = 0, 1
 PREC = {"fp64": 0, "fp32": 1, "fp32_splitgram": 2}
 
 EXPORTED = [
     "frpca_create", "frpca_destroy", "frpca_last_error", "frpca_run", "frpca_run_async", "frpca_sync",
     "frpca_refresh", "frpca_set_timing", "frpca_get_stats", "frpca_reset_stats",
     "frpca_gaussian", "frpca_spmm", "frpca_get_transpose", "frpca_lu", "frpca_gram", "frpca_eig",
-    "frpca_eigsvd", "frpca_backward", "frpca_gram_splitbf16", "frpca_lu_tournament",
+    "frpca_eigsvd", "frpca_backward", "frpca_gram_splitbf16", "frpca_lu_tournament", "frpca_set_wait_limit",
 ]
 
 
@@ -41,12 +42,12 @@ class FrpcaError(RuntimeError):
 class frpca_csr(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("values", ctypes.c_void_p),
-                ("dtype", ctypes.c_int), ("on_device", ctypes.c_int)]
+                ("dtype", ctypes.c_int), ("on_device", ctypes.c_int), ("rowptr_type", ctypes.c_int)]
 
 
 class frpca_create_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("borrow", ctypes.c_int), ("validate", ctypes.c_int),
-                ("hot_columns", ctypes.c_int)]
+                ("hot_columns", ctypes.c_int), ("max_device_bytes", ctypes.c_int64)]
 
 
 class frpca_run_opts(ctypes.Structure):
@@ -87,6 +88,7 @@ def library() -> ctypes.CDLL:
         "frpca_set_timing": [P, I],
         "frpca_get_stats": [P, P],
         "frpca_reset_stats": [P],
+        "frpca_set_wait_limit": [P, I64],
         "frpca_gaussian": [P, I64, I, I64, U64, I, P],
         "frpca_spmm": [P, I, I, P, I64, P, I64, I],
         "frpca_get_transpose": [P, P, P, P],
@@ -160,6 +162,10 @@ def frpca_get_stats(h) -> frpca_stats:
 
 def frpca_reset_stats(h) -> None:
     _check(library().frpca_reset_stats(h), h)
+
+
+def frpca_set_wait_limit(h, cycles: int) -> None:
+    _check(library().frpca_set_wait_limit(h, cycles), h)
 
 
 def frpca_gaussian(h, R, l, ld, seed, dtype, out) -> None:
@@ -265,30 +271,75 @@ class _Context:
 class FrPCA:
     """A sparse matrix resident on the GPU, ready for frPCA runs.
 
-    ``indptr`` (int64, m+1), ``indices`` (int32, nnz, sorted and unique per
-    row) and ``values`` (float32/float64, nnz) are CUDA tensors; by default they
-    are borrowed (kept alive by this object) and A^T is built on the device.
-    ``hot_columns``: 0 keeps every nonzero on the CSR kernel; -1 picks the
-    densest columns automatically and > 0 that many (multiples of 128, at most
-    256) for a dense block whose share of each pass runs on the tensor cores.
+    ``indptr`` (int64 or int32, m+1), ``indices`` (int32, nnz, sorted and
+    unique per row) and ``values`` (float32/float64, nnz) are CUDA tensors; by
+    default they are borrowed (kept alive by this object) and A^T is built on
+    the device.  ``FrPCA.from_host`` takes host arrays instead, which the
+    library copies to the device itself.  ``hot_columns``: 0 keeps every
+    nonzero on the CSR kernel; -1 picks the densest columns automatically and
+    > 0 that many (multiples of 128, at most 256) for a dense block whose share
+    of each pass runs on the tensor cores.  ``max_device_bytes`` caps the
+    device memory the handle allocates for itself (0: no cap).
     """
 
-    def __init__(self, indptr, indices, values, shape, stream=None, borrow=True, validate=True, hot_columns=0):
+    def __init__(self, indptr, indices, values, shape, stream=None, borrow=True, validate=True, hot_columns=0,
+                 max_device_bytes=0):
         torch = _torch()
         _need_cuda(indptr, indices, values)
+        if indptr.dtype not in (torch.int64, torch.int32):
+            indptr = indptr.to(torch.int64)
+        self._keep = (indptr.contiguous(), indices.contiguous().to(torch.int32), values.contiguous())
+        self.indptr, self.indices, self.values = self._keep
+        self._setup(self.indptr.data_ptr(), self.indices.data_ptr() if self.indices.numel() else None,
+                    self.values.data_ptr() if self.values.numel() else None, int(self.indices.numel()),
+                    self.indptr.dtype == torch.int32, self.values.dtype, shape, 1, self.values.device, stream,
+                    borrow, validate, hot_columns, max_device_bytes)
+
+    def _setup(self, p_indptr, p_indices, p_values, nnz, rp32, dtype, shape, on_device, device, stream, borrow,
+               validate, hot_columns, max_device_bytes):
+        torch = _torch()
         self.m, self.n = int(shape[0]), int(shape[1])
-        self.indptr = indptr.contiguous().to(torch.int64)
-        self.indices = indices.contiguous().to(torch.int32)
-        self.values = values.contiguous()
-        self.dtype = self.values.dtype
-        self.stream = stream if stream is not None else torch.cuda.current_stream()
-        csr = frpca_csr(m=self.m, n=self.n, nnz=int(self.indices.numel()), rowptr=self.indptr.data_ptr(),
-                        colidx=self.indices.data_ptr() if self.indices.numel() else None,
-                        values=self.values.data_ptr() if self.values.numel() else None,
-                        dtype=_dtype_code(self.values), on_device=1)
+        self._nnz = nnz
+        self.dtype = dtype
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        csr = frpca_csr(m=self.m, n=self.n, nnz=nnz, rowptr=p_indptr, colidx=p_indices, values=p_values,
+                        dtype=FRPCA_F32 if dtype == torch.float32 else FRPCA_F64, on_device=on_device,
+                        rowptr_type=FRPCA_I32 if rp32 else FRPCA_I64)
         opts = frpca_create_opts(stream=self.stream.cuda_stream, borrow=1 if borrow else 0,
-                                 validate=1 if validate else 0, hot_columns=int(hot_columns))
+                                 validate=1 if validate else 0, hot_columns=int(hot_columns),
+                                 max_device_bytes=int(max_device_bytes))
         self.handle = frpca_create(csr, opts)
+
+    @classmethod
+    def from_host(cls, indptr, indices, values, shape, device="cuda", stream=None, validate=True, hot_columns=0,
+                  max_device_bytes=0):
+        """From host arrays (numpy or CPU tensors; pinned memory copies fastest):
+        the C ABI's own host path (``on_device = 0``) copies them to the
+        device and validates them there."""
+        import numpy as np
+        torch = _torch()
+        to_np = lambda a: a.numpy() if hasattr(a, "numpy") and not isinstance(a, np.ndarray) else a  # noqa: E731
+        ip, ix, va = (to_np(a) for a in (indptr, indices, values))
+        if ip.dtype not in (np.int64, np.int32):
+            ip = ip.astype(np.int64)
+        ip = np.ascontiguousarray(ip)
+        ix = np.ascontiguousarray(ix, dtype=np.int32)
+        va = np.ascontiguousarray(va)
+        if va.dtype not in (np.float32, np.float64):
+            raise TypeError(f"unsupported dtype {va.dtype}")
+        self = cls.__new__(cls)
+        self._keep = None
+        self.indptr = self.indices = self.values = None
+        dev = torch.device(device)
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(dev):
+            self._setup(ip.ctypes.data, ix.ctypes.data if ix.size else None, va.ctypes.data if va.size else None,
+                        int(ix.size), ip.dtype == np.int32,
+                        torch.float32 if va.dtype == np.float32 else torch.float64, shape, 0, dev, stream,
+                        False, validate, hot_columns, max_device_bytes)
+        return self
 
     @classmethod
     def from_csr(cls, csr, device="cuda", dtype=None, **kw):
@@ -300,7 +351,7 @@ class FrPCA:
 
     @property
     def nnz(self) -> int:
-        return int(self.indices.numel())
+        return self._nnz
 
     def close(self):
         if getattr(self, "handle", None):
@@ -318,7 +369,7 @@ class FrPCA:
         """Rank-k frPCA (Alg. 5/6); returns (U m x k, S k descending float64, V n x k)."""
         torch = _torch()
         dt = torch.float64 if precision == "fp64" else torch.float32
-        dev = self.values.device
+        dev = self.device
         if out is None:
             U = torch.empty((self.m, k), dtype=dt, device=dev)
             S = torch.empty((k,), dtype=torch.float64, device=dev)
@@ -372,9 +423,13 @@ class FrPCA:
                        _dtype_code(U), out.data_ptr() if self.nnz else None)
         return out
 
+    def set_wait_limit(self, cycles: int):
+        """Bound (SM clock cycles) of the LU and eigensolver grid-barrier waits; <= 0 restores the default."""
+        frpca_set_wait_limit(self.handle, int(cycles))
+
     def transpose(self):
         torch = _torch()
-        dev = self.values.device
+        dev = self.device
         pT = torch.empty(self.n + 1, dtype=torch.int64, device=dev)
         cT = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=dev)
         vT = torch.empty(max(self.nnz, 1), dtype=self.dtype, device=dev)

@@ -374,7 +374,7 @@ size_t calu_workspace_bytes(int l) {
 }
 
 cudaError_t launch_calu(int64_t R, int l, float *M, int64_t ld, int64_t *piv, void *ws, int *d_status, int num_sms,
-                        cudaStream_t s) {
+                        cudaStream_t s, long long limit_cycles) {
     if (l < 1 || l > FRPCA_MAX_L || R < l) return cudaErrorInvalidValue;
     if (R >= ((int64_t)1 << 31)) return cudaErrorNotSupported;
     const int G = calu_blocks(R, num_sms);
@@ -407,7 +407,7 @@ cudaError_t launch_calu(int64_t R, int l, float *M, int64_t ld, int64_t *piv, vo
     if ((e = cudaMemsetAsync(ws, 0, 256, s)) != cudaSuccess) return e;
     int64_t Rv = R, ldv = ld;
     int lv = l, ldcv = ldc;
-    long long lim = kBarrierLimitCycles;
+    long long lim = limit_cycles;
     void *Mp = M;
     void *args[] = {&Rv, &lv, &Mp, &ldv, &piv, &cand, &ldcv, &bar, &d_status, &lim};
     count_launch();

@@ -29,6 +29,8 @@ struct frpca_ctx {
     SpmmPlan planA, planAT;
     DevBuf ws_q, ws_w, ws_spmm, ws_gram, ws_eig, ws_lu, ws_small, ws_sign, ws_scratch, ws_scan, ws_bwd, ws_hot, ws_plan;
     HybridCSR hy;  // the densest columns of A as a dense block (FP32 SpMM on the tensor cores)
+    MemBudget budget;                            // frpca_create_opts.max_device_bytes
+    long long wait_limit = kBarrierLimitCycles;  // frpca_set_wait_limit
     std::string err;
     // instrumentation
     bool timing = false;
@@ -211,10 +213,10 @@ frpca_status lu_step(frpca_ctx *h, int64_t R, int l, void *M, int64_t ld, frpca_
     PhaseTimer t(h, PH_LU);
     cudaError_t e = cudaErrorNotSupported;
     if (dt == FRPCA_F32 && tournament)
-        e = launch_calu(R, l, (float *)M, ld, piv, h->ws_lu.ptr, h->d_status, h->num_sms, h->stream);
+        e = launch_calu(R, l, (float *)M, ld, piv, h->ws_lu.ptr, h->d_status, h->num_sms, h->stream, h->wait_limit);
     if (e == cudaErrorNotSupported) {
         (void)cudaGetLastError();
-        e = launch_lu(R, l, M, ld, dt, piv, h->ws_lu.ptr, h->d_status, h->num_sms, h->stream);
+        e = launch_lu(R, l, M, ld, dt, piv, h->ws_lu.ptr, h->d_status, h->num_sms, h->stream, h->wait_limit);
     }
     CK(e, "lu launch");
     h->acc.lu_calls += 1;
@@ -239,7 +241,7 @@ frpca_status gram_eig(frpca_ctx *h, int64_t R, int l, const void *M, int64_t ld,
             CK(launch_gram(R, l, M, ld, dt, B, h->ws_gram.ptr, h->num_sms, h->stream), "gram launch");
     }
     PhaseTimer t(h, PH_EIG);
-    CK(launch_eig(l, B, w, V, h->ws_eig.ptr, h->d_status, h->stream), "eig launch");
+    CK(launch_eig(l, B, w, V, h->ws_eig.ptr, h->d_status, h->stream, h->wait_limit), "eig launch");
     h->acc.eigsvd_calls += 1;
     return FRPCA_OK;
 }
@@ -407,15 +409,20 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
         return st;
     };
     h->stream = opts ? (cudaStream_t)opts->stream : nullptr;
+    h->budget.limit = opts && opts->max_device_bytes > 0 ? opts->max_device_bytes : 0;
     for (DevBuf *b : {&h->own_rowptr, &h->own_colidx, &h->own_vals, &h->t_rowptr, &h->t_colidx, &h->t_vals,
                       &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
-                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot, &h->ws_plan})
+                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot, &h->ws_plan,
+                      &h->hy.b_hot, &h->hy.b_slot, &h->hy.b_dense, &h->hy.b_crow, &h->hy.b_ccol, &h->hy.b_cval}) {
         b->stream = h->stream;
+        b->budget = &h->budget;
+    }
+    for (SpmmPlan *p : {&h->planA, &h->planAT, &h->hy.plan_cold, &h->hy.plan_t_cold}) p->budget = &h->budget;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "device attribute"));
-    e = dev_malloc((void **)&h->d_status, 256, h->stream);
+    e = dev_malloc((void **)&h->d_status, 256, h->stream, &h->budget);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "alloc status"));
     e = cudaMemsetAsync(h->d_status, 0, 256, h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(h, e, "clear status"));
@@ -430,47 +437,55 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
         return bail(fail(h, FRPCA_ERR_INVALID_ARG, "need 1 <= m, n < 2^31 and 0 <= nnz < 2^31"));
     if (csr->dtype != FRPCA_F32 && csr->dtype != FRPCA_F64)
         return bail(fail(h, FRPCA_ERR_INVALID_ARG, "unknown dtype"));
+    if (csr->rowptr_type != FRPCA_I64 && csr->rowptr_type != FRPCA_I32)
+        return bail(fail(h, FRPCA_ERR_INVALID_ARG, "unknown rowptr_type"));
     if (!csr->rowptr || (nnz > 0 && (!csr->colidx || !csr->values)))
         return bail(fail(h, FRPCA_ERR_INVALID_ARG, "null CSR array"));
     const int validate = opts ? opts->validate : 1;
     const size_t vs = dsize(csr->dtype);
-    if (!csr->on_device && validate) {
-        // Host arrays: check before anything reaches the device.
-        const int64_t *rp = csr->rowptr;
-        bool bad = rp[0] != 0 || rp[m] != nnz;
-        for (int64_t i = 0; i < m && !bad; ++i) {
-            if (rp[i + 1] < rp[i] || rp[i + 1] > nnz) { bad = true; break; }
-            for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-                const int32_t c = csr->colidx[p];
-                if (c < 0 || c >= n || (p > rp[i] && csr->colidx[p - 1] >= c)) { bad = true; break; }
-            }
-        }
-        if (bad) return bail(fail(h, FRPCA_ERR_INVALID_CSR, "invalid CSR structure"));
-    }
+    const bool rp32 = csr->rowptr_type == FRPCA_I32;
     h->A.rows = m;
     h->A.cols = n;
     h->A.nnz = nnz;
     h->A.dtype = csr->dtype;
+    // Host arrays are always copied; device arrays are borrowed on request.
+    // int32 row pointers are widened into an own int64 copy either way.
     const bool borrow = csr->on_device && opts && opts->borrow;
-    if (borrow) {
+    const cudaMemcpyKind kind = csr->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (borrow && !rp32) {
         h->A.rowptr = (int64_t *)csr->rowptr;
+    } else {
+        if ((e = h->own_rowptr.ensure(8 * (size_t)(m + 1))) != cudaSuccess) return bail(cuda_fail(h, e, "alloc CSR copy"));
+        if (rp32) {
+            // The int32 pointers are staged in the transpose's scratch buffer
+            // (reused later) and widened into the handle's int64 copy.
+            if ((e = h->ws_scratch.ensure(4 * (size_t)(m + 1))) != cudaSuccess)
+                return bail(cuda_fail(h, e, "alloc CSR copy"));
+            if ((e = cudaMemcpyAsync(h->ws_scratch.ptr, csr->rowptr, 4 * (size_t)(m + 1), kind, h->stream)) !=
+                    cudaSuccess ||
+                (e = launch_widen_i32((const int32_t *)h->ws_scratch.ptr, (int64_t *)h->own_rowptr.ptr, m + 1,
+                                      h->stream)) != cudaSuccess)
+                return bail(cuda_fail(h, e, "copy CSR row pointers"));
+        } else if ((e = cudaMemcpyAsync(h->own_rowptr.ptr, csr->rowptr, 8 * (size_t)(m + 1), kind, h->stream)) !=
+                   cudaSuccess) {
+            return bail(cuda_fail(h, e, "copy CSR row pointers"));
+        }
+        h->A.rowptr = (int64_t *)h->own_rowptr.ptr;
+    }
+    if (borrow) {
         h->A.colidx = (int32_t *)csr->colidx;
         h->A.vals = (void *)csr->values;
     } else {
-        const cudaMemcpyKind kind = csr->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        if ((e = h->own_rowptr.ensure(8 * (size_t)(m + 1))) != cudaSuccess ||
-            (e = h->own_colidx.ensure(4 * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess ||
+        if ((e = h->own_colidx.ensure(4 * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess ||
             (e = h->own_vals.ensure(vs * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess)
             return bail(cuda_fail(h, e, "alloc CSR copy"));
-        if ((e = cudaMemcpyAsync(h->own_rowptr.ptr, csr->rowptr, 8 * (size_t)(m + 1), kind, h->stream)) != cudaSuccess ||
-            (nnz > 0 && (e = cudaMemcpyAsync(h->own_colidx.ptr, csr->colidx, 4 * (size_t)nnz, kind, h->stream)) != cudaSuccess) ||
+        if ((nnz > 0 && (e = cudaMemcpyAsync(h->own_colidx.ptr, csr->colidx, 4 * (size_t)nnz, kind, h->stream)) != cudaSuccess) ||
             (nnz > 0 && (e = cudaMemcpyAsync(h->own_vals.ptr, csr->values, vs * (size_t)nnz, kind, h->stream)) != cudaSuccess))
             return bail(cuda_fail(h, e, "copy CSR"));
-        h->A.rowptr = (int64_t *)h->own_rowptr.ptr;
         h->A.colidx = (int32_t *)h->own_colidx.ptr;
         h->A.vals = h->own_vals.ptr;
     }
-    if (csr->on_device && validate) {
+    if (validate) {
         if ((e = launch_validate_csr(h->A, h->d_status, h->stream)) != cudaSuccess)
             return bail(cuda_fail(h, e, "validate"));
         frpca_status st = read_status(h);
@@ -525,7 +540,7 @@ frpca_status frpca_destroy(frpca_handle h) {
         cudaEventDestroy(mk.b);
     }
     for (cudaEvent_t ev : h->pool) cudaEventDestroy(ev);
-    dev_free(h->d_status, h->stream);
+    dev_free(h->d_status, h->stream, &h->budget, 256);
     // The releases above are ordered on the handle's stream; let them retire
     // before the handle (and possibly the caller's stream) goes away.
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -550,6 +565,12 @@ frpca_status frpca_refresh(frpca_handle h) {
 frpca_status frpca_set_timing(frpca_handle h, int enable) {
     if (!h) return FRPCA_ERR_INVALID_ARG;
     h->timing = enable != 0;
+    return FRPCA_OK;
+}
+
+frpca_status frpca_set_wait_limit(frpca_handle h, int64_t cycles) {
+    if (!h) return FRPCA_ERR_INVALID_ARG;
+    h->wait_limit = cycles > 0 ? (long long)cycles : kBarrierLimitCycles;
     return FRPCA_OK;
 }
 
@@ -688,7 +709,7 @@ frpca_status frpca_eig(frpca_handle h, int n, const double *B, double *w, double
     frpca_status st = reset_status(h);
     if (st != FRPCA_OK) return st;
     CK(h->ws_eig.ensure(eig_workspace_bytes(n)), "alloc eig workspace");
-    CK(launch_eig(n, B, w, V, h->ws_eig.ptr, h->d_status, h->stream), "eig launch");
+    CK(launch_eig(n, B, w, V, h->ws_eig.ptr, h->d_status, h->stream, h->wait_limit), "eig launch");
     return read_status(h);
 }
 

@@ -649,7 +649,8 @@ size_t eig_workspace_bytes(int n) {
     return sizeof(double) * (10 * ld * ld + 5 * ld) + 64 * sizeof(int) + 8 * kLevels * kRefineSteps + 512;
 }
 
-cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, int *d_status, cudaStream_t s) {
+cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, int *d_status, cudaStream_t s,
+                       long long limit_cycles) {
     if (n < 1 || n > FRPCA_MAX_L) return cudaErrorInvalidValue;
     const int ld = FRPCA_MAX_L;
     const size_t nn = (size_t)ld * ld;
@@ -702,7 +703,7 @@ cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, i
             int ldv = ld;
             const double *cm = C;
             unsigned long long *em = emax + lv * kRefineSteps;
-            long long lim = kBarrierLimitCycles;
+            long long lim = limit_cycles;
             void *args[] = {(void *)&dn, &ldv, (void *)&cm, &Z, &Z2, &G, &T, &S, &E, &Pn, &lam_b, &em, &bar,
                             &d_status, &lim};
             const int grid = std::min({refine_ctas, sms, FRPCA_MAX_L});  // 3 norm partials per CTA fit in Pn

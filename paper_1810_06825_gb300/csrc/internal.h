@@ -12,6 +12,7 @@
 namespace frpca {
 
 struct GridBarrier;
+struct MemBudget;
 
 // Process-wide count of kernels this library has launched (instrumentation).
 void count_launch(int n = 1);
@@ -41,21 +42,35 @@ struct SpmmPlan {
     int32_t *long_rows = nullptr; // row of each long row
     int64_t *long_first = nullptr;// first segment of each long row (n_long + 1 entries)
     cudaStream_t stream = nullptr;  // stream the arrays were allocated on
+    MemBudget *budget = nullptr;    // allocation cap the arrays are charged to
+    size_t charged = 0;             // bytes charged to budget
     void free_all();
 };
 
-// Grow-only device buffer.
-// Device memory from the stream-ordered pool of the current device, on the
-// stream of its owner: up to 8 GiB of freed blocks stay cached in the pool
-// (its release threshold is raised once per device), so creating and
-// destroying handles neither maps memory again nor synchronizes the device.
-cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t s);
-void dev_free(void *p, cudaStream_t s);
+// Device memory a handle may still allocate for itself (frpca_create_opts.
+// max_device_bytes); limit 0 = no cap.  An allocation past the cap fails with
+// cudaErrorMemoryAllocation, as an exhausted pool does.
+struct MemBudget {
+    int64_t limit = 0;
+    int64_t used = 0;
+    bool take(size_t bytes);
+    void give(size_t bytes);
+};
 
+// Device memory from this library's own stream-ordered pool on the current
+// device (not the device's default pool, whose attributes belong to the
+// process), on the stream of its owner: up to 8 GiB of freed blocks stay cached
+// in the pool, so creating and destroying handles neither maps memory again
+// nor synchronizes the device.  bytes are charged to budget when given.
+cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t s, MemBudget *budget = nullptr);
+void dev_free(void *p, cudaStream_t s, MemBudget *budget = nullptr, size_t bytes = 0);
+
+// Grow-only device buffer.
 struct DevBuf {
     void *ptr = nullptr;
     size_t bytes = 0;
     cudaStream_t stream = nullptr;  // the owner's stream: allocation and release are ordered on it
+    MemBudget *budget = nullptr;    // the owner's allocation cap (nullable)
     cudaError_t ensure(size_t need);
     void release();
 };
@@ -72,6 +87,8 @@ cudaError_t csr_transpose(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, De
                           cudaStream_t s);
 cudaError_t launch_convert(const void *in, frpca_dtype din, void *out, frpca_dtype dout, int64_t n,
                            cudaStream_t s);
+// out[i] = in[i] (int32 -> int64), n elements.
+cudaError_t launch_widen_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
 // Exclusive scan of n int32 counts into n (+1 total) int64 offsets.
 cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, DevBuf &scratch,
                                       cudaStream_t s);
@@ -96,8 +113,9 @@ void set_thread_error(const std::string &msg);
 // ---- lu.cu
 size_t lu_workspace_bytes(int64_t R, int l);
 int lu_max_rows_per_block();
+// limit_cycles: bound of each grid-barrier wait (kBarrierLimitCycles by default).
 cudaError_t launch_lu(int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv, void *ws,
-                      int *d_status, int num_sms, cudaStream_t s);
+                      int *d_status, int num_sms, cudaStream_t s, long long limit_cycles);
 
 // ---- gram.cu
 size_t gram_workspace_bytes(int64_t R, int l, int num_sms);
@@ -107,7 +125,7 @@ cudaError_t launch_gram(int64_t R, int l, const void *M, int64_t ld, frpca_dtype
 // ---- eig.cu
 size_t eig_workspace_bytes(int n);
 cudaError_t launch_eig(int n, const double *B, double *w, double *V, void *ws, int *d_status,
-                       cudaStream_t s);
+                       cudaStream_t s, long long limit_cycles);
 
 // ---- apply.cu
 // W (l x kout, dtype dt, ld kout) from the eigenpairs: column j takes
@@ -139,7 +157,7 @@ cudaError_t launch_scale_columns(int64_t R, int k, void *X, int64_t ld, frpca_dt
 // a block's rows do not fit in shared memory)
 size_t calu_workspace_bytes(int l);
 cudaError_t launch_calu(int64_t R, int l, float *M, int64_t ld, int64_t *piv, void *ws, int *d_status, int num_sms,
-                        cudaStream_t s);
+                        cudaStream_t s, long long limit_cycles);
 
 // ---- spmm_tc.cu: the densest columns of A as a dense block on the tensor cores
 struct HybridCSR {

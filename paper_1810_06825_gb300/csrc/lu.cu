@@ -70,7 +70,7 @@ template <> __device__ inline float lu_mult<float>(float x, float, float rinv) {
 template <typename T>
 __global__ void __launch_bounds__(kLuThreads, 1)
 lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__ piv_out, Cand *cand,
-          GridBarrier *bar, int cache_rows, int *status) {
+          GridBarrier *bar, int cache_rows, int *status, long long limit_cycles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T urow[FRPCA_MAX_L];
     __shared__ int64_t pivots[FRPCA_MAX_L];
@@ -139,7 +139,7 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
         }
     };
     block_reduce_write(0);
-    bool ok = grid_barrier(bar, G, status, kBarrierLimitCycles);
+    bool ok = grid_barrier(bar, G, status, limit_cycles);
 
     for (int j = 0; j < l && ok; ++j) {
         // (1) the pivot of column j, identical in every block: thread k reads
@@ -254,12 +254,12 @@ lu_kernel(int64_t R, int l, T *__restrict__ M, int64_t ld, int64_t *__restrict__
                 const T *row = cache + (size_t)(mine - r0) * cst;
                 for (int c = j + 1 + threadIdx.x; c < l; c += kLuThreads) M[mine * ld + c] = row[c];
             }
-            ok = grid_barrier(bar, G, status, kBarrierLimitCycles);
+            ok = grid_barrier(bar, G, status, limit_cycles);
         }
     }
     if (ok) {
         // The last pivot row: wait until every block has read it.
-        ok = grid_barrier(bar, G, status, kBarrierLimitCycles);
+        ok = grid_barrier(bar, G, status, limit_cycles);
         if (ok) {
             const int64_t pl = pivots[l - 1];
             if (pl >= r0 && pl < r1) {
@@ -287,7 +287,7 @@ size_t lu_workspace_bytes(int64_t R, int l) {
 }
 
 cudaError_t launch_lu(int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int64_t *piv, void *ws, int *d_status,
-                      int num_sms, cudaStream_t s) {
+                      int num_sms, cudaStream_t s, long long limit_cycles) {
     if (l < 1 || l > FRPCA_MAX_L || R < l) return cudaErrorInvalidValue;
     char *p = (char *)ws;
     GridBarrier *bar = (GridBarrier *)p;
@@ -319,7 +319,8 @@ cudaError_t launch_lu(int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, int
     void *Mp = M;
     int64_t Rv = R, ldv = ld;
     int lv = l, cr = cache_rows;
-    void *args[] = {&Rv, &lv, &Mp, &ldv, &piv, &cand, &bar, &cr, &d_status};
+    long long lim = limit_cycles;
+    void *args[] = {&Rv, &lv, &Mp, &ldv, &piv, &cand, &bar, &cr, &d_status, &lim};
     count_launch();
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kLuThreads), args, smem, s);
 }

@@ -173,6 +173,8 @@ void SpmmPlan::free_all() {
     dev_free(seg_len, stream);
     dev_free(long_rows, stream);
     dev_free(long_first, stream);
+    if (budget) budget->give(charged);
+    charged = 0;
     short_rows = nullptr;
     seg_start = nullptr;
     seg_len = nullptr;
@@ -216,7 +218,8 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
     plan.n_segs = (int64_t)sstart.size();
     auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
         if (bytes == 0) return cudaSuccess;
-        cudaError_t r = dev_malloc(dst, bytes, s);
+        cudaError_t r = dev_malloc(dst, bytes, s, plan.budget);
+        if (r == cudaSuccess) plan.charged += bytes;
         if (r != cudaSuccess) return r;
         return cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s);
     };
@@ -322,7 +325,10 @@ cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *cons
         plan.n_long = A.rows - plan.n_short;
         plan.n_segs = totals[2 * c + 1];
         auto alloc = [&](void **dst, size_t bytes) -> cudaError_t {
-            return bytes ? dev_malloc(dst, bytes, s) : cudaSuccess;
+            if (!bytes) return cudaSuccess;
+            cudaError_t r = dev_malloc(dst, bytes, s, plan.budget);
+            if (r == cudaSuccess) plan.charged += bytes;
+            return r;
         };
         if ((e = alloc((void **)&plan.short_rows, 4 * (size_t)plan.n_short)) != cudaSuccess ||
             (e = alloc((void **)&plan.long_rows, 4 * (size_t)plan.n_long)) != cudaSuccess ||

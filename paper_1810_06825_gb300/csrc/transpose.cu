@@ -332,6 +332,13 @@ cudaError_t launch_convert(const void *in, frpca_dtype din, void *out, frpca_dty
     return cudaGetLastError();
 }
 
+cudaError_t launch_widen_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    convert_kernel<int32_t, int64_t><<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t transpose_typed(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, DevBuf &scan_scratch,
                             cudaStream_t s) {
@@ -401,37 +408,71 @@ cudaError_t csr_transpose(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, De
     return transpose_typed<double>(A, AT, scratch, scan_scratch, s);
 }
 
-cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t s) {
+bool MemBudget::take(size_t bytes) {
+    if (limit > 0 && used + (int64_t)bytes > limit) return false;
+    used += (int64_t)bytes;
+    return true;
+}
+
+void MemBudget::give(size_t bytes) { used -= (int64_t)bytes; }
+
+namespace {
+
+// One pool per device, created on first use and kept for the life of the
+// process; its release threshold keeps up to 8 GiB of freed blocks mapped.
+cudaError_t library_pool(int dev, cudaMemPool_t *out) {
     static std::mutex mu;
-    static bool configured[64] = {};
+    static cudaMemPool_t pools[64] = {};
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = 8ull << 30;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        pools[dev] = pool;
+    }
+    *out = pools[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t s, MemBudget *budget) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) {
-        std::lock_guard<std::mutex> lock(mu);
-        if (!configured[dev]) {
-            cudaMemPool_t pool;
-            if ((e = cudaDeviceGetDefaultMemPool(&pool, dev)) != cudaSuccess) return e;
-            uint64_t keep = 8ull << 30;  // up to 8 GiB of freed blocks stay cached for reuse
-            if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
-            configured[dev] = true;
-        }
-    }
-    return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool = nullptr;
+    if ((e = library_pool(dev, &pool)) != cudaSuccess) return e;
+    if (budget && !budget->take(bytes)) return cudaErrorMemoryAllocation;
+    e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    if (e != cudaSuccess && budget) budget->give(bytes);
+    return e;
 }
 
-void dev_free(void *p, cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
+void dev_free(void *p, cudaStream_t s, MemBudget *budget, size_t bytes) {
+    if (!p) return;
+    cudaFreeAsync(p, s);
+    if (budget) budget->give(bytes);
 }
 
 cudaError_t DevBuf::ensure(size_t need) {
     if (need <= bytes) return cudaSuccess;
     if (ptr) {
-        dev_free(ptr, stream);
+        dev_free(ptr, stream, budget, bytes);
         ptr = nullptr;
         bytes = 0;
     }
-    cudaError_t e = dev_malloc(&ptr, need, stream);
+    cudaError_t e = dev_malloc(&ptr, need, stream, budget);
     if (e != cudaSuccess) {
         ptr = nullptr;
         return e;
@@ -441,7 +482,7 @@ cudaError_t DevBuf::ensure(size_t need) {
 }
 
 void DevBuf::release() {
-    dev_free(ptr, stream);
+    dev_free(ptr, stream, budget, bytes);
     ptr = nullptr;
     bytes = 0;
 }

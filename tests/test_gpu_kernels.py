@@ -93,17 +93,19 @@ def test_transpose_bit_exact(idx, dtype):
 
 
 # ---------------------------------------------------------------- SpMM
-def _spmm_bound(A, X, trans, eps):
+def _spmm_bound(A, X, trans, eps, hot_block=False):
+    """Element-wise bound on |Y - Y_exact|: a sum of d products in the CSR
+    order rounds at most (d + 2) eps * (|A| |X|) (d additions, one product
+    each, and the final store).  With the densest columns as a dense block on
+    the tensor cores (hot_block), FP32 accumulation also rounds once per
+    16-column K-step with a nonzero product (at most once per entry), plus the
+    split remainder (< 2^-26 per product) and the sums of the correction
+    accumulator and of the cold part: (2 d + 8) eps * (|A| |X|)."""
     Aabs = synthetic.CSR(A.m, A.n, A.indptr, A.indices, np.abs(A.data.astype(np.float64)))
     f = oracle.spmm_t if trans else oracle.spmm
     mag = f(Aabs.m, Aabs.n, Aabs.indptr, Aabs.indices, Aabs.data, np.abs(X))
     deg = np.diff(A.indptr) if not trans else np.bincount(A.indices, minlength=A.n)
-    if eps == EPS32:
-        # FP32 matrices keep their densest columns as a dense block on the
-        # tensor cores: FP32 accumulation rounds once per 16-column K-step with
-        # a nonzero product (at most once per entry) on top of the CSR order's
-        # rounding, plus the split remainder (< 2^-26 per product) and the sums
-        # of the correction accumulator and of the cold part.
+    if hot_block:
         return (2 * deg[:, None] + 8) * eps * mag + 1e-300
     return (deg[:, None] + 2) * eps * mag + 1e-300
 
@@ -148,7 +150,7 @@ def test_spmm_hot_columns_match_oracle(hot, l, trans):
     Y = _cpu(mat.spmm(Xg, trans=bool(trans)))
     f = oracle.spmm_t if trans else oracle.spmm
     ref = f(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64), X.astype(np.float64))
-    assert np.all(np.abs(Y - ref) <= _spmm_bound(A, X.astype(np.float64), trans, EPS32))
+    assert np.all(np.abs(Y - ref) <= _spmm_bound(A, X.astype(np.float64), trans, EPS32, hot_block=hot != 0))
     mat.close()
 
 

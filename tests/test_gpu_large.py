@@ -3,9 +3,14 @@
 FP32, int32 indices, A and A^T both resident on the GPU; k=100, l=120, q=5
 (Alg. 6, the odd-pass scheme).
 
-At this size the oracle runs one output at a time rather than the whole
-method, so the checks are what holds at any size (Alg. 6's final step and the
-orthonormality of its factors) plus the convergence of the leading triplet:
+test_large_powerlaw_matches_oracle runs the whole FP64 oracle on the same
+matrix and Gaussian test matrix and gates the FP32 path at the stated
+tolerances: singular values within 1e-4 relative, element by element, and the
+largest principal-angle sines of U and V within 1e-3.
+
+test_large_powerlaw_12000000x320000_fp32 checks what holds at any size (Alg.
+6's final step and the orthonormality of its factors) plus the convergence of
+the leading triplet, with the oracle forming single outputs:
 
 - A V = U diag(S) on seeded rows: the final step gives U = A Q V^ diag(1./S^)
   and V = Q V^, so the identity holds up to float rounding of the last pass
@@ -63,8 +68,53 @@ def _gram64(X, chunk=1 << 20):
     return G
 
 
-def test_large_powerlaw_12000000x320000_fp32():
-    A = synthetic.make_workload("powerlaw_12000000x320000_deg40")
+@pytest.fixture(scope="module")
+def large():
+    return synthetic.make_workload("powerlaw_12000000x320000_deg40")
+
+
+def _sine_from_grams(X, Y, chunk=1 << 20):
+    """Largest principal-angle sine between range(X) and range(Y) for tall X, Y
+    (same width), from FP64 Gram-sized products only: with X^T X = Lx Lx^T and
+    Y^T Y = Ly Ly^T, the cosines of the principal angles are the singular
+    values of Lx^-1 X^T Y Ly^-T."""
+    k = X.shape[1]
+    Gx, Gy, C = np.zeros((k, k)), np.zeros((k, k)), np.zeros((k, k))
+    for r in range(0, X.shape[0], chunk):
+        Xc, Yc = X[r:r + chunk].astype(np.float64), Y[r:r + chunk].astype(np.float64)
+        Gx += Xc.T @ Xc
+        Gy += Yc.T @ Yc
+        C += Xc.T @ Yc
+    Lx, Ly = np.linalg.cholesky(Gx), np.linalg.cholesky(Gy)
+    Mx = np.linalg.solve(Lx, C)
+    Mxy = np.linalg.solve(Ly, Mx.T).T
+    cmin = float(np.linalg.svd(Mxy, compute_uv=False).min())
+    return float(np.sqrt(max(0.0, 1.0 - min(cmin, 1.0) ** 2)))
+
+
+def test_large_powerlaw_matches_oracle(large):
+    """FP32 GPU path vs the FP64 oracle at full size (Alg. 6, q = 5, same
+    Philox Omega): sigma within 1e-4 relative element by element, principal-
+    angle sines of U and V within 1e-3."""
+    A = large
+    k, l, q = 100, 120, 5
+    mat = frpca.FrPCA.from_csr(A, device=DEV)
+    U, S, V = mat.run(k, l, q, seed=0, precision="fp32")
+    U, S, V = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+    mat.close()
+    del mat
+    torch.cuda.empty_cache()
+    Uo, So, Vo = oracle.frpca(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64), k, l, q, 0)
+    es = float(np.max(np.abs(S - So) / So))
+    eu = _sine_from_grams(U, Uo)
+    ev = _sine_from_grams(V, Vo)
+    print(f"large workload vs oracle: sigma rel {es:.2e}, sine U {eu:.2e}, sine V {ev:.2e}")
+    assert es <= 1e-4
+    assert eu <= 1e-3 and ev <= 1e-3
+
+
+def test_large_powerlaw_12000000x320000_fp32(large):
+    A = large
     k, l, q = 100, 120, 5
     assert A.nnz > 400_000_000
     mat = frpca.FrPCA.from_csr(A, device=DEV)
