@@ -35,7 +35,7 @@ WORKLOAD = "powerlaw_12000000x320000_deg40"
 SIDE_WORKLOAD = "powerlaw_200000x50000_deg100"
 BWD_WORKLOAD = "powerlaw_100000x20000_deg50"
 L2_BYTES = 129 * 2**20
-PRECISIONS = ("fp32", "fp64", "fp32_splitgram")
+PRECISIONS = ("fp32", "fp64", "fp32_dfgram")
 
 # DRAM traffic of one SpMM pass (dram__bytes_read.sum + dram__bytes_write.sum),
 # averaged over the q = 5 schedule (3 passes with A, 2 with A^T), from an ncu
@@ -319,7 +319,8 @@ def _timed_steps(mat, k, l, q, precision, steps, warmup, stream, U, S, V):
     return e0.elapsed_time(e1) / steps, st
 
 
-PHASES = ("spmm_ms", "lu_ms", "gram_ms", "eig_ms", "apply_ms", "gaussian_ms", "transpose_ms", "finish_ms")
+PHASES = ("spmm_ms", "spmm_a_ms", "spmm_t_ms", "lu_ms", "gram_ms", "eig_ms", "apply_ms", "gaussian_ms",
+          "transpose_ms", "finish_ms")
 
 
 def _side_workload(dev, stream, args, peak, peak_kind, with_ref: bool) -> dict:
@@ -489,7 +490,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--q", type=int, default=5)
-    ap.add_argument("--precision", default="fp32", choices=list(PRECISIONS))
+    ap.add_argument("--precision", default="fp32", choices=list(PRECISIONS) + ["fp32_splitgram"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the per-precision comparison")

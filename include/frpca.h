@@ -54,13 +54,19 @@ typedef enum frpca_index { FRPCA_I64 = 0, FRPCA_I32 = 1 } frpca_index;
  * the apply step in float (the apply step, Y = M W with l, k <= 128, on the
  * tensor cores from split-BF16 operands: every product exact, accumulated in
  * float); the l x l eigendecomposition always returns double precision
- * eigenpairs.  FP32_SPLITGRAM: FP32 with the Gram matrix of the
- * final eigSVD (the one over max(m, n) rows) formed on the tensor cores from
- * split-BF16 operands; needs l <= 128 (see frpca_gram_splitbf16). */
+ * eigenpairs.  The Gram matrix of the final eigSVD (the one over max(m, n)
+ * rows, a dense contraction) is formed on the tensor cores from split-BF16
+ * operands when l <= 128 (see frpca_gram_splitbf16); the power-iteration
+ * eigSVD's Gram, whose condition number eigSVD squares after the LU, is
+ * accumulated in double-float on the CUDA cores.  FP32_SPLITGRAM: the same
+ * arithmetic as FP32 (the name of this precision form), but l > 128 is
+ * refused instead of falling back.  FP32_DFGRAM: FP32 with every Gram in
+ * double-float on the CUDA cores (slower; for comparison). */
 typedef enum frpca_precision {
     FRPCA_PREC_FP64 = 0,
     FRPCA_PREC_FP32 = 1,
-    FRPCA_PREC_FP32_SPLITGRAM = 2
+    FRPCA_PREC_FP32_SPLITGRAM = 2,
+    FRPCA_PREC_FP32_DFGRAM = 3
 } frpca_precision;
 
 typedef struct frpca_ctx *frpca_handle;
@@ -139,9 +145,11 @@ frpca_status frpca_run(frpca_handle h, const frpca_run_opts *opts, void *U, doub
 frpca_status frpca_run_async(frpca_handle h, const frpca_run_opts *opts, void *U, double *S, void *V);
 frpca_status frpca_sync(frpca_handle h);
 
-/* Rebuilds the device CSR of A^T from A (same structure; values may have been
- * changed in place in borrowed arrays).  Enqueued on the handle's stream (no
- * synchronization); runs enqueued after it see the new A^T. */
+/* Refreshes the values of the device CSR of A^T from those of A after they
+ * changed in place in borrowed arrays (the structure must be the one given at
+ * create): one gather through the entry permutation the create's sort kept.
+ * Enqueued on the handle's stream (no synchronization); runs enqueued after
+ * it see the new A^T. */
 frpca_status frpca_refresh(frpca_handle h);
 
 /* ---- instrumentation --------------------------------------------------------- */
@@ -160,6 +168,8 @@ typedef struct frpca_stats {
     int64_t eigsvd_calls;
     double gram_ms, eig_ms, apply_ms;
     double gaussian_ms, transpose_ms, finish_ms;
+    int64_t spmm_a_passes, spmm_t_passes; /* passes with A and with A^T         */
+    double spmm_a_ms, spmm_t_ms;          /* their device time (sum: spmm_ms)  */
 } frpca_stats;
 
 /* enable != 0 records events around every phase (adds a few microseconds per

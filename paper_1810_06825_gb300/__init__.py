@@ -23,7 +23,7 @@ STATUS_NAMES = {
 }
 FRPCA_F32, FRPCA_F64 = 0, 1
 FRPCA_I64, FRPCA_I32 = 0, 1
-PREC = {"fp64": 0, "fp32": 1, "fp32_splitgram": 2}
+PREC = {"fp64": 0, "fp32": 1, "fp32_splitgram": 2, "fp32_dfgram": 3}
 
 EXPORTED = [
     "frpca_create", "frpca_destroy", "frpca_last_error", "frpca_run", "frpca_run_async", "frpca_sync",
@@ -60,7 +60,9 @@ class frpca_stats(ctypes.Structure):
                 ("spmm_ms", ctypes.c_double), ("spmm_bytes", ctypes.c_double), ("spmm_flops", ctypes.c_double),
                 ("lu_calls", ctypes.c_int64), ("lu_ms", ctypes.c_double), ("eigsvd_calls", ctypes.c_int64),
                 ("gram_ms", ctypes.c_double), ("eig_ms", ctypes.c_double), ("apply_ms", ctypes.c_double),
-                ("gaussian_ms", ctypes.c_double), ("transpose_ms", ctypes.c_double), ("finish_ms", ctypes.c_double)]
+                ("gaussian_ms", ctypes.c_double), ("transpose_ms", ctypes.c_double), ("finish_ms", ctypes.c_double),
+                ("spmm_a_passes", ctypes.c_int64), ("spmm_t_passes", ctypes.c_int64), ("spmm_a_ms", ctypes.c_double),
+                ("spmm_t_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

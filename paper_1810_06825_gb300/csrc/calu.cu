@@ -8,8 +8,10 @@
 // column j holds its multipliers left of j, 1 at j and 0 right of j).
 //
 // Partial pivoting needs one grid-wide argmax per column, i.e. l grid
-// barriers; here a panel costs one.  One cooperative launch; block b keeps its
-// contiguous row range in shared memory.  Per panel (columns c0 .. c0+w-1):
+// barriers; here a panel costs one.  One cooperative launch; block b owns a
+// contiguous row range, cached in shared memory when it fits (up to 512 rows,
+// one per thread), otherwise updated in place in M (up to 8 rows per thread,
+// 4,096 per block).  Per panel (columns c0 .. c0+w-1):
 //  (1) every block runs partial pivoting on a copy of the panel restricted to
 //      its unpivoted rows (one thread per row) and publishes the w rows it
 //      picked (their current full rows) to a double-buffered candidate area;
@@ -52,10 +54,11 @@ __device__ inline unsigned int pack_key(float v, int index, int bits) {
 }
 __device__ inline int key_index(unsigned int key, int bits) { return (int)((1u << bits) - 1u - (key & ((1u << bits) - 1u))); }
 
-constexpr int kRowBits = 9;    // local row < 512
+constexpr int kRowBits = 12;   // local row < 4096 (kCaluThreads * kMaxRpt)
 constexpr int kSlotBits = 11;  // candidate slot < 2048
 
 constexpr int kCaluWarps = kCaluThreads / 32;
+constexpr int kMaxRpt = 8;  // rows per thread of the global-memory form
 
 // Block-wide max of a key with one barrier; every thread gets it.  Callers
 // alternate between two tables, so a table is rewritten only after every
@@ -79,9 +82,11 @@ struct CaluLayout {
 // stride, so its size is only a multiple of 4 bytes).
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-__host__ __device__ inline CaluLayout calu_layout(int rows_max, int l) {
+// cache_rows rows of the block are cached (0 in the global-memory form);
+// rows_max is the most rows a block owns.
+__host__ __device__ inline CaluLayout calu_layout(int cache_rows, int rows_max, int l) {
     CaluLayout s{};
-    size_t off = align16((size_t)rows_max * (l + 1) * sizeof(float));
+    size_t off = align16((size_t)cache_rows * (l + 1) * sizeof(float));
     s.tv = off; off = align16(off + (size_t)kMaxCand * kPanel * sizeof(float));
     s.tid = off; off = align16(off + (size_t)kMaxCand * sizeof(int));
     s.urows = off; off = align16(off + (size_t)kPanel * FRPCA_MAX_L * sizeof(float));
@@ -98,6 +103,10 @@ struct CandArea {
     float *rows;     // [2][kMaxCand][ldc]
 };
 
+// RPT rows per thread.  SMEM: the block's rows are cached in shared memory
+// (RPT = 1, at most 512 rows); otherwise they stay in M and every access goes
+// to global memory (up to 512 * RPT rows per block).
+template <int RPT, bool SMEM>
 __global__ void __launch_bounds__(kCaluThreads, 1)
 calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__restrict__ piv_out, CandArea cand,
             int ldc, GridBarrier *bar, int *status, long long limit_cycles) {
@@ -113,9 +122,9 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
     const int64_t r0 = (int64_t)blockIdx.x * R / G, r1 = (int64_t)(blockIdx.x + 1) * R / G;
     const int nrows = (int)(r1 - r0);
     const int rows_max = (int)((R + G - 1) / G);
-    const int cst = l + 1;
-    const CaluLayout L = calu_layout(rows_max, l);
-    float *cache = reinterpret_cast<float *>(smem);
+    const int64_t cst = SMEM ? l + 1 : ld;
+    const CaluLayout L = calu_layout(SMEM ? rows_max : 0, rows_max, l);
+    float *cache = SMEM ? reinterpret_cast<float *>(smem) : M + r0 * ld;
     float *tv = reinterpret_cast<float *>(smem + L.tv);    // kPanel x candidate (column-major)
     int *tid = reinterpret_cast<int *>(smem + L.tid);      // candidate row ids (-1: none)
     float *U = reinterpret_cast<float *>(smem + L.urows);  // kPanel x FRPCA_MAX_L: winners' rows
@@ -123,9 +132,11 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
     const int ncand = (int)G * kPanel;
 
     for (int i = t; i < nrows; i += kCaluThreads) pivd[i] = 0;
-    for (int idx = t; idx < nrows * l; idx += kCaluThreads) {
-        const int i = idx / l, c = idx - i * l;
-        cache[i * cst + c] = M[(r0 + i) * ld + c];
+    if (SMEM) {
+        for (int idx = t; idx < nrows * l; idx += kCaluThreads) {
+            const int i = idx / l, c = idx - i * l;
+            cache[i * cst + c] = M[(r0 + i) * ld + c];
+        }
     }
     __syncthreads();
 
@@ -135,40 +146,65 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
         int *cids = cand.ids + (size_t)(panel & 1) * kMaxCand;
         float *cpan = cand.panel + (size_t)(panel & 1) * kMaxCand * kPanel;
         float *crows = cand.rows + (size_t)(panel & 1) * kMaxCand * ldc;
-        // (1) Local partial pivoting on a copy of the panel, one thread per row.
-        float pv[kPanel];
-        const bool mine = t < nrows && !pivd[t];
-        bool picked = false;
+        // (1) Local partial pivoting on a copy of the panel; thread t holds the
+        // rows t + j kCaluThreads.
+        float pv[RPT][kPanel];
+        bool mine[RPT], picked[RPT];
 #pragma unroll
-        for (int k = 0; k < kPanel; ++k) pv[k] = (mine && k < w) ? cache[t * cst + c0 + k] : 0.0f;
+        for (int j = 0; j < RPT; ++j) {
+            const int i = t + j * kCaluThreads;
+            mine[j] = i < nrows && !pivd[i];
+            picked[j] = false;
+#pragma unroll
+            for (int k = 0; k < kPanel; ++k) pv[j][k] = (mine[j] && k < w) ? cache[i * cst + c0 + k] : 0.0f;
+        }
         for (int k = 0; k < w; ++k) {
-            float pk = 0.0f;
+            unsigned int my = 0u;
 #pragma unroll
-            for (int kk = 0; kk < kPanel; ++kk)
-                if (kk == k) pk = pv[kk];
-            const unsigned int key = block_max1((mine && !picked) ? pack_key(pk, t, kRowBits) : 0u, wmax2[k & 1]);
+            for (int j = 0; j < RPT; ++j) {
+                float pk = 0.0f;
+#pragma unroll
+                for (int kk = 0; kk < kPanel; ++kk)
+                    if (kk == k) pk = pv[j][kk];
+                if (mine[j] && !picked[j]) my = max(my, pack_key(pk, t + j * kCaluThreads, kRowBits));
+            }
+            const unsigned int key = block_max1(my, wmax2[k & 1]);
             const int slot = blockIdx.x * kPanel + k;
             if (key == 0u) {  // no nonzero entry left in this block
                 if (t == 0) cids[slot] = -1;
                 continue;
             }
             const int wl = key_index(key, kRowBits);
-            if (t == wl) {
-                picked = true;
+            if (t == wl % kCaluThreads) {
 #pragma unroll
-                for (int kk = 0; kk < kPanel; ++kk) pvw[kk] = pv[kk];
-                pvr = 1.0f / pk;
+                for (int j = 0; j < RPT; ++j) {
+                    if (j != wl / kCaluThreads) continue;
+                    picked[j] = true;
+                    float pk = 0.0f;
+#pragma unroll
+                    for (int kk = 0; kk < kPanel; ++kk) {
+                        pvw[kk] = pv[j][kk];
+                        if (kk == k) pk = pv[j][kk];
+                    }
+                    pvr = 1.0f / pk;
+                }
                 cids[slot] = (int)(r0 + wl);
             }
             // Publish the picked row as it is (not the eliminated copy).
             for (int c = t; c < l; c += kCaluThreads) crows[(size_t)slot * ldc + c] = cache[wl * cst + c];
             if (t < kPanel) cpan[slot * kPanel + t] = (t < w) ? cache[wl * cst + c0 + t] : 0.0f;
             __syncthreads();
-            if (mine && !picked) {
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) {
+                if (!mine[j] || picked[j]) continue;
+                float pk = 0.0f;
+#pragma unroll
+                for (int kk = 0; kk < kPanel; ++kk)
+                    if (kk == k) pk = pv[j][kk];
                 const float m = pk * pvr;
 #pragma unroll
                 for (int kk = 0; kk < kPanel; ++kk)
-                    if (kk > k && kk < w) pv[kk] = fmaf(-m, pvw[kk], pv[kk]);
+                    if (kk > k && kk < w) pv[j][kk] = fmaf(-m, pvw[kk], pv[j][kk]);
             }
         }
         for (int k = w + t; k < kPanel; k += kCaluThreads) cids[blockIdx.x * kPanel + k] = -1;
@@ -292,17 +328,18 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
 
         // (4) Own rows.  Winners take their final form; the others get their
         // multipliers for the panel (forward substitution with U11).
-        if (t < nrows && !pivd[t]) {
-            const int gr = (int)(r0 + t);
+        for (int i = t; i < nrows; i += kCaluThreads) {
+            if (pivd[i]) continue;
+            const int gr = (int)(r0 + i);
             int wk = -1;
             for (int k = 0; k < w; ++k)
                 if (win_row[k] == gr) wk = k;
-            float *row = cache + t * cst;
+            float *row = cache + i * cst;
             if (wk >= 0) {
                 for (int k = 0; k < wk; ++k) row[c0 + k] = U[wk * FRPCA_MAX_L + c0 + k];
                 row[c0 + wk] = 1.0f;
                 for (int c = c0 + wk + 1; c < l; ++c) row[c] = 0.0f;
-                pivd[t] = 1;
+                pivd[i] = 1;
             } else {
                 for (int k = 0; k < w; ++k) {
                     const float m = row[c0 + k] * rdiag[k];
@@ -356,9 +393,11 @@ calu_kernel(int64_t R, int l, float *__restrict__ M, int64_t ld, int64_t *__rest
         __syncthreads();
     }
     __syncthreads();
-    for (int idx = t; idx < nrows * l; idx += kCaluThreads) {
-        const int i = idx / l, c = idx - i * l;
-        M[(r0 + i) * ld + c] = cache[i * cst + c];
+    if (SMEM) {
+        for (int idx = t; idx < nrows * l; idx += kCaluThreads) {
+            const int i = idx / l, c = idx - i * l;
+            M[(r0 + i) * ld + c] = cache[i * cst + c];
+        }
     }
 }
 
@@ -379,22 +418,37 @@ cudaError_t launch_calu(int64_t R, int l, float *M, int64_t ld, int64_t *piv, vo
     if (R >= ((int64_t)1 << 31)) return cudaErrorNotSupported;
     const int G = calu_blocks(R, num_sms);
     const int rows_max = (int)ceil_div(R, G);
-    if (rows_max > kCaluThreads) return cudaErrorNotSupported;
-    const CaluLayout L = calu_layout(rows_max, l);
+    if (rows_max > kCaluThreads * kMaxRpt) return cudaErrorNotSupported;
     int dev = 0, max_optin = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
         return e;
-    cudaFuncAttributes attr;
-    if ((e = cudaFuncGetAttributes(&attr, calu_kernel)) != cudaSuccess) return e;
-    if (L.total + attr.sharedSizeBytes > (size_t)max_optin) return cudaErrorNotSupported;
-    if ((e = cudaFuncSetAttribute(calu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total)) !=
-        cudaSuccess)
+    // The block's rows in shared memory when they fit (one per thread), in M
+    // otherwise (2, 4, 6 or 8 per thread).
+    const void *fn = nullptr;
+    size_t smem = 0;
+    if (rows_max <= kCaluThreads) {
+        cudaFuncAttributes attr;
+        const CaluLayout L = calu_layout(rows_max, rows_max, l);
+        if ((e = cudaFuncGetAttributes(&attr, calu_kernel<1, true>)) != cudaSuccess) return e;
+        if (L.total + attr.sharedSizeBytes <= (size_t)max_optin) {
+            fn = (const void *)calu_kernel<1, true>;
+            smem = L.total;
+        }
+    }
+    if (!fn) {
+        const int rpt = (int)ceil_div(rows_max, kCaluThreads);
+        fn = rpt <= 2 ? (const void *)calu_kernel<2, false>
+           : rpt <= 4 ? (const void *)calu_kernel<4, false>
+           : rpt <= 6 ? (const void *)calu_kernel<6, false>
+                      : (const void *)calu_kernel<8, false>;
+        smem = calu_layout(0, rows_max, l).total;
+    }
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, calu_kernel, kCaluThreads, L.total)) !=
-        cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCaluThreads, smem)) != cudaSuccess)
         return e;
     if (per_sm < 1 || (int64_t)per_sm * num_sms < G) return cudaErrorNotSupported;
     char *p = (char *)ws;
@@ -411,8 +465,7 @@ cudaError_t launch_calu(int64_t R, int l, float *M, int64_t ld, int64_t *piv, vo
     void *Mp = M;
     void *args[] = {&Rv, &lv, &Mp, &ldv, &piv, &cand, &ldcv, &bar, &d_status, &lim};
     count_launch();
-    return cudaLaunchCooperativeKernel((const void *)calu_kernel, dim3((unsigned)G), dim3(kCaluThreads), args,
-                                       L.total, s);
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kCaluThreads), args, smem, s);
 }
 
 }  // namespace frpca

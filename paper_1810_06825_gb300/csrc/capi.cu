@@ -23,7 +23,7 @@ struct frpca_ctx {
     bool has_matrix = false;
     DeviceCSR A, AT;
     DevBuf own_rowptr, own_colidx, own_vals;    // copies of A (when not borrowed)
-    DevBuf t_rowptr, t_colidx, t_vals;          // A^T
+    DevBuf t_rowptr, t_colidx, t_vals, t_perm;  // A^T and the entry of A at each of its positions
     DevBuf alt_A, alt_AT;                        // values converted to the other dtype
     bool alt_ready = false;
     SpmmPlan planA, planAT;
@@ -57,7 +57,7 @@ int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
-enum Phase { PH_SPMM, PH_LU, PH_GRAM, PH_EIG, PH_APPLY, PH_GAUSS, PH_TRANSPOSE, PH_FINISH, PH_COUNT };
+enum Phase { PH_SPMM, PH_SPMM_T, PH_LU, PH_GRAM, PH_EIG, PH_APPLY, PH_GAUSS, PH_TRANSPOSE, PH_FINISH, PH_COUNT };
 
 cudaEvent_t take_event(frpca_ctx *h) {
     if (!h->pool.empty()) {
@@ -176,7 +176,7 @@ frpca_status spmm_pass(frpca_ctx *h, int trans, int l, const void *X, int64_t ld
         const SpmmPlan &Pc = trans ? h->hy.plan_t_cold : h->hy.plan_cold;
         CK(h->ws_spmm.ensure(std::max<size_t>(256, spmm_scratch_bytes(Pc, l, dt))), "alloc spmm scratch");
         CK(h->ws_hot.ensure(hybrid_workspace_bytes(h->A.rows, h->hy.h, h->num_sms)), "alloc hybrid workspace");
-        PhaseTimer t(h, PH_SPMM);
+        PhaseTimer t(h, trans ? PH_SPMM_T : PH_SPMM);
         if (!trans) {  // A X = A_H X_H + A_cold X
             CK(launch_hot_ax(h->hy, h->A.rows, l, (const float *)X, ldx, (float *)Y, ldy, h->ws_hot.ptr, h->num_sms,
                              h->d_status, h->stream), "hot-column spmm launch");
@@ -190,13 +190,14 @@ frpca_status spmm_pass(frpca_ctx *h, int trans, int l, const void *X, int64_t ld
         t.done();
     } else {
         CK(h->ws_spmm.ensure(std::max<size_t>(256, spmm_scratch_bytes(P, l, dt))), "alloc spmm scratch");
-        PhaseTimer t(h, PH_SPMM);
+        PhaseTimer t(h, trans ? PH_SPMM_T : PH_SPMM);
         CK(launch_spmm(C, trans ? vat : va, P, l, X, ldx, Y, ldy, dt, h->ws_spmm.ptr, h->stream), "spmm launch");
         t.done();
     }
     // Algorithmic bytes: CSR arrays once, input and output blocks once each.
     const double sv = (double)dsize(dt);
     h->acc.spmm_passes += 1;
+    (trans ? h->acc.spmm_t_passes : h->acc.spmm_a_passes) += 1;
     h->acc.spmm_bytes += (double)C.nnz * (sv + 4.0) + (double)(C.rows + 1) * 8.0 +
                          ((double)C.cols + (double)C.rows) * (double)l * sv;
     h->acc.spmm_flops += 2.0 * (double)C.nnz * (double)l;
@@ -301,11 +302,14 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
         return fail(h, FRPCA_ERR_INVALID_ARG, "need 1 <= k <= l <= min(m, n) and q >= 2");
     if (l > FRPCA_MAX_L) return fail(h, FRPCA_ERR_UNSUPPORTED, "l > 160 is not supported");
     if (o->precision != FRPCA_PREC_FP64 && o->precision != FRPCA_PREC_FP32 &&
-        o->precision != FRPCA_PREC_FP32_SPLITGRAM)
+        o->precision != FRPCA_PREC_FP32_SPLITGRAM && o->precision != FRPCA_PREC_FP32_DFGRAM)
         return fail(h, FRPCA_ERR_INVALID_ARG, "unknown precision");
-    const bool split_gram = o->precision == FRPCA_PREC_FP32_SPLITGRAM;
-    if (split_gram && l > gram_tc_max_l())
+    if (o->precision == FRPCA_PREC_FP32_SPLITGRAM && l > gram_tc_max_l())
         return fail(h, FRPCA_ERR_UNSUPPORTED, "FP32_SPLITGRAM needs l <= 128");
+    // The final Gram (over max(m, n) rows) goes to the tensor cores in the
+    // float precisions unless the double-float form is asked for or l > 128.
+    const bool split_gram = o->precision != FRPCA_PREC_FP64 && o->precision != FRPCA_PREC_FP32_DFGRAM &&
+                            l <= gram_tc_max_l();
     int alg = o->alg ? o->alg : (m >= n ? 6 : 5);
     if ((alg != 5 && alg != 6) || (alg == 6 && m < n) || (alg == 5 && m > n))
         return fail(h, FRPCA_ERR_INVALID_ARG, "Alg. 6 needs m >= n and Alg. 5 needs m <= n");
@@ -411,7 +415,7 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
     h->stream = opts ? (cudaStream_t)opts->stream : nullptr;
     h->budget.limit = opts && opts->max_device_bytes > 0 ? opts->max_device_bytes : 0;
     for (DevBuf *b : {&h->own_rowptr, &h->own_colidx, &h->own_vals, &h->t_rowptr, &h->t_colidx, &h->t_vals,
-                      &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
+                      &h->t_perm, &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
                       &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot, &h->ws_plan,
                       &h->hy.b_hot, &h->hy.b_slot, &h->hy.b_dense, &h->hy.b_crow, &h->hy.b_ccol, &h->hy.b_cval}) {
         b->stream = h->stream;
@@ -498,12 +502,13 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
     h->AT.dtype = csr->dtype;
     if ((e = h->t_rowptr.ensure(8 * (size_t)(n + 1))) != cudaSuccess ||
         (e = h->t_colidx.ensure(4 * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess ||
-        (e = h->t_vals.ensure(vs * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess)
+        (e = h->t_vals.ensure(vs * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess ||
+        (e = h->t_perm.ensure(4 * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess)
         return bail(cuda_fail(h, e, "alloc transpose"));
     h->AT.rowptr = (int64_t *)h->t_rowptr.ptr;
     h->AT.colidx = (int32_t *)h->t_colidx.ptr;
     h->AT.vals = h->t_vals.ptr;
-    if ((e = csr_transpose(h->A, h->AT, h->ws_scratch, h->ws_scan, h->stream)) != cudaSuccess)
+    if ((e = csr_transpose(h->A, h->AT, (int32_t *)h->t_perm.ptr, h->ws_scratch, h->ws_scan, h->stream)) != cudaSuccess)
         return bail(cuda_fail(h, e, "transpose"));
     std::string perr;
     {
@@ -532,7 +537,7 @@ frpca_status frpca_destroy(frpca_handle h) {
     h->planAT.free_all();
     h->hy.free_all();
     for (DevBuf *b : {&h->own_rowptr, &h->own_colidx, &h->own_vals, &h->t_rowptr, &h->t_colidx, &h->t_vals,
-                      &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
+                      &h->t_perm, &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
                       &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot, &h->ws_plan})
         b->release();
     for (auto &mk : h->marks) {
@@ -555,7 +560,7 @@ frpca_status frpca_refresh(frpca_handle h) {
     if (!h) return FRPCA_ERR_INVALID_ARG;
     if (!h->has_matrix) return fail(h, FRPCA_ERR_INVALID_ARG, "handle has no matrix");
     PhaseTimer t(h, PH_TRANSPOSE);
-    CK(csr_transpose(h->A, h->AT, h->ws_scratch, h->ws_scan, h->stream), "transpose");
+    CK(csr_transpose_values(h->A, h->AT, (const int32_t *)h->t_perm.ptr, h->stream), "transpose values");
     CK(refresh_hybrid(h->A, h->hy, h->stream), "hot-column block");
     t.done();
     h->alt_ready = false;
@@ -599,7 +604,9 @@ frpca_status frpca_get_stats(frpca_handle h, frpca_stats *out) {
         h->pool.push_back(mk.b);
     }
     h->marks.clear();
-    h->acc.spmm_ms += ms_by_phase[PH_SPMM];
+    h->acc.spmm_ms += ms_by_phase[PH_SPMM] + ms_by_phase[PH_SPMM_T];
+    h->acc.spmm_a_ms += ms_by_phase[PH_SPMM];
+    h->acc.spmm_t_ms += ms_by_phase[PH_SPMM_T];
     h->acc.lu_ms += ms_by_phase[PH_LU];
     h->acc.gram_ms += ms_by_phase[PH_GRAM];
     h->acc.eig_ms += ms_by_phase[PH_EIG];

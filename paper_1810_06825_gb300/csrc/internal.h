@@ -81,10 +81,14 @@ cudaError_t launch_gaussian(int64_t R, int l, int64_t ld, uint64_t seed, frpca_d
 
 // ---- transpose.cu
 cudaError_t launch_validate_csr(const DeviceCSR &A, int *d_status, cudaStream_t s);
-// Stable transpose; AT arrays must be allocated by the caller (cols+1, nnz, nnz).
-// Asynchronous on s; scratch buffers grow on first use and are reused.
-cudaError_t csr_transpose(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, DevBuf &scan_scratch,
+// Stable transpose; AT arrays and perm (nnz int32) must be allocated by the
+// caller (cols+1, nnz, nnz).  perm[p] receives the row-major index of the
+// entry of A at position p of A^T.  Asynchronous on s; scratch buffers grow on
+// first use and are reused.
+cudaError_t csr_transpose(const DeviceCSR &A, DeviceCSR &AT, int32_t *perm, DevBuf &scratch, DevBuf &scan_scratch,
                           cudaStream_t s);
+// Values of A^T from those of A through perm (same structure).
+cudaError_t csr_transpose_values(const DeviceCSR &A, DeviceCSR &AT, const int32_t *perm, cudaStream_t s);
 cudaError_t launch_convert(const void *in, frpca_dtype din, void *out, frpca_dtype dout, int64_t n,
                            cudaStream_t s);
 // out[i] = in[i] (int32 -> int64), n elements.

@@ -6,7 +6,9 @@
 // entries start in row-major order, so a stable sort leaves every column's
 // rows ascending, and the result is unique (bit-exact whatever the schedule).
 // The sort is an LSD radix sort over 8-bit digits of the column index that
-// carries each entry's row and value along.  Each pass is a stable counting
+// carries each entry's row and index along; the final positions of the
+// entries (a permutation kept by the handle) then gather the values, so a
+// refresh after the values changed in place is a single gather.  Each pass is a stable counting
 // sort over CTA tiles of 4096 entries: a tile's digit counts come from a
 // digit-major scan of all tiles' histograms; inside the tile, warps rank equal
 // digits (eight ballots per 32-entry chunk) in entry order, the tile is reordered by digit
@@ -256,7 +258,7 @@ radix_scatter_kernel(const uint32_t *__restrict__ keys_in, const int32_t *__rest
             const int pos = wrun[warp * kRadix + dig[c]] + __popc(peer[c] & lt);
             skey[pos] = key[c];
             srow[pos] = rows_in[e];
-            sval[pos] = vals_in[e];
+            sval[pos] = vals_in ? vals_in[e] : (T)e;
         }
         __syncwarp();
         if (e < nnz && lane == 31 - __clz(peer[c])) wrun[warp * kRadix + dig[c]] += __popc(peer[c]);
@@ -339,9 +341,20 @@ cudaError_t launch_widen_i32(const int32_t *in, int64_t *out, int64_t n, cudaStr
     return cudaGetLastError();
 }
 
+namespace {
+
+// perm[p] = the entry of A that lands at position p of A^T (row-major entry
+// index); values of A^T are gathered through it, so a refresh after the values
+// changed in place is one gather instead of a sort.
 template <typename T>
-cudaError_t transpose_typed(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, DevBuf &scan_scratch,
-                            cudaStream_t s) {
+__global__ void gather_values_kernel(const int32_t *__restrict__ perm, const T *__restrict__ vals, int64_t nnz,
+                                     T *__restrict__ out) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        out[p] = vals[perm[p]];
+}
+
+cudaError_t sort_structure(const DeviceCSR &A, DeviceCSR &AT, int32_t *perm, DevBuf &scratch, DevBuf &scan_scratch,
+                           cudaStream_t s) {
     const int64_t nnz = A.nnz, n = A.cols;
     cudaError_t e;
     if (nnz == 0) {
@@ -353,8 +366,7 @@ cudaError_t transpose_typed(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, 
     const size_t cnt_bytes = sizeof(int32_t) * (size_t)round_up(kRadix * ntiles, 64);
     const size_t off_bytes = sizeof(int64_t) * (size_t)round_up(kRadix * ntiles + 1, 64);
     const size_t i32_bytes = sizeof(int32_t) * (size_t)round_up(nnz, 64);
-    const size_t val_bytes = sizeof(T) * (size_t)round_up(nnz, 64);
-    const size_t need = cnt_bytes + off_bytes + 5 * i32_bytes + 2 * val_bytes;
+    const size_t need = cnt_bytes + off_bytes + 7 * i32_bytes;
     if ((e = scratch.ensure(need)) != cudaSuccess) return e;
     char *p = (char *)scratch.ptr;
     int32_t *counts = (int32_t *)p; p += cnt_bytes;
@@ -362,7 +374,7 @@ cudaError_t transpose_typed(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, 
     uint32_t *keys[2] = {(uint32_t *)p, (uint32_t *)(p + i32_bytes)}; p += 2 * i32_bytes;
     int32_t *rows[2] = {(int32_t *)p, (int32_t *)(p + i32_bytes)}; p += 2 * i32_bytes;
     int32_t *row_of = (int32_t *)p; p += i32_bytes;
-    T *vals[2] = {(T *)p, (T *)(p + val_bytes)};
+    int32_t *ids[2] = {(int32_t *)p, (int32_t *)(p + i32_bytes)};
 
     row_of_entry_kernel<<<(unsigned)ceil_div(A.rows * 32, 256), 256, 0, s>>>(A.rows, A.rowptr, row_of);
     count_launch();
@@ -371,30 +383,30 @@ cudaError_t transpose_typed(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, 
     int bits = 1;
     while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
     const int passes = (bits + 7) / 8;
-    const size_t smem = (size_t)kSortTile * (sizeof(T) + 8) + sizeof(int32_t) * (kSortWarps + 1) * kRadix;
-    if ((e = cudaFuncSetAttribute(radix_scatter_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = (size_t)kSortTile * (sizeof(int32_t) + 8) + sizeof(int32_t) * (kSortWarps + 1) * kRadix;
+    if ((e = cudaFuncSetAttribute(radix_scatter_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
         return e;
     const uint32_t *kin = (const uint32_t *)A.colidx;
     const int32_t *rin = row_of;
-    const T *vin = (const T *)A.vals;
+    const int32_t *iin = nullptr;  // first pass: the entry index itself
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
         const bool last = pass + 1 == passes;
         uint32_t *kout = keys[pass & 1];
         int32_t *rout = last ? AT.colidx : rows[pass & 1];
-        T *vout = last ? (T *)AT.vals : vals[pass & 1];
+        int32_t *iout = last ? perm : ids[pass & 1];
         radix_hist_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, nnz, shift, ntiles, counts);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = exclusive_scan<int32_t>(counts, offs, kRadix * ntiles, scan_scratch, s)) != cudaSuccess) return e;
-        radix_scatter_kernel<T><<<(unsigned)ntiles, kSortThreads, smem, s>>>(kin, rin, vin, nnz, shift, ntiles, offs,
-                                                                             kout, rout, vout);
+        radix_scatter_kernel<int32_t><<<(unsigned)ntiles, kSortThreads, smem, s>>>(kin, rin, iin, nnz, shift, ntiles,
+                                                                                   offs, kout, rout, iout);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         kin = kout;
         rin = rout;
-        vin = vout;
+        iin = iout;
     }
     rowptr_from_sorted_kernel<<<(unsigned)std::min<int64_t>(ceil_div(nnz + 1, 256), 1 << 20), 256, 0, s>>>(
         kin, nnz, n, AT.rowptr);
@@ -402,10 +414,24 @@ cudaError_t transpose_typed(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, 
     return cudaGetLastError();
 }
 
-cudaError_t csr_transpose(const DeviceCSR &A, DeviceCSR &AT, DevBuf &scratch, DevBuf &scan_scratch,
+}  // namespace
+
+cudaError_t csr_transpose_values(const DeviceCSR &A, DeviceCSR &AT, const int32_t *perm, cudaStream_t s) {
+    if (A.nnz == 0) return cudaSuccess;
+    const unsigned g = grid_for(A.nnz, 256);
+    if (A.dtype == FRPCA_F32)
+        gather_values_kernel<float><<<g, 256, 0, s>>>(perm, (const float *)A.vals, A.nnz, (float *)AT.vals);
+    else
+        gather_values_kernel<double><<<g, 256, 0, s>>>(perm, (const double *)A.vals, A.nnz, (double *)AT.vals);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t csr_transpose(const DeviceCSR &A, DeviceCSR &AT, int32_t *perm, DevBuf &scratch, DevBuf &scan_scratch,
                           cudaStream_t s) {
-    if (A.dtype == FRPCA_F32) return transpose_typed<float>(A, AT, scratch, scan_scratch, s);
-    return transpose_typed<double>(A, AT, scratch, scan_scratch, s);
+    cudaError_t e = sort_structure(A, AT, perm, scratch, scan_scratch, s);
+    if (e != cudaSuccess) return e;
+    return csr_transpose_values(A, AT, perm, s);
 }
 
 bool MemBudget::take(size_t bytes) {

@@ -93,7 +93,7 @@ def test_host_invalid_csr_rejected():
     ip = A.indptr.copy()
     ip[-1] -= 1  # rowptr[m] != nnz
     with pytest.raises(frpca.FrpcaError) as ei:
-        frpca.FrPCA.from_host(ip, A.indices[:-1], A.data[:-1], (A.m, A.n), device=DEV)
+        frpca.FrPCA.from_host(ip, A.indices, A.data, (A.m, A.n), device=DEV)
     assert ei.value.status == 2
     ip = A.indptr.astype(np.int32)
     ip[10], ip[11] = ip[11], ip[10]  # non-monotone

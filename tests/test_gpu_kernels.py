@@ -331,11 +331,13 @@ def _lu_tournament(M):
 
 
 @pytest.mark.parametrize("R,l", [(50, 8), (300, 45), (4099, 48), (20_000, 120), (50_000, 120), (9_000, 160),
-                                 (1000, 1), (33, 33)])
+                                 (1000, 1), (33, 33), (100_003, 120), (320_000, 120), (600_001, 37)])
 def test_lu_tournament_structure_and_range(R, l):
     """Lemma 3 for any pivot rows: range(P^T L) = range(M); the pivot row of
     column j holds 1 at j and 0 right of j; the unit lower factor stays
-    moderate (tournament pivoting does not bound it by 1)."""
+    moderate (tournament pivoting does not bound it by 1).  Up to 512 rows per
+    block the rows are cached in shared memory; the larger cases (100,003 to
+    600,001 rows) take the form that updates them in place in global memory."""
     M = np.random.default_rng(R + 7 * l).standard_normal((R, l)).astype(np.float32)
     P, piv = _lu_tournament(M)
     assert len(set(piv.tolist())) == l and piv.min() >= 0 and piv.max() < R
