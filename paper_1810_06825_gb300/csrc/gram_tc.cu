@@ -1,6 +1,6 @@
 // gram_tc.cu -- step 1 of eigSVD (Alg. 2), B = M^T M, on the tcgen05 tensor
-// cores for an FP32 block M (R x l, l <= 128): the precision form
-// FRPCA_PREC_FP32_SPLITGRAM.
+// cores for an FP32 block M (R x l, l <= 128): the Gram of the final eigSVD in
+// the FP32 precisions.
 //
 // Each FP32 entry is split into three BF16 terms, x = h + m + s exactly
 // (h = bf16(x), m = bf16(x - h), s = bf16(x - h - m): 3 x 8 significand bits
@@ -9,12 +9,15 @@
 // the dropped products (Mm^T S, S^T Mm, S^T S) being below float rounding.
 // Every BF16 x BF16 product is exact in the FP32 accumulator; H^T H and the
 // corrections go to two separate TMEM accumulators, so the corrections'
-// rounding is relative to their own (2^-8 smaller) size.  A CTA takes
-// 128-row chunks of M: it splits a chunk into shared memory, one thread
-// issues 8 K-steps x 6 MMAs (M = N = 128, K = 16), the accumulators are read
-// back with tcgen05.ld and added into a per-CTA FP64 copy of B in shared
-// memory.  So FP32 accumulation never spans more than 128 rows; partial B's
-// of the CTAs are summed in FP64, in CTA order, by a second kernel.
+// rounding is relative to their own (2^-8 smaller) size.  A persistent CTA per
+// SM takes 128-row chunks of M: the chunk is split into one of two shared-
+// memory operand stages while the previous chunk's MMAs run, one thread issues
+// 8 K-steps x 6 MMAs (M = N = 128, K = 16), and groups of 4 chunks accumulate
+// into one of two TMEM accumulator pairs.  A finished group's pair is read back
+// with tcgen05.ld during the next group's MMAs and added into the CTA's copy
+// of B in double-float (pairs of floats, TwoSum), so FP32 accumulation spans at
+// most 512 rows and no FP64 arithmetic sits in the loop; the CTAs' partial B's
+// are summed in FP64, in CTA order, by a second kernel.
 //
 // Operands sit in shared memory in the no-swizzle K-major layout of the
 // tcgen05 shared-memory descriptor: 8 x 8 "core matrices" of 128 contiguous
@@ -38,10 +41,11 @@ using namespace tc;
 constexpr int kTcThreads = 256;
 constexpr int kTile = 128;                         // l padded to 128; rows per chunk
 constexpr int kOpBytes = kTile * kTile * 2;        // one BF16 operand, 32 KiB
-constexpr int kAccStride = kTile + 1;              // FP64 accumulator row stride (fewer bank conflicts)
-constexpr int kAccBytes = kTile * kAccStride * 8;  // 132,096 bytes
-constexpr int kSmemBytes = 3 * kOpBytes + kAccBytes + 64;
-constexpr uint32_t kTmemCols = 256;                // two 128-column FP32 accumulators
+constexpr int kStages = 2;                         // operand stages (H, M, S splits of one chunk)
+constexpr int kStageBytes = 3 * kOpBytes;          // 96 KiB
+constexpr int kGroup = 4;                          // chunks accumulated in TMEM between drains (512 rows)
+constexpr int kSmemBytes = kStages * kStageBytes + 64;
+constexpr uint32_t kTmemCols = 512;                // two pairs of 128-column FP32 accumulators
 // Thread t loads column group j4 = t % 32 (4 columns) of the 8-row groups
 // rg = t / 32 and rg + 8 of a chunk: 16 float4 loads, rows coalesced per warp.
 struct ChunkRegs {
@@ -94,100 +98,164 @@ __device__ inline void store_chunk(const ChunkRegs &c, unsigned char *opH, unsig
     }
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
-gram_tc_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, double *__restrict__ partial,
-               int *status, long long limit_cycles) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *opH = smem;
-    unsigned char *opM = smem + kOpBytes;
-    unsigned char *opS = smem + 2 * kOpBytes;
-    double *acc = reinterpret_cast<double *>(smem + 3 * kOpBytes);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 3 * kOpBytes + kAccBytes);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// x16 variant of tmem_ld32: 16 consecutive FP32 columns of this thread's lane.
+__device__ inline void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
 
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(kTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+// (hi, lo) += (a, b) in double-float arithmetic, with |b| << |a|: TwoSum of the
+// leading parts, the trailing parts added to the error, then renormalized.
+__device__ inline void df_add(float &hi, float &lo, float a, float b) {
+    const float s = hi + a;
+    const float bp = s - hi;
+    float e = (hi - (s - bp)) + (a - bp);
+    e += lo + b;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
+// Adds accumulator pair `pair` (main, correction) of TMEM into this CTA's
+// double-float copy of B (acc_hi / acc_lo, 128 x 128 floats each, L2-resident):
+// warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of B) and the 64 columns
+// 64 (w / 4) .. +63, 16 at a time.
+__device__ inline void drain_pair(uint32_t tmem, int pair, float *__restrict__ acc_hi, float *__restrict__ acc_lo) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = 32 * (warp & 3) + lane;
+    const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t d_main = tmem + (uint32_t)pair * 2 * kTile, d_corr = d_main + kTile;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+        const int col0 = 64 * (warp >> 2) + 16 * q;
+        float vm[16], vc[16];
+        tmem_ld16(d_main + lane_addr + col0, vm);
+        tmem_ld16(d_corr + lane_addr + col0, vc);
+        float4 *ph = reinterpret_cast<float4 *>(acc_hi + row * kTile + col0);
+        float4 *pl = reinterpret_cast<float4 *>(acc_lo + row * kTile + col0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float4 h = ph[u], o = pl[u];
+            df_add(h.x, o.x, vm[4 * u + 0], vc[4 * u + 0]);
+            df_add(h.y, o.y, vm[4 * u + 1], vc[4 * u + 1]);
+            df_add(h.z, o.z, vm[4 * u + 2], vc[4 * u + 2]);
+            df_add(h.w, o.w, vm[4 * u + 3], vc[4 * u + 3]);
+            ph[u] = h;
+            pl[u] = o;
+        }
     }
+}
+
+// One CTA per SM, persistent over the 128-row chunks c = blockIdx.x + i G.
+// Chunk i is split into operand stage i % 2 while the MMAs of chunk i - 1 run
+// (the stage is reused once the commit of chunk i - 2 has arrived), and its
+// MMAs accumulate into TMEM pair (i / kGroup) % 2 (main and correction, 128
+// columns each; 512 columns in all).  When a group of kGroup chunks is
+// complete, its pair is drained into the CTA's double-float copy of B during
+// the next chunk's MMAs, so FP32 accumulation spans at most kGroup * 128 rows.
+__global__ void __launch_bounds__(kTcThreads, 1)
+gram_tc_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, float *__restrict__ accws,
+               double *__restrict__ partial, int *status, long long limit_cycles) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + kStages);
+    const int warp = threadIdx.x >> 5;
+    float *acc_hi = accws + (size_t)blockIdx.x * 2 * kTile * kTile;
+    float *acc_lo = acc_hi + kTile * kTile;
+
+    if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int st = 0; st < kStages; ++st) mbar_init(smem_u32(mbar + st), 1);
+        fence_mbar_init();
     }
-    for (int i = threadIdx.x; i < kTile * kAccStride; i += kTcThreads) acc[i] = 0.0;
+    for (int i = threadIdx.x; i < kTile * kTile / 4; i += kTcThreads) {
+        reinterpret_cast<float4 *>(acc_hi)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4 *>(acc_lo)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t d_main = tmem, d_corr = tmem + kTile;
-    const uint32_t mb = smem_u32(mbar);
 
     const int64_t nchunks = ceil_div(R, kTile);
+    const int64_t G = gridDim.x;
+    const int64_t nmine = nchunks > blockIdx.x ? (nchunks - blockIdx.x + G - 1) / G : 0;
     ChunkRegs regs;
-    int64_t c = blockIdx.x;
-    if (c < nchunks) load_chunk(M, ld, R, l, c * kTile, regs);
-    uint32_t parity = 0;
+    if (nmine > 0) load_chunk(M, ld, R, l, (int64_t)blockIdx.x * kTile, regs);
+    // Waits for the commit of local chunk j (stage j % 2, its (j / 2)-th use).
+    auto wait_commit = [&](int64_t j) -> bool {
+        const bool done = mbar_wait_bounded(smem_u32(mbar + (j & 1)), (uint32_t)((j >> 1) & 1), limit_cycles);
+        const bool all = __syncthreads_and(done) != 0;
+        fence_after();
+        return all;
+    };
     bool ok = true;
-    for (; c < nchunks && ok; c += gridDim.x) {
+    int64_t pending = -1;  // last chunk of a complete group whose pair awaits draining
+    int64_t issued = -1;   // last chunk whose MMAs were issued
+    for (int64_t i = 0; i < nmine && ok; ++i) {
+        const int st = (int)(i & 1);
+        unsigned char *opH = smem + st * kStageBytes, *opM = opH + kOpBytes, *opS = opM + kOpBytes;
+        if (i >= 2 && !(ok = wait_commit(i - 2))) break;
         store_chunk(regs, opH, opM, opS);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_async_smem();
         fence_before();
         __syncthreads();
         fence_after();
         if (threadIdx.x == 0) {
+            const int pair = (int)((i / kGroup) & 1);
+            const uint32_t d_main = tmem + (uint32_t)pair * 2 * kTile, d_corr = d_main + kTile;
+            const bool first = (i % kGroup) == 0;
             const uint32_t aH = smem_u32(opH), aM = smem_u32(opM), aS = smem_u32(opS);
 #pragma unroll 1
             for (int ks = 0; ks < kTile / 16; ++ks) {
                 const uint32_t koff = (uint32_t)(2 * ks * kLbo);  // two core matrices per K-step of 16
-                const uint64_t h = make_desc(aH + koff), m = make_desc(aM + koff), s = make_desc(aS + koff);
-                mma_split6(d_main, d_corr, h, m, s, h, m, s, ks > 0);
+                const uint64_t h = make_desc(aH + koff), m = make_desc(aM + koff), sd = make_desc(aS + koff);
+                mma_split6(d_main, d_corr, h, m, sd, h, m, sd, !(first && ks == 0));
             }
-            mma_commit(mb);
+            mma_commit(smem_u32(mbar + st));
         }
+        issued = i;
         // Prefetch the next chunk while the tensor cores run.
-        const int64_t cn = c + gridDim.x;
-        if (cn < nchunks) load_chunk(M, ld, R, l, cn * kTile, regs);
-        const long long t0 = clock64();
-        bool done = false;
-        while (!(done = mbar_try_wait(mb, parity))) {
-            if (clock64() - t0 > limit_cycles) break;
+        if (i + 1 < nmine) load_chunk(M, ld, R, l, (blockIdx.x + (i + 1) * G) * kTile, regs);
+        if (pending >= 0) {
+            if (!(ok = wait_commit(pending))) break;
+            drain_pair(tmem, (int)((pending / kGroup) & 1), acc_hi, acc_lo);
+            fence_before();
+            pending = -1;
         }
-        parity ^= 1u;
-        ok = __syncthreads_and(done) != 0;
-        if (!ok) {
-            set_status(status, FRPCA_ERR_TIMEOUT);
-            break;
-        }
-        fence_after();
-        // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of B) and
-        // columns 64 (w / 4) .. +63 of both accumulators.
-        const int row = 32 * (warp & 3) + lane;
-        const int col0 = 64 * (warp >> 2);
-        const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
-#pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            float vm[32], vc[32];
-            tmem_ld32(d_main + lane_addr + col0 + 32 * h, vm);
-            tmem_ld32(d_corr + lane_addr + col0 + 32 * h, vc);
-            double *ar = acc + row * kAccStride + col0 + 32 * h;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) ar[i] += (double)vm[i] + (double)vc[i];
-        }
-        fence_before();
-        __syncthreads();
+        if (i % kGroup == kGroup - 1) pending = i;
     }
+    if (ok && issued >= 0) {
+        // The last group (complete or not) and any pending one.
+        if ((ok = wait_commit(issued))) {
+            if (pending >= 0 && pending != issued) drain_pair(tmem, (int)((pending / kGroup) & 1), acc_hi, acc_lo);
+            drain_pair(tmem, (int)((issued / kGroup) & 1), acc_hi, acc_lo);
+            fence_before();
+        }
+    } else if (!ok && issued >= 0) {
+        // A wait ran out: give the MMAs already issued a bounded chance to
+        // finish before the TMEM is released.
+        (void)mbar_wait_bounded(smem_u32(mbar + (issued & 1)), (uint32_t)((issued >> 1) & 1), limit_cycles);
+    }
+    if (!ok && threadIdx.x == 0) set_status(status, FRPCA_ERR_TIMEOUT);
     __syncthreads();
-    // This CTA's partial B (l x l), written even when it had no chunk.
+    // This CTA's partial B (l x l) in FP64, written even when it had no chunk.
     double *out = partial + (size_t)blockIdx.x * l * l;
     for (int i = threadIdx.x; i < l * l; i += kTcThreads) {
         const int r = i / l, cc = i - r * l;
-        out[i] = acc[r * kAccStride + cc];
+        out[i] = (double)acc_hi[r * kTile + cc] + (double)acc_lo[r * kTile + cc];
     }
     fence_before();
     __syncthreads();
     fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 // B[i][j] = sum_g (P_g[i][j] + P_g[j][i]) / 2 in CTA order (deterministic and
@@ -211,7 +279,8 @@ int tc_blocks(int64_t R, int sms) { return (int)std::max<int64_t>(1, std::min<in
 int gram_tc_max_l() { return kTile; }
 
 size_t gram_tc_workspace_bytes(int64_t R, int l, int sms) {
-    return sizeof(double) * (size_t)tc_blocks(R, sms) * l * l + 256;
+    const size_t G = (size_t)tc_blocks(R, sms);
+    return sizeof(float) * G * 2 * kTile * kTile + sizeof(double) * G * l * l + 256;
 }
 
 cudaError_t launch_gram_tc(int64_t R, int l, const float *M, int64_t ld, double *B, void *ws, int sms, int *d_status,
@@ -220,8 +289,9 @@ cudaError_t launch_gram_tc(int64_t R, int l, const float *M, int64_t ld, double 
     const int G = tc_blocks(R, sms);
     cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
-    double *partial = static_cast<double *>(ws);
-    gram_tc_kernel<<<G, kTcThreads, kSmemBytes, s>>>(R, l, M, ld, partial, d_status, kBarrierLimitCycles);
+    float *accws = static_cast<float *>(ws);
+    double *partial = reinterpret_cast<double *>(accws + (size_t)G * 2 * kTile * kTile);
+    gram_tc_kernel<<<G, kTcThreads, kSmemBytes, s>>>(R, l, M, ld, accws, partial, d_status, kBarrierLimitCycles);
     gram_tc_reduce_kernel<<<(int)ceil_div((int64_t)l * l, 256), 256, 0, s>>>(l, G, partial, B);
     count_launch(2);
     return cudaGetLastError();

@@ -2,10 +2,11 @@
 (Alg. 2, step 1) on the tcgen05 tensor cores from split-BF16 operands.
 
 Kernel parity against the oracle's FP64 Gram of the same float block, entry by
-entry, within 32 * 2^-24 * (|M|^T |M|)_ij: the three-term split leaves at most
-~5 * 2^-27 |x||y| per product (split remainder and the dropped products), and
-FP32 accumulation in tensor memory spans at most 128 rows (8 MMAs of 16) per
-chunk before the FP64 sum.  End to end, frPCA with the form against the FP64
+entry, within 64 * 2^-24 * (|M|^T |M|)_ij: the three-term split leaves at most
+~5 * 2^-27 |x||y| per product (split remainder and the dropped products), FP32
+accumulation in tensor memory spans at most 512 rows (32 MMAs of K = 16, each
+rounding the running sum once) before the sum moves to double-float, and the
+other 32 units cover each MMA's own summation of its 16 products.  End to end, frPCA with the form against the FP64
 oracle at the FP32 path's gates (sigma rel. error <= 1e-4, principal-angle sine
 <= 1e-3), and the measured errors are printed.
 """
@@ -47,7 +48,7 @@ def _block(R, l, seed, scale_cols=False, pad_nan=True):
 
 
 @pytest.mark.parametrize("R,l", [(1, 1), (1, 128), (100, 7), (128, 64), (129, 120), (1000, 128), (5000, 33),
-                                 (50000, 120), (200001, 120)])
+                                 (50000, 120), (200001, 120), (77_953, 128), (1_000_000, 120)])
 def test_gram_splitbf16_matches_oracle(R, l):
     X, buf = _block(R, l, seed=R + l, scale_cols=(R % 2 == 1))
     B = torch.empty((l, l), dtype=torch.float64, device=DEV)
@@ -55,7 +56,7 @@ def test_gram_splitbf16_matches_oracle(R, l):
     B = B.cpu().numpy()
     X64 = X.astype(np.float64)
     ref = oracle.gram(X64)
-    bound = 32 * 2.0 ** -24 * (np.abs(X64).T @ np.abs(X64))
+    bound = 64 * 2.0 ** -24 * (np.abs(X64).T @ np.abs(X64))
     assert np.all(np.abs(B - ref) <= bound), np.max(np.abs(B - ref) / bound)
     assert np.array_equal(B, B.T)
 
