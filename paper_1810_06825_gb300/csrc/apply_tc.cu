@@ -11,9 +11,11 @@
 // B operand (K-major, no swizzle) for all of the CTA's 128-row tiles of M; a
 // tile is read once from HBM in chunks of 64 columns that are split in
 // registers (the next chunk is loaded while the current one is stored and
-// multiplied), and its result is staged through shared memory so rows of Y
-// are written coalesced.  A tile's rows are read completely before they are
-// written, so Y may be M itself (same leading dimension).
+// multiplied).  Tiles alternate between two TMEM accumulator pairs, so a
+// tile's result is read back (tcgen05.ld) and written to Y, 32 consecutive
+// floats of a row per thread, while the next tile's MMAs run.  A tile's rows
+// are read completely before they are written, so Y may be M itself (same
+// leading dimension).
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -35,8 +37,6 @@ constexpr int kAtMaxChunks = 2;                // l <= 128
 constexpr int kAtStage = 3 * kAtOp;            // the three splits of one chunk of M
 constexpr int kAtBytesB = 3 * kAtMaxChunks * kAtOp;  // W, resident: 96 KiB
 constexpr int kAtSmem = kAtBytesB + 2 * kAtStage + 64;
-constexpr int kAtOutStride = kAtRows + 1;      // staged output rows (floats)
-static_assert(kAtRows * kAtOutStride * 4 <= 2 * kAtStage, "output staging fits in the two stages");
 
 // One chunk of M for a thread: items (row, 8-column group) t + 256 u.
 struct AtRegs {
@@ -87,21 +87,59 @@ __device__ inline void at_store(const AtRegs &a, unsigned char *stage) {
     }
 }
 
+// Writes this thread's part of a finished tile from TMEM accumulator pair
+// `pair` straight to Y: warp w holds rows 32 (w % 4) .. +31 of the tile (its
+// TMEM lanes) and columns 64 (w / 4) .. +63, so every thread writes runs of
+// 32 consecutive floats of one row.
+__device__ inline void at_epilogue(uint32_t tmem, int pair, int64_t row0, int64_t R, int kout, float *Y, int64_t ldy,
+                                   bool vec4) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = 32 * (warp & 3) + lane;
+    const int col0 = 64 * (warp >> 2);
+    const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t d_main = tmem + (uint32_t)pair * 256, d_corr = d_main + 128;
+    const int64_t row = row0 + r;
+#pragma unroll 1
+    for (int q = 0; q < 2; ++q) {
+        const int c0 = col0 + 32 * q;
+        if (c0 >= kout) break;  // warp-uniform
+        float vm[32], vc[32];
+        tmem_ld32(d_main + lane_addr + c0, vm);
+        tmem_ld32(d_corr + lane_addr + c0, vc);
+        if (row >= R) continue;
+        float *yr = Y + row * ldy + c0;
+        if (vec4 && c0 + 32 <= kout) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+                *reinterpret_cast<float4 *>(yr + i) =
+                    make_float4(vm[i] + vc[i], vm[i + 1] + vc[i + 1], vm[i + 2] + vc[i + 2], vm[i + 3] + vc[i + 3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (c0 + i < kout) yr[i] = vm[i] + vc[i];
+        }
+    }
+}
+
+// Persistent CTA per SM over 128-row tiles.  A tile's chunks are split into
+// the two operand stages and multiplied into TMEM accumulator pair
+// (tile index) % 2; the previous tile's pair is read out and written to Y
+// while the current tile's MMAs run.
 __global__ void __launch_bounds__(kAtThreads, 1)
 apply_tc_kernel(int64_t R, int l, int kout, const float *M, int64_t ldm, const float *__restrict__ W, float *Y,
                 int64_t ldy, int *status, long long limit_cycles) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *Bres = smem;                       // chunk c, split z at (3 c + z) kAtOp
     unsigned char *stages = smem + kAtBytesB;         // stage b at b kAtStage
+    // mbar[0..1]: operand stages; mbar[2..3]: accumulator pairs (one commit per tile).
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + kAtBytesB + 2 * kAtStage);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 2);
-    float *otile = reinterpret_cast<float *>(stages);  // kAtRows x kAtOutStride, after a tile's MMAs
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 4);
+    const int warp = threadIdx.x >> 5, t = threadIdx.x;
     const int nch = (l + kAtKc - 1) / kAtKc;
-    if (warp == 0) tmem_alloc(tmem_slot, 256);
+    const bool vec4 = (ldy % 4) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15u) == 0;
+    if (warp == 0) tmem_alloc(tmem_slot, 512);
     if (t == 0) {
-        mbar_init(smem_u32(mbar), 1);
-        mbar_init(smem_u32(mbar + 1), 1);
+        for (int i = 0; i < 4; ++i) mbar_init(smem_u32(mbar + i), 1);
         fence_mbar_init();
     }
     // W as the B operand: element (n = output column, k) at op_offset(n, k mod 64).
@@ -124,15 +162,19 @@ apply_tc_kernel(int64_t R, int l, int kout, const float *M, int64_t ldm, const f
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t d_main = *tmem_slot, d_corr = d_main + 128;
+    const uint32_t tmem = *tmem_slot;
     const int64_t ntiles = ceil_div(R, kAtRows);
     uint32_t uses[2] = {0u, 0u};
     bool ok = true;
     AtRegs areg;
     if ((int64_t)blockIdx.x < ntiles) at_load(M, ldm, R, l, (int64_t)blockIdx.x * kAtRows, 0, areg);
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    int64_t prev_row0 = -1;  // the previous tile, whose pair is still to be written out
+    int prev_pair = 0;
+    int64_t it_no = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it_no) {
         const int64_t row0 = tile * kAtRows;
-        int last = 0;
+        const int pair = (int)(it_no & 1);
+        const uint32_t d_main = tmem + (uint32_t)pair * 256, d_corr = d_main + 128;
         for (int c = 0; c < nch; ++c) {
             const int b = c & 1;
             unsigned char *stage = stages + b * kAtStage;
@@ -162,44 +204,51 @@ apply_tc_kernel(int64_t R, int l, int kout, const float *M, int64_t ldm, const f
                                make_desc(bb + 2 * kAtOp + koff), c > 0 || ks > 0);
                 }
                 mma_commit(smem_u32(mbar + b));
+                if (c + 1 == nch) mma_commit(smem_u32(mbar + 2 + pair));
             }
             uses[b] += 1;
-            last = b;
         }
         if (!ok) break;
-        // The last commit covers every MMA of the tile; both stages are free.
-        const bool done = mbar_wait_bounded(smem_u32(mbar + last), (uses[last] - 1) & 1, limit_cycles);
-        if (!__syncthreads_and(done)) {
-            ok = false;
-            break;
+        // The previous tile's pair is final once its own commit (the
+        // (it_no - 1) / 2-th on that pair's barrier, whose next commit is
+        // only issued after this wait) has arrived: write it out while this
+        // tile's MMAs run.
+        if (prev_row0 >= 0) {
+            const bool done =
+                mbar_wait_bounded(smem_u32(mbar + 2 + prev_pair), (uint32_t)(((it_no - 1) >> 1) & 1), limit_cycles);
+            if (!__syncthreads_and(done)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            at_epilogue(tmem, prev_pair, prev_row0, R, kout, Y, ldy, vec4);
+            fence_before();
         }
-        fence_after();
-        const int row = 32 * (warp & 3) + lane;  // TMEM lane = row of the tile
-        const int col0 = 64 * (warp >> 2);
-        const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
-#pragma unroll 1
-        for (int q = 0; q < 2; ++q) {
-            float vm[32], vc[32];
-            tmem_ld32(d_main + lane_addr + col0 + 32 * q, vm);
-            tmem_ld32(d_corr + lane_addr + col0 + 32 * q, vc);
-            float *orow = otile + row * kAtOutStride + col0 + 32 * q;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) orow[i] = vm[i] + vc[i];
-        }
-        fence_before();
-        __syncthreads();
-        const int rows = (int)std::min<int64_t>(kAtRows, R - row0);
-        for (int idx = t; idx < rows * kout; idx += kAtThreads) {
-            const int r = idx / kout, cc = idx - r * kout;
-            Y[(row0 + r) * ldy + cc] = otile[r * kAtOutStride + cc];
-        }
-        __syncthreads();
+        prev_row0 = row0;
+        prev_pair = pair;
     }
-    if (!ok && t == 0) set_status(status, FRPCA_ERR_TIMEOUT);
+    if (ok && prev_row0 >= 0) {
+        const bool done =
+            mbar_wait_bounded(smem_u32(mbar + 2 + prev_pair), (uint32_t)(((it_no - 1) >> 1) & 1), limit_cycles);
+        if (__syncthreads_and(done)) {
+            fence_after();
+            at_epilogue(tmem, prev_pair, prev_row0, R, kout, Y, ldy, vec4);
+        } else {
+            ok = false;
+        }
+    }
+    if (!ok) {
+        // A wait ran out: give the MMAs already issued (covered by each
+        // stage's newest commit) a bounded chance to finish before the TMEM
+        // is released.
+        for (int b = 0; b < 2; ++b)
+            if (uses[b] > 0) (void)mbar_wait_bounded(smem_u32(mbar + b), (uses[b] - 1) & 1, limit_cycles);
+        if (t == 0) set_status(status, FRPCA_ERR_TIMEOUT);
+    }
     fence_before();
     __syncthreads();
     fence_after();
-    if (warp == 0) tmem_dealloc(d_main, 256);
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 }  // namespace

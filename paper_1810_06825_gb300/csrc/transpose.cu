@@ -346,11 +346,29 @@ namespace {
 // perm[p] = the entry of A that lands at position p of A^T (row-major entry
 // index); values of A^T are gathered through it, so a refresh after the values
 // changed in place is one gather instead of a sort.
+// Each thread gathers kGatherUnroll entries spaced a block apart, with all of
+// their (random) value loads issued before the first store, so enough reads
+// are in flight to cover DRAM latency.
+constexpr int kGatherUnroll = 8;
 template <typename T>
-__global__ void gather_values_kernel(const int32_t *__restrict__ perm, const T *__restrict__ vals, int64_t nnz,
-                                     T *__restrict__ out) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
-        out[p] = vals[perm[p]];
+__global__ void __launch_bounds__(256)
+gather_values_kernel(const int32_t *__restrict__ perm, const T *__restrict__ vals, int64_t nnz,
+                     T *__restrict__ out) {
+    const int64_t base = (int64_t)blockIdx.x * 256 * kGatherUnroll + threadIdx.x;
+    int32_t src[kGatherUnroll];
+    T v[kGatherUnroll];
+#pragma unroll
+    for (int u = 0; u < kGatherUnroll; ++u) {
+        const int64_t p = base + (int64_t)u * 256;
+        src[u] = p < nnz ? __ldcs(perm + p) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kGatherUnroll; ++u) v[u] = base + (int64_t)u * 256 < nnz ? __ldg(vals + src[u]) : T(0);
+#pragma unroll
+    for (int u = 0; u < kGatherUnroll; ++u) {
+        const int64_t p = base + (int64_t)u * 256;
+        if (p < nnz) __stcs(out + p, v[u]);
+    }
 }
 
 cudaError_t sort_structure(const DeviceCSR &A, DeviceCSR &AT, int32_t *perm, DevBuf &scratch, DevBuf &scan_scratch,
@@ -418,7 +436,7 @@ cudaError_t sort_structure(const DeviceCSR &A, DeviceCSR &AT, int32_t *perm, Dev
 
 cudaError_t csr_transpose_values(const DeviceCSR &A, DeviceCSR &AT, const int32_t *perm, cudaStream_t s) {
     if (A.nnz == 0) return cudaSuccess;
-    const unsigned g = grid_for(A.nnz, 256);
+    const unsigned g = (unsigned)ceil_div(A.nnz, 256 * kGatherUnroll);
     if (A.dtype == FRPCA_F32)
         gather_values_kernel<float><<<g, 256, 0, s>>>(perm, (const float *)A.vals, A.nnz, (float *)AT.vals);
     else
