@@ -103,6 +103,11 @@ typedef struct frpca_create_opts {
                                  workspaces; the caller's buffers are not counted).  An
                                  allocation that would pass it fails with FRPCA_ERR_OOM,
                                  as a failed cudaMallocAsync does                          */
+    int panel_rows;           /* the pass that gathers rows of the larger dense block (A^T X
+                                 when m >= n) reads that block in panels of this many rows,
+                                 one after the other into the output, so a panel stays in
+                                 L2: 0 = automatic (131,072 rows when the block has at least
+                                 three times that many), -1 = off, > 0 = that many rows   */
 } frpca_create_opts;
 
 /* Creates a handle.  csr may be NULL: the handle then serves only the

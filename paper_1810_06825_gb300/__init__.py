@@ -47,7 +47,7 @@ class frpca_csr(ctypes.Structure):
 
 class frpca_create_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("borrow", ctypes.c_int), ("validate", ctypes.c_int),
-                ("hot_columns", ctypes.c_int), ("max_device_bytes", ctypes.c_int64)]
+                ("hot_columns", ctypes.c_int), ("max_device_bytes", ctypes.c_int64), ("panel_rows", ctypes.c_int)]
 
 
 class frpca_run_opts(ctypes.Structure):
@@ -281,11 +281,13 @@ class FrPCA:
     nonzero on the CSR kernel; -1 picks the densest columns automatically and
     > 0 that many (multiples of 128, at most 256) for a dense block whose share
     of each pass runs on the tensor cores.  ``max_device_bytes`` caps the
-    device memory the handle allocates for itself (0: no cap).
+    device memory the handle allocates for itself (0: no cap).  ``panel_rows``:
+    the panel height of the pass that gathers rows of the larger dense block
+    (0 automatic, -1 off).
     """
 
     def __init__(self, indptr, indices, values, shape, stream=None, borrow=True, validate=True, hot_columns=0,
-                 max_device_bytes=0):
+                 max_device_bytes=0, panel_rows=0):
         torch = _torch()
         _need_cuda(indptr, indices, values)
         if indptr.dtype not in (torch.int64, torch.int32):
@@ -295,10 +297,10 @@ class FrPCA:
         self._setup(self.indptr.data_ptr(), self.indices.data_ptr() if self.indices.numel() else None,
                     self.values.data_ptr() if self.values.numel() else None, int(self.indices.numel()),
                     self.indptr.dtype == torch.int32, self.values.dtype, shape, 1, self.values.device, stream,
-                    borrow, validate, hot_columns, max_device_bytes)
+                    borrow, validate, hot_columns, max_device_bytes, panel_rows)
 
     def _setup(self, p_indptr, p_indices, p_values, nnz, rp32, dtype, shape, on_device, device, stream, borrow,
-               validate, hot_columns, max_device_bytes):
+               validate, hot_columns, max_device_bytes, panel_rows=0):
         torch = _torch()
         self.m, self.n = int(shape[0]), int(shape[1])
         self._nnz = nnz
@@ -310,12 +312,12 @@ class FrPCA:
                         rowptr_type=FRPCA_I32 if rp32 else FRPCA_I64)
         opts = frpca_create_opts(stream=self.stream.cuda_stream, borrow=1 if borrow else 0,
                                  validate=1 if validate else 0, hot_columns=int(hot_columns),
-                                 max_device_bytes=int(max_device_bytes))
+                                 max_device_bytes=int(max_device_bytes), panel_rows=int(panel_rows))
         self.handle = frpca_create(csr, opts)
 
     @classmethod
     def from_host(cls, indptr, indices, values, shape, device="cuda", stream=None, validate=True, hot_columns=0,
-                  max_device_bytes=0):
+                  max_device_bytes=0, panel_rows=0):
         """From host arrays (numpy or CPU tensors; pinned memory copies fastest):
         the C ABI's own host path (``on_device = 0``) copies them to the
         device and validates them there."""
@@ -340,7 +342,7 @@ class FrPCA:
             self._setup(ip.ctypes.data, ix.ctypes.data if ix.size else None, va.ctypes.data if va.size else None,
                         int(ix.size), ip.dtype == np.int32,
                         torch.float32 if va.dtype == np.float32 else torch.float64, shape, 0, dev, stream,
-                        False, validate, hot_columns, max_device_bytes)
+                        False, validate, hot_columns, max_device_bytes, panel_rows)
         return self
 
     @classmethod

@@ -29,6 +29,9 @@ struct frpca_ctx {
     SpmmPlan planA, planAT;
     DevBuf ws_q, ws_w, ws_spmm, ws_gram, ws_eig, ws_lu, ws_small, ws_sign, ws_scratch, ws_scan, ws_bwd, ws_hot, ws_plan;
     HybridCSR hy;  // the densest columns of A as a dense block (FP32 SpMM on the tensor cores)
+    PanelCSR pan;  // the pass that gathers rows of the larger block, by panels of those rows
+    int pan_trans = 1;           // which pass uses it: 1 = A^T X (m >= n), 0 = A X (m < n)
+    bool at_vals_stale = false;  // A^T's values wait for a refresh (the panel pass had its own)
     MemBudget budget;                            // frpca_create_opts.max_device_bytes
     long long wait_limit = kBarrierLimitCycles;  // frpca_set_wait_limit
     std::string err;
@@ -144,7 +147,17 @@ bool ld_ok(int64_t ld, int l, frpca_dtype dt) {
 }
 
 // Values of A / A^T in dtype dt (converted once if A was given in the other).
+// A^T's own values, after a refresh that only updated the panel form.
+frpca_status fresh_at_values(frpca_ctx *h) {
+    if (!h->at_vals_stale) return FRPCA_OK;
+    CK(csr_transpose_values(h->A, h->AT, (const int32_t *)h->t_perm.ptr, h->stream), "transpose values");
+    h->at_vals_stale = false;
+    return FRPCA_OK;
+}
+
 frpca_status values_for(frpca_ctx *h, frpca_dtype dt, const void **va, const void **vat) {
+    frpca_status st0 = fresh_at_values(h);
+    if (st0 != FRPCA_OK) return st0;
     if (dt == h->A.dtype) {
         *va = h->A.vals;
         *vat = h->AT.vals;
@@ -166,6 +179,21 @@ frpca_status values_for(frpca_ctx *h, frpca_dtype dt, const void **va, const voi
 // One SpMM pass with the handle's matrix (trans selects A^T).
 frpca_status spmm_pass(frpca_ctx *h, int trans, int l, const void *X, int64_t ldx, void *Y, int64_t ldy,
                        frpca_dtype dt) {
+    if (h->pan.active() && trans == h->pan_trans && dt == h->A.dtype) {
+        // The gathered block is read panel by panel, each panel resident in L2.
+        CK(h->ws_spmm.ensure(std::max<size_t>(256, panel_scratch_bytes(h->pan, l, dt))), "alloc spmm scratch");
+        PhaseTimer t(h, trans ? PH_SPMM_T : PH_SPMM);
+        CK(launch_spmm_panels(h->pan, l, X, ldx, Y, ldy, dt, h->ws_spmm.ptr, h->stream), "panel spmm launch");
+        t.done();
+        const double sv = (double)dsize(dt);
+        const DeviceCSR &C = trans ? h->AT : h->A;
+        h->acc.spmm_passes += 1;
+        (trans ? h->acc.spmm_t_passes : h->acc.spmm_a_passes) += 1;
+        h->acc.spmm_bytes += (double)C.nnz * (sv + 4.0) + (double)(C.rows + 1) * 8.0 +
+                             ((double)C.cols + (double)C.rows) * (double)l * sv;
+        h->acc.spmm_flops += 2.0 * (double)C.nnz * (double)l;
+        return FRPCA_OK;
+    }
     const void *va, *vat;
     frpca_status st = values_for(h, dt, &va, &vat);
     if (st != FRPCA_OK) return st;
@@ -518,12 +546,39 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
             return bail(cuda_fail(h, e, perr.c_str()));
     }
     {
+        // Panels over the rows of the larger dense block when it is well
+        // beyond L2: 131,072 rows (64 MiB of float rows at l <= 128) each.
+        const int64_t big = std::max(m, n);
+        const int pr = opts ? opts->panel_rows : 0;
+        const int64_t P = pr > 0 ? (int64_t)pr : (int64_t)131072;
+        h->pan_trans = m >= n ? 1 : 0;
+        const DeviceCSR &C = m >= n ? h->AT : h->A;
+        const bool want = pr > 0 ? big > P : (pr == 0 && big >= 3 * P);
+        if (want && nnz > 0 && ceil_div(big, P) * C.rows < ((int64_t)1 << 31)) {
+            h->pan.plan.budget = &h->budget;
+            for (DevBuf *b : {&h->pan.b_rowptr, &h->pan.b_colidx, &h->pan.b_vals, &h->pan.b_perm}) {
+                b->stream = h->stream;
+                b->budget = &h->budget;
+            }
+            if ((e = build_panel_csr(C, m >= n ? (const int32_t *)h->t_perm.ptr : nullptr, P, h->pan, h->ws_scratch,
+                                     h->ws_scan, h->stream)) != cudaSuccess ||
+                (e = panel_values(h->A, h->pan, h->stream)) != cudaSuccess)
+                return bail(cuda_fail(h, e, "panel form"));
+            if ((e = build_panel_plan(h->pan, h->ws_plan, h->ws_scan, h->stream, perr)) != cudaSuccess)
+                return bail(cuda_fail(h, e, perr.c_str()));
+        }
+    }
+    {
         const int hc = opts ? opts->hot_columns : 0;
         const int want = hc < 0 ? -1 : hc;  // -1 automatic, 0 off, > 0 a count
         if ((e = build_hybrid(h->A, h->AT, want, h->hy, h->ws_scan, h->stream, perr)) != cudaSuccess)
             return bail(cuda_fail(h, e, perr.empty() ? "hot-column block" : perr.c_str()));
     }
     h->has_matrix = true;
+    // The sort scratch (several int32 arrays of nnz entries) is needed again
+    // only by a later create; give it back.
+    h->ws_scratch.release();
+    h->ws_plan.release();
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "synchronize"));
     *out = h;
     return FRPCA_OK;
@@ -536,6 +591,7 @@ frpca_status frpca_destroy(frpca_handle h) {
     h->planA.free_all();
     h->planAT.free_all();
     h->hy.free_all();
+    h->pan.free_all();
     for (DevBuf *b : {&h->own_rowptr, &h->own_colidx, &h->own_vals, &h->t_rowptr, &h->t_colidx, &h->t_vals,
                       &h->t_perm, &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
                       &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot, &h->ws_plan})
@@ -560,7 +616,17 @@ frpca_status frpca_refresh(frpca_handle h) {
     if (!h) return FRPCA_ERR_INVALID_ARG;
     if (!h->has_matrix) return fail(h, FRPCA_ERR_INVALID_ARG, "handle has no matrix");
     PhaseTimer t(h, PH_TRANSPOSE);
-    CK(csr_transpose_values(h->A, h->AT, (const int32_t *)h->t_perm.ptr, h->stream), "transpose values");
+    if (h->pan.active()) {
+        // The runs read the panel form; A^T's own values follow when needed.
+        CK(panel_values(h->A, h->pan, h->stream), "panel values");
+        h->at_vals_stale = true;
+    } else {
+        CK(csr_transpose_values(h->A, h->AT, (const int32_t *)h->t_perm.ptr, h->stream), "transpose values");
+    }
+    if (h->hy.h > 0) {
+        frpca_status st = fresh_at_values(h);
+        if (st != FRPCA_OK) return st;
+    }
     CK(refresh_hybrid(h->A, h->hy, h->stream), "hot-column block");
     t.done();
     h->alt_ready = false;
@@ -654,6 +720,8 @@ frpca_status frpca_spmm(frpca_handle h, int trans, int l, const void *X, int64_t
 frpca_status frpca_get_transpose(frpca_handle h, int64_t *rowptrT, int32_t *colidxT, void *valuesT) {
     if (!h) return FRPCA_ERR_INVALID_ARG;
     if (!h->has_matrix) return fail(h, FRPCA_ERR_INVALID_ARG, "handle has no matrix");
+    frpca_status st = fresh_at_values(h);
+    if (st != FRPCA_OK) return st;
     CK(cudaMemcpyAsync(rowptrT, h->AT.rowptr, 8 * (size_t)(h->AT.rows + 1), cudaMemcpyDeviceToDevice, h->stream),
        "copy rowptr");
     if (h->A.nnz > 0) {

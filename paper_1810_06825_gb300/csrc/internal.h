@@ -44,6 +44,7 @@ struct SpmmPlan {
     cudaStream_t stream = nullptr;  // stream the arrays were allocated on
     MemBudget *budget = nullptr;    // allocation cap the arrays are charged to
     size_t charged = 0;             // bytes charged to budget
+    bool skip_empty = false;        // leave empty rows out (their output rows are not written)
     void free_all();
 };
 
@@ -75,6 +76,28 @@ struct DevBuf {
     void release();
 };
 
+// The gathering pass reorganized by panels of the gathered block: C's entries
+// (C = A or A^T, whichever gathers rows of the larger dense block) stably
+// sorted by (panel of their column, row of C), as a CSR over the virtual rows
+// b * src_rows + j (row j of C restricted to panel b, columns b P .. b P + P-1).
+// A pass runs one panel after the other into the zeroed output, each panel's
+// rows accumulating onto the previous panels' sums, so the panel of the
+// gathered block a launch reads stays resident in L2.
+struct PanelCSR {
+    int64_t panel_rows = 0;   // P: rows of the gathered block per panel
+    int64_t npanels = 0;
+    int64_t src_rows = 0;     // rows of C
+    DeviceCSR virt;           // npanels * src_rows virtual rows
+    SpmmPlan plan;            // over virt, empty virtual rows left out
+    // per panel b (npanels + 1 entries): first short row, first long row and
+    // first segment of the plan that belong to panel b
+    std::vector<int64_t> short_off, long_off, seg_off;
+    int64_t max_panel_segs = 0;
+    DevBuf b_rowptr, b_colidx, b_vals, b_perm;  // perm: entry of A at each position of virt
+    bool active() const { return npanels > 0; }
+    void free_all();
+};
+
 // ---- gaussian.cu
 cudaError_t launch_gaussian(int64_t R, int l, int64_t ld, uint64_t seed, frpca_dtype dt, void *out,
                             cudaStream_t s);
@@ -89,6 +112,12 @@ cudaError_t csr_transpose(const DeviceCSR &A, DeviceCSR &AT, int32_t *perm, DevB
                           cudaStream_t s);
 // Values of A^T from those of A through perm (same structure).
 cudaError_t csr_transpose_values(const DeviceCSR &A, DeviceCSR &AT, const int32_t *perm, cudaStream_t s);
+// Panel-major CSR of C (the entries of A mapped by mapC: position in C -> entry
+// of A, NULL for C = A) with panels of P columns of C; values gathered by
+// panel_values.  Needs npanels * rows(C) < 2^31.
+cudaError_t build_panel_csr(const DeviceCSR &C, const int32_t *mapC, int64_t P, PanelCSR &pc, DevBuf &scratch,
+                            DevBuf &scan_scratch, cudaStream_t s);
+cudaError_t panel_values(const DeviceCSR &A, PanelCSR &pc, cudaStream_t s);
 cudaError_t launch_convert(const void *in, frpca_dtype din, void *out, frpca_dtype dout, int64_t n,
                            cudaStream_t s);
 // out[i] = in[i] (int32 -> int64), n elements.
@@ -107,6 +136,13 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
 // per-row flags and scans.
 cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *const *plans, int count, DevBuf &scratch,
                                     DevBuf &scan_scratch, cudaStream_t s, std::string &err);
+// The plan of a PanelCSR (empty virtual rows left out) and its per-panel
+// offsets (one host synchronization).
+cudaError_t build_panel_plan(PanelCSR &pc, DevBuf &scratch, DevBuf &scan_scratch, cudaStream_t s, std::string &err);
+size_t panel_scratch_bytes(const PanelCSR &pc, int l, frpca_dtype dt);
+// Y (src_rows x l) = C X, panel by panel (Y is zeroed first).
+cudaError_t launch_spmm_panels(const PanelCSR &pc, int l, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                               frpca_dtype dt, void *scratch, cudaStream_t s);
 size_t spmm_scratch_bytes(const SpmmPlan &plan, int l, frpca_dtype dt);
 cudaError_t launch_spmm(const DeviceCSR &A, const void *vals, const SpmmPlan &plan, int l, const void *X,
                         int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *scratch, cudaStream_t s, bool accumulate = false);

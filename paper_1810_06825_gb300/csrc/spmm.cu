@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kThreads)
 spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, const T *__restrict__ vals,
             const int32_t *__restrict__ short_rows, int64_t n_short, const int64_t *__restrict__ seg_start,
             const int32_t *__restrict__ seg_len, int64_t n_segs, int nvec, const T *__restrict__ X, int64_t ldx,
-            T *__restrict__ Y, int64_t ldy, T *__restrict__ partial, int accumulate) {
+            T *__restrict__ Y, int64_t ldy, T *__restrict__ partial, int accumulate, int64_t out_row_offset) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::width;
     const int lane = threadIdx.x & 31;
@@ -42,7 +42,7 @@ spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ coli
         const int32_t row = short_rows[w];
         start = rowptr[row];
         len = (int)(rowptr[row + 1] - start);
-        out = reinterpret_cast<V *>(Y + (int64_t)row * ldy);
+        out = reinterpret_cast<V *>(Y + ((int64_t)row - out_row_offset) * ldy);
     } else if (w - n_short < n_segs) {
         const int64_t sidx = w - n_short;
         start = seg_start[sidx];
@@ -112,17 +112,20 @@ spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ coli
     }
 }
 
+// partial holds the segments seg_base, seg_base + 1, ... (long_first values
+// are absolute segment indices); output row = long row - out_row_offset.
 template <typename T>
 __global__ void spmm_fixup_kernel(int64_t n_long, const int32_t *__restrict__ long_rows,
                                   const int64_t *__restrict__ long_first, int nvec, const T *__restrict__ partial,
-                                  T *__restrict__ Y, int64_t ldy, int accumulate) {
+                                  T *__restrict__ Y, int64_t ldy, int accumulate, int64_t seg_base,
+                                  int64_t out_row_offset) {
     using V = typename Vec<T>::type;
     const int lane = threadIdx.x & 31;
     const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (r >= n_long) return;
-    const int64_t s0 = long_first[r], s1 = long_first[r + 1];
+    const int64_t s0 = long_first[r] - seg_base, s1 = long_first[r + 1] - seg_base;
     const V *P = reinterpret_cast<const V *>(partial);
-    V *out = reinterpret_cast<V *>(Y + (int64_t)long_rows[r] * ldy);
+    V *out = reinterpret_cast<V *>(Y + ((int64_t)long_rows[r] - out_row_offset) * ldy);
     for (int vi = lane; vi < nvec; vi += 32) {
         V acc = accumulate ? out[vi] : Vec<T>::zero();
         for (int64_t s = s0; s < s1; ++s) Vec<T>::add(acc, P[s * nvec + vi]);
@@ -130,8 +133,27 @@ __global__ void spmm_fixup_kernel(int64_t n_long, const int32_t *__restrict__ lo
     }
 }
 
+// The rows of one launch: a sub-range of a plan's lists (whole rows, segments
+// of long rows, long rows for the fix-up).
+struct SpmmWork {
+    const int32_t *short_rows;
+    int64_t n_short;
+    const int64_t *seg_start;
+    const int32_t *seg_len;
+    int64_t n_segs, seg_base;
+    const int32_t *long_rows;
+    const int64_t *long_first;
+    int64_t n_long;
+    int64_t out_row_offset;
+};
+
+SpmmWork whole_plan(const SpmmPlan &p) {
+    return SpmmWork{p.short_rows, p.n_short, p.seg_start, p.seg_len, p.n_segs, 0, p.long_rows, p.long_first,
+                    p.n_long, 0};
+}
+
 template <typename T>
-cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmPlan &p, int l, const T *X, int64_t ldx, T *Y,
+cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmWork &p, int l, const T *X, int64_t ldx, T *Y,
                          int64_t ldy, T *partial, bool accumulate, cudaStream_t s) {
     constexpr int W = Vec<T>::width;
     const int nvec = (int)ceil_div(l, W);
@@ -143,7 +165,9 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmPlan &p, i
     case NVV:                                                                                                 \
         spmm_kernel<T, NVV><<<(unsigned)blocks, kThreads, 0, s>>>(A.rowptr, A.colidx, vals, p.short_rows,     \
                                                                   p.n_short, p.seg_start, p.seg_len,          \
-                                                                  p.n_segs, nvec, X, ldx, Y, ldy, partial, accumulate); count_launch();   \
+                                                                  p.n_segs, nvec, X, ldx, Y, ldy, partial,    \
+                                                                  accumulate, p.out_row_offset);              \
+        count_launch();                                                                                       \
         break;
         switch (nv) {
             FRPCA_SPMM_CASE(1)
@@ -157,9 +181,9 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmPlan &p, i
         if (e != cudaSuccess) return e;
     }
     if (p.n_long > 0) {
-        spmm_fixup_kernel<T><<<(unsigned)ceil_div(p.n_long * 32, 256), 256, 0, s>>>(p.n_long, p.long_rows,
-                                                                                   p.long_first, nvec, partial,
-                                                                                   Y, ldy, accumulate); count_launch();
+        spmm_fixup_kernel<T><<<(unsigned)ceil_div(p.n_long * 32, 256), 256, 0, s>>>(
+            p.n_long, p.long_rows, p.long_first, nvec, partial, Y, ldy, accumulate, p.seg_base, p.out_row_offset);
+        count_launch();
         return cudaGetLastError();
     }
     return cudaSuccess;
@@ -237,32 +261,36 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
 // ---- the same plan built on the device (no host pass over the rows)
 namespace {
 
-// Per row: 1 if handled whole (at most seg entries), and its number of
-// segments otherwise.
-__global__ void plan_flags_kernel(int64_t m, const int64_t *__restrict__ rowptr, int seg, int32_t *__restrict__ is_short,
+// Per row: 1 if handled whole (at most seg entries; an empty row only when the
+// plan keeps empty rows), 1 if cut into segments, and its number of segments.
+__global__ void plan_flags_kernel(int64_t m, const int64_t *__restrict__ rowptr, int seg, int skip_empty,
+                                  int32_t *__restrict__ is_short, int32_t *__restrict__ is_long,
                                   int32_t *__restrict__ nseg) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= m) return;
     const int64_t len = rowptr[i + 1] - rowptr[i];
-    is_short[i] = len <= seg ? 1 : 0;
+    is_short[i] = (len <= seg && (len > 0 || !skip_empty)) ? 1 : 0;
+    is_long[i] = len > seg ? 1 : 0;
     nseg[i] = len <= seg ? 0 : (int32_t)((len + seg - 1) / seg);
 }
 
 // Order-preserving compaction from the scans: short rows, long rows with
 // their first segment, and every segment's (start, length).
 __global__ void plan_fill_kernel(int64_t m, const int64_t *__restrict__ rowptr, int seg,
-                                 const int32_t *__restrict__ is_short, const int64_t *__restrict__ short_pos,
+                                 const int32_t *__restrict__ is_short, const int32_t *__restrict__ is_long,
+                                 const int64_t *__restrict__ short_pos, const int64_t *__restrict__ long_pos,
                                  const int64_t *__restrict__ seg_off, int32_t *__restrict__ short_rows,
                                  int32_t *__restrict__ long_rows, int64_t *__restrict__ long_first,
                                  int64_t *__restrict__ seg_start, int32_t *__restrict__ seg_len) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i == 0) long_first[m - short_pos[m]] = seg_off[m];
+    if (i == 0) long_first[long_pos[m]] = seg_off[m];
     if (i >= m) return;
     if (is_short[i]) {
         short_rows[short_pos[i]] = (int32_t)i;
         return;
     }
-    const int64_t j = i - short_pos[i];  // rank among the long rows
+    if (!is_long[i]) return;  // an empty row left out
+    const int64_t j = long_pos[i];  // rank among the long rows
     const int64_t first = seg_off[i], start = rowptr[i], end = rowptr[i + 1];
     long_rows[j] = (int32_t)i;
     long_first[j] = first;
@@ -272,44 +300,79 @@ __global__ void plan_fill_kernel(int64_t m, const int64_t *__restrict__ rowptr, 
     }
 }
 
+// First entry of each panel in the plan's sorted row lists: short rows and
+// long rows of panel b are those with virtual row in [b rows, (b + 1) rows).
+__global__ void panel_offsets_kernel(int64_t npanels, int64_t rows, const int32_t *__restrict__ short_rows,
+                                     int64_t n_short, const int32_t *__restrict__ long_rows, int64_t n_long,
+                                     const int64_t *__restrict__ long_first, int64_t *__restrict__ out) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b > npanels) return;
+    const int64_t key = b * rows;
+    int64_t lo = 0, hi = n_short;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if ((int64_t)short_rows[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    out[b] = lo;
+    lo = 0;
+    hi = n_long;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if ((int64_t)long_rows[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    out[(npanels + 1) + b] = lo;
+    out[2 * (npanels + 1) + b] = long_first[lo];
+}
+
 }  // namespace
 
 cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *const *plans, int count, DevBuf &scratch,
                                     DevBuf &scan_scratch, cudaStream_t s, std::string &err) {
-    // Scratch per matrix: flags (2 x rows int32) and scans (2 x (rows + 1) int64).
+    // Scratch per matrix: flags (3 x rows int32) and scans (3 x (rows + 1) int64).
     std::vector<size_t> off((size_t)count + 1, 0);
     for (int c = 0; c < count; ++c)
-        off[c + 1] = off[c] + round_up(8 * (size_t)mats[c]->rows + 16 * ((size_t)mats[c]->rows + 1), 256);
+        off[c + 1] = off[c] + round_up(12 * (size_t)mats[c]->rows + 24 * ((size_t)mats[c]->rows + 1) + 16, 256);
     cudaError_t e = scratch.ensure(std::max<size_t>(off[count], 256));
     if (e != cudaSuccess) {
         err = "spmm plan: scratch allocation failed";
         return e;
     }
-    auto parts = [&](int c, int32_t *&is_short, int32_t *&nseg, int64_t *&short_pos, int64_t *&seg_off) {
+    struct Parts {
+        int32_t *is_short, *is_long, *nseg;
+        int64_t *short_pos, *long_pos, *seg_off;
+    };
+    auto parts = [&](int c) {
         const int64_t m = mats[c]->rows;
         char *p = (char *)scratch.ptr + off[c];
-        is_short = (int32_t *)p;
-        nseg = is_short + m;
-        short_pos = (int64_t *)round_up((int64_t)(uintptr_t)(nseg + m), 8);
-        seg_off = short_pos + m + 1;
+        Parts q;
+        q.is_short = (int32_t *)p;
+        q.is_long = q.is_short + m;
+        q.nseg = q.is_long + m;
+        q.short_pos = (int64_t *)round_up((int64_t)(uintptr_t)(q.nseg + m), 8);
+        q.long_pos = q.short_pos + m + 1;
+        q.seg_off = q.long_pos + m + 1;
+        return q;
     };
-    std::vector<int64_t> totals(2 * (size_t)count, 0);
+    std::vector<int64_t> totals(3 * (size_t)count, 0);
     for (int c = 0; c < count; ++c) {
         const DeviceCSR &A = *mats[c];
+        const bool skip = plans[c]->skip_empty;
         plans[c]->free_all();
         plans[c]->stream = s;
         plans[c]->seg = kDefaultSeg;
-        int32_t *is_short, *nseg;
-        int64_t *short_pos, *seg_off;
-        parts(c, is_short, nseg, short_pos, seg_off);
-        plan_flags_kernel<<<(unsigned)ceil_div(A.rows, 256), 256, 0, s>>>(A.rows, A.rowptr, kDefaultSeg, is_short,
-                                                                         nseg);
+        const Parts q = parts(c);
+        plan_flags_kernel<<<(unsigned)ceil_div(A.rows, 256), 256, 0, s>>>(A.rows, A.rowptr, kDefaultSeg, skip ? 1 : 0,
+                                                                         q.is_short, q.is_long, q.nseg);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess ||
-            (e = exclusive_scan_i32_to_i64(is_short, short_pos, A.rows, scan_scratch, s)) != cudaSuccess ||
-            (e = exclusive_scan_i32_to_i64(nseg, seg_off, A.rows, scan_scratch, s)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(&totals[2 * c], short_pos + A.rows, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(&totals[2 * c + 1], seg_off + A.rows, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+            (e = exclusive_scan_i32_to_i64(q.is_short, q.short_pos, A.rows, scan_scratch, s)) != cudaSuccess ||
+            (e = exclusive_scan_i32_to_i64(q.is_long, q.long_pos, A.rows, scan_scratch, s)) != cudaSuccess ||
+            (e = exclusive_scan_i32_to_i64(q.nseg, q.seg_off, A.rows, scan_scratch, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&totals[3 * c], q.short_pos + A.rows, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&totals[3 * c + 1], q.long_pos + A.rows, 8, cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(&totals[3 * c + 2], q.seg_off + A.rows, 8, cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess) {
             err = "spmm plan: device pass failed";
             return e;
         }
@@ -321,9 +384,9 @@ cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *cons
     for (int c = 0; c < count; ++c) {
         const DeviceCSR &A = *mats[c];
         SpmmPlan &plan = *plans[c];
-        plan.n_short = totals[2 * c];
-        plan.n_long = A.rows - plan.n_short;
-        plan.n_segs = totals[2 * c + 1];
+        plan.n_short = totals[3 * c];
+        plan.n_long = totals[3 * c + 1];
+        plan.n_segs = totals[3 * c + 2];
         auto alloc = [&](void **dst, size_t bytes) -> cudaError_t {
             if (!bytes) return cudaSuccess;
             cudaError_t r = dev_malloc(dst, bytes, s, plan.budget);
@@ -338,12 +401,10 @@ cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *cons
             err = "spmm plan: device allocation failed";
             return e;
         }
-        int32_t *is_short, *nseg;
-        int64_t *short_pos, *seg_off;
-        parts(c, is_short, nseg, short_pos, seg_off);
+        const Parts q = parts(c);
         plan_fill_kernel<<<(unsigned)ceil_div(A.rows, 256), 256, 0, s>>>(
-            A.rows, A.rowptr, kDefaultSeg, is_short, short_pos, seg_off, plan.short_rows, plan.long_rows,
-            plan.long_first, plan.seg_start, plan.seg_len);
+            A.rows, A.rowptr, kDefaultSeg, q.is_short, q.is_long, q.short_pos, q.long_pos, q.seg_off, plan.short_rows,
+            plan.long_rows, plan.long_first, plan.seg_start, plan.seg_len);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) {
             err = "spmm plan: fill failed";
@@ -351,6 +412,80 @@ cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *cons
         }
     }
     return cudaSuccess;
+}
+
+cudaError_t build_panel_plan(PanelCSR &pc, DevBuf &scratch, DevBuf &scan_scratch, cudaStream_t s, std::string &err) {
+    pc.plan.skip_empty = true;
+    const DeviceCSR *mats[1] = {&pc.virt};
+    SpmmPlan *plans[1] = {&pc.plan};
+    cudaError_t e = build_spmm_plans_device(mats, plans, 1, scratch, scan_scratch, s, err);
+    if (e != cudaSuccess) return e;
+    const int64_t np1 = pc.npanels + 1;
+    DevBuf offs;
+    offs.stream = s;
+    if ((e = offs.ensure(sizeof(int64_t) * 3 * (size_t)np1)) != cudaSuccess) {
+        err = "spmm plan: scratch allocation failed";
+        return e;
+    }
+    panel_offsets_kernel<<<(unsigned)ceil_div(np1, 128), 128, 0, s>>>(
+        pc.npanels, pc.src_rows, pc.plan.short_rows, pc.plan.n_short, pc.plan.long_rows, pc.plan.n_long,
+        pc.plan.long_first, (int64_t *)offs.ptr);
+    count_launch();
+    std::vector<int64_t> h(3 * (size_t)np1);
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h.data(), offs.ptr, sizeof(int64_t) * h.size(), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        offs.release();
+        err = "spmm plan: panel offsets failed";
+        return e;
+    }
+    offs.release();
+    pc.short_off.assign(h.begin(), h.begin() + np1);
+    pc.long_off.assign(h.begin() + np1, h.begin() + 2 * np1);
+    pc.seg_off.assign(h.begin() + 2 * np1, h.end());
+    pc.max_panel_segs = 0;
+    for (int64_t b = 0; b < pc.npanels; ++b)
+        pc.max_panel_segs = std::max(pc.max_panel_segs, pc.seg_off[b + 1] - pc.seg_off[b]);
+    return cudaSuccess;
+}
+
+size_t panel_scratch_bytes(const PanelCSR &pc, int l, frpca_dtype dt) {
+    const int W = dt == FRPCA_F32 ? 4 : 2;
+    return (size_t)pc.max_panel_segs * (size_t)ceil_div(l, W) * 16;
+}
+
+cudaError_t launch_spmm_panels(const PanelCSR &pc, int l, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                               frpca_dtype dt, void *scratch, cudaStream_t s) {
+    const size_t es = dt == FRPCA_F32 ? 4 : 8;
+    cudaError_t e = cudaMemsetAsync(Y, 0, es * (size_t)pc.src_rows * (size_t)ldy, s);
+    if (e != cudaSuccess) return e;
+    for (int64_t b = 0; b < pc.npanels; ++b) {
+        const SpmmPlan &p = pc.plan;
+        const int64_t s0 = pc.short_off[b], s1 = pc.short_off[b + 1];
+        const int64_t l0 = pc.long_off[b], l1 = pc.long_off[b + 1];
+        const int64_t g0 = pc.seg_off[b], g1 = pc.seg_off[b + 1];
+        if (s1 == s0 && l1 == l0) continue;
+        const SpmmWork w{p.short_rows + s0, s1 - s0, p.seg_start + g0, p.seg_len + g0, g1 - g0, g0,
+                         p.long_rows + l0, p.long_first + l0, l1 - l0, b * pc.src_rows};
+        if (dt == FRPCA_F32)
+            e = launch_typed<float>(pc.virt, (const float *)pc.virt.vals, w, l, (const float *)X, ldx, (float *)Y,
+                                    ldy, (float *)scratch, true, s);
+        else
+            e = launch_typed<double>(pc.virt, (const double *)pc.virt.vals, w, l, (const double *)X, ldx,
+                                     (double *)Y, ldy, (double *)scratch, true, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void PanelCSR::free_all() {
+    plan.free_all();
+    for (DevBuf *b : {&b_rowptr, &b_colidx, &b_vals, &b_perm}) b->release();
+    npanels = 0;
+    short_off.clear();
+    long_off.clear();
+    seg_off.clear();
 }
 
 size_t spmm_scratch_bytes(const SpmmPlan &plan, int l, frpca_dtype dt) {
@@ -361,10 +496,11 @@ size_t spmm_scratch_bytes(const SpmmPlan &plan, int l, frpca_dtype dt) {
 cudaError_t launch_spmm(const DeviceCSR &A, const void *vals, const SpmmPlan &plan, int l, const void *X,
                         int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *scratch, cudaStream_t s,
                         bool accumulate) {
+    const SpmmWork w = whole_plan(plan);
     if (dt == FRPCA_F32)
-        return launch_typed<float>(A, (const float *)vals, plan, l, (const float *)X, ldx, (float *)Y, ldy,
+        return launch_typed<float>(A, (const float *)vals, w, l, (const float *)X, ldx, (float *)Y, ldy,
                                    (float *)scratch, accumulate, s);
-    return launch_typed<double>(A, (const double *)vals, plan, l, (const double *)X, ldx, (double *)Y, ldy,
+    return launch_typed<double>(A, (const double *)vals, w, l, (const double *)X, ldx, (double *)Y, ldy,
                                 (double *)scratch, accumulate, s);
 }
 

@@ -432,6 +432,25 @@ cudaError_t sort_structure(const DeviceCSR &A, DeviceCSR &AT, int32_t *perm, Dev
     return cudaGetLastError();
 }
 
+// Panel index of every entry (its column of C divided by the panel height).
+__global__ void panel_keys_kernel(const int32_t *__restrict__ colidx, int64_t nnz, int64_t P,
+                                  uint32_t *__restrict__ keys) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        keys[p] = (uint32_t)(colidx[p] / P);
+}
+
+// After the stable sort by panel: the virtual row b * rows + j of every entry
+// (b its panel, j its row of C) and the entry of A it came from.
+__global__ void panel_vkeys_kernel(const uint32_t *__restrict__ bkeys, const int32_t *__restrict__ ids,
+                                   const int32_t *__restrict__ row_of, const int32_t *__restrict__ mapC, int64_t nnz,
+                                   int64_t rows, uint32_t *__restrict__ vkeys, int32_t *__restrict__ permP) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = ids[q];
+        vkeys[q] = (uint32_t)((int64_t)bkeys[q] * rows + row_of[p]);
+        permP[q] = mapC ? mapC[p] : p;
+    }
+}
+
 }  // namespace
 
 cudaError_t csr_transpose_values(const DeviceCSR &A, DeviceCSR &AT, const int32_t *perm, cudaStream_t s) {
@@ -529,6 +548,98 @@ void DevBuf::release() {
     dev_free(ptr, stream, budget, bytes);
     ptr = nullptr;
     bytes = 0;
+}
+
+cudaError_t build_panel_csr(const DeviceCSR &C, const int32_t *mapC, int64_t P, PanelCSR &pc, DevBuf &scratch,
+                            DevBuf &scan_scratch, cudaStream_t s) {
+    const int64_t nnz = C.nnz;
+    pc.panel_rows = P;
+    pc.npanels = ceil_div(C.cols, P);
+    pc.src_rows = C.rows;
+    const int64_t vrows = pc.npanels * C.rows;
+    if (P < 1 || vrows >= ((int64_t)1 << 31) || nnz == 0) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = pc.b_rowptr.ensure(8 * (size_t)(vrows + 1))) != cudaSuccess ||
+        (e = pc.b_colidx.ensure(4 * (size_t)nnz)) != cudaSuccess ||
+        (e = pc.b_vals.ensure((C.dtype == FRPCA_F32 ? 4 : 8) * (size_t)nnz)) != cudaSuccess ||
+        (e = pc.b_perm.ensure(4 * (size_t)nnz)) != cudaSuccess)
+        return e;
+    pc.virt.rows = vrows;
+    pc.virt.cols = C.cols;
+    pc.virt.nnz = nnz;
+    pc.virt.dtype = C.dtype;
+    pc.virt.rowptr = (int64_t *)pc.b_rowptr.ptr;
+    pc.virt.colidx = (int32_t *)pc.b_colidx.ptr;
+    pc.virt.vals = pc.b_vals.ptr;
+
+    const int64_t ntiles = ceil_div(nnz, kSortTile);
+    const size_t cnt_bytes = sizeof(int32_t) * (size_t)round_up(kRadix * ntiles, 64);
+    const size_t off_bytes = sizeof(int64_t) * (size_t)round_up(kRadix * ntiles + 1, 64);
+    const size_t i32_bytes = sizeof(int32_t) * (size_t)round_up(nnz, 64);
+    if ((e = scratch.ensure(cnt_bytes + off_bytes + 8 * i32_bytes)) != cudaSuccess) return e;
+    char *p = (char *)scratch.ptr;
+    int32_t *counts = (int32_t *)p; p += cnt_bytes;
+    int64_t *offs = (int64_t *)p; p += off_bytes;
+    uint32_t *keys0 = (uint32_t *)p; p += i32_bytes;
+    uint32_t *keys[2] = {(uint32_t *)p, (uint32_t *)(p + i32_bytes)}; p += 2 * i32_bytes;
+    int32_t *rows[2] = {(int32_t *)p, (int32_t *)(p + i32_bytes)}; p += 2 * i32_bytes;
+    int32_t *row_of = (int32_t *)p; p += i32_bytes;
+    int32_t *ids[2] = {(int32_t *)p, (int32_t *)(p + i32_bytes)};
+
+    const unsigned g = grid_for(nnz, 256);
+    panel_keys_kernel<<<g, 256, 0, s>>>(C.colidx, nnz, P, keys0);
+    row_of_entry_kernel<<<(unsigned)ceil_div(C.rows * 32, 256), 256, 0, s>>>(C.rows, C.rowptr, row_of);
+    count_launch(2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) < pc.npanels) ++bits;
+    const int passes = (bits + 7) / 8;
+    const size_t smem = (size_t)kSortTile * (sizeof(int32_t) + 8) + sizeof(int32_t) * (kSortWarps + 1) * kRadix;
+    if ((e = cudaFuncSetAttribute(radix_scatter_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    // Stable sort of C's entries (row-major order) by panel: the result is in
+    // (panel, row of C, column) order.  The column (row index of the gathered
+    // block) and the entry's position in C ride along.
+    const uint32_t *kin = keys0;
+    const int32_t *rin = C.colidx;
+    const int32_t *iin = nullptr;  // first pass: the position itself
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        const bool last = pass + 1 == passes;
+        uint32_t *kout = keys[pass & 1];
+        int32_t *rout = last ? pc.virt.colidx : rows[pass & 1];
+        int32_t *iout = ids[pass & 1];
+        radix_hist_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, nnz, shift, ntiles, counts);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = exclusive_scan<int32_t>(counts, offs, kRadix * ntiles, scan_scratch, s)) != cudaSuccess) return e;
+        radix_scatter_kernel<int32_t><<<(unsigned)ntiles, kSortThreads, smem, s>>>(kin, rin, iin, nnz, shift, ntiles,
+                                                                                   offs, kout, rout, iout);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        kin = kout;
+        rin = rout;
+        iin = iout;
+    }
+    // keys0 is free again: it holds the virtual row keys.
+    panel_vkeys_kernel<<<g, 256, 0, s>>>(kin, iin, row_of, mapC, nnz, C.rows, keys0, (int32_t *)pc.b_perm.ptr);
+    rowptr_from_sorted_kernel<<<(unsigned)std::min<int64_t>(ceil_div(nnz + 1, 256), 1 << 20), 256, 0, s>>>(
+        keys0, nnz, vrows, pc.virt.rowptr);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t panel_values(const DeviceCSR &A, PanelCSR &pc, cudaStream_t s) {
+    if (A.nnz == 0) return cudaSuccess;
+    const unsigned g = (unsigned)ceil_div(A.nnz, 256 * kGatherUnroll);
+    const int32_t *perm = (const int32_t *)pc.b_perm.ptr;
+    if (A.dtype == FRPCA_F32)
+        gather_values_kernel<float><<<g, 256, 0, s>>>(perm, (const float *)A.vals, A.nnz, (float *)pc.virt.vals);
+    else
+        gather_values_kernel<double><<<g, 256, 0, s>>>(perm, (const double *)A.vals, A.nnz, (double *)pc.virt.vals);
+    count_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace frpca

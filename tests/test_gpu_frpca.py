@@ -86,6 +86,19 @@ def test_frpca_small(q, prec, shape):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", ["tall", "wide"])
+def test_frpca_panels(prec, shape):
+    """The whole method with the larger block's pass run by panels (250 rows
+    each, so a dozen panels at this size)."""
+    A = SMALL_TALL if shape == "tall" else SMALL_WIDE
+    A = A.astype(np.float64 if prec == "fp64" else np.float32)
+    mat = frpca.FrPCA.from_csr(A, device=DEV, panel_rows=250)
+    for q in (3, 4, 5):
+        _compare(A, 10, 24, q, 7, prec, mat=mat)
+    mat.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_frpca_uniform_2000x1000(prec):
     """The uniform 2,000 x 1,000 workload, k = 10, l = 20, 3 passes, seed 0."""
     w = synthetic.WORKLOADS["uniform_2000x1000_nnz20000"]

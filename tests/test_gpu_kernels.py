@@ -365,3 +365,70 @@ def test_lu_tournament_singular_pivot_reports():
     with pytest.raises(frpca.FrpcaError) as ei:
         _lu_tournament(M)
     assert ei.value.status == 5
+
+
+# ---------------------------------------------------------------- SpMM by panels of the gathered block
+def _panel_bound(A, X, trans, eps):
+    """Sums continue from one panel to the next in the output itself (a float
+    stored and reloaded exactly), so the only roundings beyond the CSR
+    order's d + 2 are the fix-up's additions of the 1,024-entry segments of a
+    long row within a panel: (d + 4 + d / 512) eps (|A| |X|)."""
+    Aabs = synthetic.CSR(A.m, A.n, A.indptr, A.indices, np.abs(A.data.astype(np.float64)))
+    f = oracle.spmm_t if trans else oracle.spmm
+    mag = f(Aabs.m, Aabs.n, Aabs.indptr, Aabs.indices, Aabs.data, np.abs(X))
+    deg = np.diff(A.indptr) if not trans else np.bincount(A.indices, minlength=A.n)
+    return (deg[:, None] + 4 + deg[:, None] // 512) * eps * mag + 1e-300
+
+
+def _wide(A):
+    pT, cT, vT = oracle.csr_transpose(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64))
+    return synthetic.CSR(A.n, A.m, pT, cT, vT)
+
+
+@pytest.mark.parametrize("idx", range(len(MATS)))
+@pytest.mark.parametrize("shape", ["tall", "wide"])
+@pytest.mark.parametrize("panel_rows", [64, 700])
+@pytest.mark.parametrize("l,dtype", [(120, np.float32), (5, np.float32), (48, np.float64)])
+def test_spmm_panels_match_oracle(idx, shape, panel_rows, l, dtype):
+    """The pass that gathers rows of the larger block (A^T X for a tall A, A X
+    for a wide one) run panel by panel: every entry within the summation
+    bound of the oracle's product; the other pass and the A^T values are
+    unaffected."""
+    A = (MATS[idx] if shape == "tall" else _wide(MATS[idx])).astype(dtype)
+    mat = frpca.FrPCA.from_csr(A, device=DEV, panel_rows=panel_rows)
+    trans = 1 if A.m >= A.n else 0
+    rng = np.random.default_rng(l + idx)
+    X = rng.standard_normal((A.m if trans else A.n, l)).astype(dtype)
+    Xg = frpca.empty_block(X.shape[0], l, torch.float64 if dtype == np.float64 else torch.float32, DEV)
+    Xg.copy_(torch.from_numpy(X))
+    Y = _cpu(mat.spmm(Xg, trans=bool(trans)))
+    f = oracle.spmm_t if trans else oracle.spmm
+    ref = f(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64), X.astype(np.float64))
+    eps = EPS64 if dtype == np.float64 else EPS32
+    assert np.all(np.abs(Y - ref) <= _panel_bound(A, X.astype(np.float64), trans, eps))
+    assert torch.equal(mat.spmm(Xg, trans=bool(trans)), mat.spmm(Xg, trans=bool(trans)))
+    pT, cT, vT = mat.transpose()
+    rp, ci, va = oracle.csr_transpose(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64))
+    assert np.array_equal(cT.cpu().numpy(), ci) and np.array_equal(vT.cpu().numpy(), va.astype(dtype))
+    mat.close()
+
+
+def test_spmm_panels_refresh():
+    """After the values change in place, frpca_refresh updates the panel form
+    (and A^T's own values when they are next read)."""
+    A = MATS[1].astype(np.float32)
+    vals = torch.tensor(A.data, device=DEV)
+    mat = frpca.FrPCA(torch.tensor(A.indptr, device=DEV), torch.tensor(A.indices, device=DEV), vals, (A.m, A.n),
+                      panel_rows=1000)
+    X = frpca.empty_block(A.m, 64, torch.float32, DEV)
+    X.copy_(torch.randn(A.m, 64, generator=torch.Generator().manual_seed(0)))
+    Y1 = mat.spmm(X, trans=True).clone()
+    with torch.no_grad():
+        vals.mul_(2.0)
+    mat.refresh()
+    Y2 = mat.spmm(X, trans=True).clone()
+    assert torch.equal(Y2, 2.0 * Y1)  # scaling by 2 is exact
+    _, _, vT = mat.transpose()
+    _, _, va = oracle.csr_transpose(A.m, A.n, A.indptr, A.indices, 2.0 * A.data.astype(np.float64))
+    assert np.array_equal(vT.cpu().numpy(), va.astype(np.float32))
+    mat.close()
