@@ -94,13 +94,29 @@ spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ coli
                 }
             }
         } else {
-            for (int t = 0; t < cnt; ++t) {
-                const int32_t c = __shfl_sync(0xffffffffu, my_col, t);
-                const T v = __shfl_sync(0xffffffffu, my_val, t);
+            // A partial chunk, still eight gathers in flight at a time: the
+            // entries past cnt are skipped (their loads are not issued), and
+            // the valid ones are added in CSR order.
+            for (int t0 = 0; t0 < cnt; t0 += 8) {
+                int32_t c[8];
+                T v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    c[u] = __shfl_sync(0xffffffffu, my_col, (t0 + u) & 31);
+                    v[u] = __shfl_sync(0xffffffffu, my_val, (t0 + u) & 31);
+                }
 #pragma unroll
                 for (int k = 0; k < NV; ++k) {
                     const int vi = lane + 32 * k;
-                    if (vi < nvec) Vec<T>::fma(acc[k], v, __ldg(Xv + (int64_t)c * ldxv + vi));
+                    if (vi < nvec) {
+                        V x[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            x[u] = (t0 + u < cnt) ? __ldg(Xv + (int64_t)c[u] * ldxv + vi) : Vec<T>::zero();
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            if (t0 + u < cnt) Vec<T>::fma(acc[k], v[u], x[u]);
+                    }
                 }
             }
         }
