@@ -130,125 +130,6 @@ spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ coli
 
 // partial holds the segments seg_base, seg_base + 1, ... (long_first values
 // are absolute segment indices); output row = long row - out_row_offset.
-// Eight gathers in flight: the entries t0 .. t0 + 7 of the current 32-entry
-// chunk (held one per lane in col / val), added in CSR order; entries at or
-// past cnt are skipped.
-template <typename T, int NV>
-__device__ inline void gather_chunk(typename Vec<T>::type (&acc)[NV], int32_t col, T val, int cnt, int lane, int nvec,
-                                    const typename Vec<T>::type *__restrict__ Xv, int64_t ldxv) {
-    using V = typename Vec<T>::type;
-    for (int t0 = 0; t0 < cnt; t0 += 8) {
-        int32_t c[8];
-        T v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            c[u] = __shfl_sync(0xffffffffu, col, (t0 + u) & 31);
-            v[u] = __shfl_sync(0xffffffffu, val, (t0 + u) & 31);
-        }
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            const int vi = lane + 32 * k;
-            if (vi < nvec) {
-                V x[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    x[u] = (t0 + u < cnt) ? __ldg(Xv + (int64_t)c[u] * ldxv + vi) : Vec<T>::zero();
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (t0 + u < cnt) Vec<T>::fma(acc[k], v[u], x[u]);
-            }
-        }
-    }
-}
-
-// Whole rows (at most seg entries), kRowGroup consecutive entries of the
-// plan's row list per warp, walked as one sequence of 32-entry chunks: the
-// (column, value) pairs of the next chunk -- of the same row or of the next
-// one -- are loaded while the current chunk's rows of X are gathered, so the
-// index loads leave the critical path.  Each row is still summed by one warp
-// in CSR order (bit-identical with one warp per row).
-constexpr int kRowGroup = 4;
-
-template <typename T, int NV>
-__global__ void __launch_bounds__(kThreads)
-spmm_rows_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, const T *__restrict__ vals,
-                 const int32_t *__restrict__ short_rows, int64_t n_short, int nvec, const T *__restrict__ X,
-                 int64_t ldx, T *__restrict__ Y, int64_t ldy, int accumulate, int64_t out_row_offset) {
-    using V = typename Vec<T>::type;
-    constexpr int W = Vec<T>::width;
-    const int lane = threadIdx.x & 31;
-    const int64_t w = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
-    const int64_t first = w * kRowGroup;
-    if (first >= n_short) return;
-    const int nr = (int)min((int64_t)kRowGroup, n_short - first);
-    // Lane g < nr holds row g of the group, its first entry and its length.
-    int32_t my_row = 0;
-    int64_t my_start = 0;
-    int my_len = 0;
-    if (lane < nr) {
-        my_row = short_rows[first + lane];
-        my_start = rowptr[my_row];
-        my_len = (int)(rowptr[my_row + 1] - my_start);
-    }
-    const V *Xv = reinterpret_cast<const V *>(X);
-    const int64_t ldxv = ldx / W;
-    auto load_pairs = [&](int g, int base, int32_t &c, T &v) {
-        const int64_t st = __shfl_sync(0xffffffffu, my_start, g);
-        const int len = __shfl_sync(0xffffffffu, my_len, g);
-        c = 0;
-        v = T(0);
-        if (base + lane < len) {
-            c = __ldg(colidx + st + base + lane);
-            v = __ldg(vals + st + base + lane);
-        }
-    };
-    auto row_out = [&](int g) {
-        const int32_t row = __shfl_sync(0xffffffffu, my_row, g);
-        return reinterpret_cast<V *>(Y + ((int64_t)row - out_row_offset) * ldy);
-    };
-    auto init_acc = [&](int g, V (&acc)[NV]) {
-        V *out = row_out(g);
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            const int vi = lane + 32 * k;
-            acc[k] = (accumulate && vi < nvec) ? out[vi] : Vec<T>::zero();
-        }
-    };
-    V acc[NV];
-    int g = 0, base = 0;
-    int32_t cur_c;
-    T cur_v;
-    load_pairs(0, 0, cur_c, cur_v);
-    init_acc(0, acc);
-    while (true) {
-        const int len = __shfl_sync(0xffffffffu, my_len, g);
-        const int cnt = min(32, len - base);
-        int g2 = g, base2 = base + 32;
-        if (base2 >= len) {
-            g2 = g + 1;
-            base2 = 0;
-        }
-        int32_t nxt_c = 0;
-        T nxt_v = T(0);
-        if (g2 < nr) load_pairs(g2, base2, nxt_c, nxt_v);
-        if (cnt > 0) gather_chunk<T, NV>(acc, cur_c, cur_v, cnt, lane, nvec, Xv, ldxv);
-        if (g2 != g) {
-            V *out = row_out(g);
-#pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                const int vi = lane + 32 * k;
-                if (vi < nvec) out[vi] = acc[k];
-            }
-            if (g2 >= nr) break;
-            init_acc(g2, acc);
-        }
-        g = g2;
-        base = base2;
-        cur_c = nxt_c;
-        cur_v = nxt_v;
-    }
-}
-
 template <typename T>
 __global__ void spmm_fixup_kernel(int64_t n_long, const int32_t *__restrict__ long_rows,
                                   const int64_t *__restrict__ long_first, int nvec, const T *__restrict__ partial,
@@ -293,22 +174,16 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmWork &p, i
     constexpr int W = Vec<T>::width;
     const int nvec = (int)ceil_div(l, W);
     const int nv = (int)ceil_div(nvec, 32);
-    const int64_t groups = ceil_div(p.n_short, kRowGroup);
-    if (groups > 0 || p.n_segs > 0) {
+    const int64_t warps = p.n_short + p.n_segs;
+    if (warps > 0) {
+        const int64_t blocks = ceil_div(warps * 32, kThreads);
 #define FRPCA_SPMM_CASE(NVV)                                                                                  \
     case NVV:                                                                                                 \
-        if (groups > 0) {                                                                                     \
-            spmm_rows_kernel<T, NVV><<<(unsigned)ceil_div(groups * 32, kThreads), kThreads, 0, s>>>(          \
-                A.rowptr, A.colidx, vals, p.short_rows, p.n_short, nvec, X, ldx, Y, ldy, accumulate,          \
-                p.out_row_offset);                                                                            \
-            count_launch();                                                                                   \
-        }                                                                                                     \
-        if (p.n_segs > 0) {                                                                                   \
-            spmm_kernel<T, NVV><<<(unsigned)ceil_div(p.n_segs * 32, kThreads), kThreads, 0, s>>>(             \
-                A.rowptr, A.colidx, vals, nullptr, 0, p.seg_start, p.seg_len, p.n_segs, nvec, X, ldx, Y, ldy, \
-                partial, accumulate, p.out_row_offset);                                                       \
-            count_launch();                                                                                   \
-        }                                                                                                     \
+        spmm_kernel<T, NVV><<<(unsigned)blocks, kThreads, 0, s>>>(A.rowptr, A.colidx, vals, p.short_rows,     \
+                                                                  p.n_short, p.seg_start, p.seg_len,          \
+                                                                  p.n_segs, nvec, X, ldx, Y, ldy, partial,    \
+                                                                  accumulate, p.out_row_offset);              \
+        count_launch();                                                                                       \
         break;
         switch (nv) {
             FRPCA_SPMM_CASE(1)
