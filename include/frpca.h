@@ -108,6 +108,10 @@ typedef struct frpca_create_opts {
                                  one after the other into the output, so a panel stays in
                                  L2: 0 = automatic (131,072 rows when the block has at least
                                  three times that many), -1 = off, > 0 = that many rows   */
+    int fused_sweep;          /* with panels: 0 = each power-iteration pair of passes
+                                 (A^T (A Q) for Alg. 6) runs as one sweep, panel by panel,
+                                 the intermediate panel of A Q staying in L2 instead of
+                                 being written to and read back from HBM; -1 = two passes */
 } frpca_create_opts;
 
 /* Creates a handle.  csr may be NULL: the handle then serves only the
@@ -174,7 +178,9 @@ typedef struct frpca_stats {
     double gram_ms, eig_ms, apply_ms;
     double gaussian_ms, transpose_ms, finish_ms;
     int64_t spmm_a_passes, spmm_t_passes; /* passes with A and with A^T         */
-    double spmm_a_ms, spmm_t_ms;          /* their device time (sum: spmm_ms)  */
+    double spmm_a_ms, spmm_t_ms;          /* their device time (sum: spmm_ms); a
+                                             fused sweep's time goes to spmm_t_ms */
+    int64_t fused_sweeps;                 /* pass pairs run as one sweep        */
 } frpca_stats;
 
 /* enable != 0 records events around every phase (adds a few microseconds per

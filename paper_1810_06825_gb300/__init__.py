@@ -47,7 +47,8 @@ class frpca_csr(ctypes.Structure):
 
 class frpca_create_opts(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("borrow", ctypes.c_int), ("validate", ctypes.c_int),
-                ("hot_columns", ctypes.c_int), ("max_device_bytes", ctypes.c_int64), ("panel_rows", ctypes.c_int)]
+                ("hot_columns", ctypes.c_int), ("max_device_bytes", ctypes.c_int64), ("panel_rows", ctypes.c_int),
+                ("fused_sweep", ctypes.c_int)]
 
 
 class frpca_run_opts(ctypes.Structure):
@@ -62,7 +63,7 @@ class frpca_stats(ctypes.Structure):
                 ("gram_ms", ctypes.c_double), ("eig_ms", ctypes.c_double), ("apply_ms", ctypes.c_double),
                 ("gaussian_ms", ctypes.c_double), ("transpose_ms", ctypes.c_double), ("finish_ms", ctypes.c_double),
                 ("spmm_a_passes", ctypes.c_int64), ("spmm_t_passes", ctypes.c_int64), ("spmm_a_ms", ctypes.c_double),
-                ("spmm_t_ms", ctypes.c_double)]
+                ("spmm_t_ms", ctypes.c_double), ("fused_sweeps", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -283,11 +284,12 @@ class FrPCA:
     of each pass runs on the tensor cores.  ``max_device_bytes`` caps the
     device memory the handle allocates for itself (0: no cap).  ``panel_rows``:
     the panel height of the pass that gathers rows of the larger dense block
-    (0 automatic, -1 off).
+    (0 automatic, -1 off); ``fused_sweep`` -1 keeps the power iteration's two
+    passes apart instead of one panel-by-panel sweep.
     """
 
     def __init__(self, indptr, indices, values, shape, stream=None, borrow=True, validate=True, hot_columns=0,
-                 max_device_bytes=0, panel_rows=0):
+                 max_device_bytes=0, panel_rows=0, fused_sweep=0):
         torch = _torch()
         _need_cuda(indptr, indices, values)
         if indptr.dtype not in (torch.int64, torch.int32):
@@ -297,10 +299,10 @@ class FrPCA:
         self._setup(self.indptr.data_ptr(), self.indices.data_ptr() if self.indices.numel() else None,
                     self.values.data_ptr() if self.values.numel() else None, int(self.indices.numel()),
                     self.indptr.dtype == torch.int32, self.values.dtype, shape, 1, self.values.device, stream,
-                    borrow, validate, hot_columns, max_device_bytes, panel_rows)
+                    borrow, validate, hot_columns, max_device_bytes, panel_rows, fused_sweep)
 
     def _setup(self, p_indptr, p_indices, p_values, nnz, rp32, dtype, shape, on_device, device, stream, borrow,
-               validate, hot_columns, max_device_bytes, panel_rows=0):
+               validate, hot_columns, max_device_bytes, panel_rows=0, fused_sweep=0):
         torch = _torch()
         self.m, self.n = int(shape[0]), int(shape[1])
         self._nnz = nnz
@@ -312,12 +314,13 @@ class FrPCA:
                         rowptr_type=FRPCA_I32 if rp32 else FRPCA_I64)
         opts = frpca_create_opts(stream=self.stream.cuda_stream, borrow=1 if borrow else 0,
                                  validate=1 if validate else 0, hot_columns=int(hot_columns),
-                                 max_device_bytes=int(max_device_bytes), panel_rows=int(panel_rows))
+                                 max_device_bytes=int(max_device_bytes), panel_rows=int(panel_rows),
+                                 fused_sweep=int(fused_sweep))
         self.handle = frpca_create(csr, opts)
 
     @classmethod
     def from_host(cls, indptr, indices, values, shape, device="cuda", stream=None, validate=True, hot_columns=0,
-                  max_device_bytes=0, panel_rows=0):
+                  max_device_bytes=0, panel_rows=0, fused_sweep=0):
         """From host arrays (numpy or CPU tensors; pinned memory copies fastest):
         the C ABI's own host path (``on_device = 0``) copies them to the
         device and validates them there."""
@@ -342,7 +345,7 @@ class FrPCA:
             self._setup(ip.ctypes.data, ix.ctypes.data if ix.size else None, va.ctypes.data if va.size else None,
                         int(ix.size), ip.dtype == np.int32,
                         torch.float32 if va.dtype == np.float32 else torch.float64, shape, 0, dev, stream,
-                        False, validate, hot_columns, max_device_bytes, panel_rows)
+                        False, validate, hot_columns, max_device_bytes, panel_rows, fused_sweep)
         return self
 
     @classmethod

@@ -32,6 +32,7 @@ struct frpca_ctx {
     PanelCSR pan;  // the pass that gathers rows of the larger block, by panels of those rows
     int pan_trans = 1;           // which pass uses it: 1 = A^T X (m >= n), 0 = A X (m < n)
     bool at_vals_stale = false;  // A^T's values wait for a refresh (the panel pass had its own)
+    bool fused = true;           // the power iteration's pass pairs as one sweep when it applies
     MemBudget budget;                            // frpca_create_opts.max_device_bytes
     long long wait_limit = kBarrierLimitCycles;  // frpca_set_wait_limit
     std::string err;
@@ -232,6 +233,43 @@ frpca_status spmm_pass(frpca_ctx *h, int trans, int l, const void *X, int64_t ld
     return FRPCA_OK;
 }
 
+// M = Bk (F Q) in one sweep (Alg. 6's power-iteration body A^T (A Q); Alg. 5's
+// A (A^T Q)): the rows of F Q are made panel by panel into a two-slot ring at
+// the start of W and gathered from there by the panel form of Bk while still
+// in L2; the result goes to W after the ring and is copied to Q.  Returns
+// false (nothing done) when the sweep does not apply.
+bool fused_sweep_applies(frpca_ctx *h, int64_t rq, int64_t rw, int64_t ld, frpca_dtype dt, int fwd_trans) {
+    return h->pan.active() && !h->pan.prod_short_off.empty() && dt == h->A.dtype && h->pan_trans == 1 - fwd_trans &&
+           rw >= 2 * h->pan.panel_rows + rq && ld > 0;
+}
+
+frpca_status fused_sweep(frpca_ctx *h, int fwd_trans, int l, void *Q, void *W, int64_t ld, int64_t rq,
+                         frpca_dtype dt) {
+    const size_t es = dsize(dt);
+    void *ring = W;
+    void *Z = (char *)W + es * (size_t)(2 * h->pan.panel_rows) * (size_t)ld;
+    const DeviceCSR &F = fwd_trans ? h->AT : h->A;
+    const SpmmPlan &P = fwd_trans ? h->planAT : h->planA;
+    CK(h->ws_spmm.ensure(std::max<size_t>(256, fused_scratch_bytes(h->pan, l, dt))), "alloc spmm scratch");
+    {
+        PhaseTimer t(h, PH_SPMM_T);
+        CK(launch_fused_sweep(F, P, h->pan, l, Q, ld, ring, ld, Z, ld, dt, h->ws_spmm.ptr, h->stream),
+           "fused sweep launch");
+        CK(cudaMemcpyAsync(Q, Z, es * (size_t)rq * (size_t)ld, cudaMemcpyDeviceToDevice, h->stream), "copy sweep");
+    }
+    const double sv = (double)es;
+    for (int trans = 0; trans < 2; ++trans) {
+        const DeviceCSR &C = trans ? h->AT : h->A;
+        h->acc.spmm_passes += 1;
+        (trans ? h->acc.spmm_t_passes : h->acc.spmm_a_passes) += 1;
+        h->acc.spmm_bytes += (double)C.nnz * (sv + 4.0) + (double)(C.rows + 1) * 8.0 +
+                             ((double)C.cols + (double)C.rows) * (double)l * sv;
+        h->acc.spmm_flops += 2.0 * (double)C.nnz * (double)l;
+    }
+    h->acc.fused_sweeps += 1;
+    return FRPCA_OK;
+}
+
 // lu() of Alg. 5/6.  FP64: partial pivoting, reproducible bit for bit.  FP32:
 // tournament pivoting (one grid barrier per 8 columns instead of per column)
 // when a block's rows fit in shared memory, partial pivoting otherwise; both
@@ -385,9 +423,14 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
     // of A^T A Q (about 1e4 here) to that of the unit-lower factor (about 1e2),
     // which float storage of the block can carry.
     const int loops = (q - 1) / 2;
+    const bool fused = h->fused && fused_sweep_applies(h, rq, rw, ld, dt, fwd_trans);
     for (int i = 1; i <= loops; ++i) {
-        if ((st = spmm_pass(h, fwd_trans, l, Q, ld, W, ld, dt)) != FRPCA_OK) return st;
-        if ((st = spmm_pass(h, bwd_trans, l, W, ld, Q, ld, dt)) != FRPCA_OK) return st;
+        if (fused) {
+            if ((st = fused_sweep(h, fwd_trans, l, Q, W, ld, rq, dt)) != FRPCA_OK) return st;
+        } else {
+            if ((st = spmm_pass(h, fwd_trans, l, Q, ld, W, ld, dt)) != FRPCA_OK) return st;
+            if ((st = spmm_pass(h, bwd_trans, l, W, ld, Q, ld, dt)) != FRPCA_OK) return st;
+        }
         if (i < loops || dt == FRPCA_F32) {
             if ((st = lu_step(h, rq, l, Q, ld, dt, nullptr)) != FRPCA_OK) return st;
         }
@@ -551,6 +594,7 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
         const int64_t big = std::max(m, n);
         const int pr = opts ? opts->panel_rows : 0;
         const int64_t P = pr > 0 ? (int64_t)pr : (int64_t)131072;
+        h->fused = opts ? opts->fused_sweep >= 0 : true;
         h->pan_trans = m >= n ? 1 : 0;
         const DeviceCSR &C = m >= n ? h->AT : h->A;
         const bool want = pr > 0 ? big > P : (pr == 0 && big >= 3 * P);
@@ -565,6 +609,8 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
                 (e = panel_values(h->A, h->pan, h->stream)) != cudaSuccess)
                 return bail(cuda_fail(h, e, "panel form"));
             if ((e = build_panel_plan(h->pan, h->ws_plan, h->ws_scan, h->stream, perr)) != cudaSuccess)
+                return bail(cuda_fail(h, e, perr.c_str()));
+            if ((e = build_fused_offsets(h->pan, m >= n ? h->planA : h->planAT, h->stream, perr)) != cudaSuccess)
                 return bail(cuda_fail(h, e, perr.c_str()));
         }
     }

@@ -79,7 +79,8 @@ struct DevBuf {
 // The gathering pass reorganized by panels of the gathered block: C's entries
 // (C = A or A^T, whichever gathers rows of the larger dense block) stably
 // sorted by (panel of their column, row of C), as a CSR over the virtual rows
-// b * src_rows + j (row j of C restricted to panel b, columns b P .. b P + P-1).
+// b * src_rows + j (row j of C restricted to panel b, columns b P .. b P + P-1,
+// stored as offsets 0 .. P-1 from the panel's first row).
 // A pass runs one panel after the other into the zeroed output, each panel's
 // rows accumulating onto the previous panels' sums, so the panel of the
 // gathered block a launch reads stays resident in L2.
@@ -93,6 +94,11 @@ struct PanelCSR {
     // first segment of the plan that belong to panel b
     std::vector<int64_t> short_off, long_off, seg_off;
     int64_t max_panel_segs = 0;
+    // The same per-panel offsets into the plan of the product that writes the
+    // gathered block (A X for A^T panels, rows b P .. b P + P-1 of panel b),
+    // for the fused sweep; empty when not built.
+    std::vector<int64_t> prod_short_off, prod_long_off, prod_seg_off;
+    int64_t prod_max_segs = 0;
     DevBuf b_rowptr, b_colidx, b_vals, b_perm;  // perm: entry of A at each position of virt
     bool active() const { return npanels > 0; }
     void free_all();
@@ -143,6 +149,18 @@ size_t panel_scratch_bytes(const PanelCSR &pc, int l, frpca_dtype dt);
 // Y (src_rows x l) = C X, panel by panel (Y is zeroed first).
 cudaError_t launch_spmm_panels(const PanelCSR &pc, int l, const void *X, int64_t ldx, void *Y, int64_t ldy,
                                frpca_dtype dt, void *scratch, cudaStream_t s);
+// Per-panel offsets of the plan of the producing product (the CSR P whose
+// rows are the rows of the gathered block; plan including empty rows).
+cudaError_t build_fused_offsets(PanelCSR &pc, const SpmmPlan &prod, cudaStream_t s, std::string &err);
+// The fused sweep Z = C (P Q) (Alg. 6's power-iteration body A^T (A Q) with
+// C = A^T, P = A): for each panel b, the rows b P .. b P + P-1 of P Q go to a
+// slot of `ring` (2 slots of panel_rows x ldr) and are gathered from there by
+// panel b of C while still in L2; the m x l intermediate is never written in
+// full.  Z (src_rows x l, ldz) must not overlap Q or ring.
+size_t fused_scratch_bytes(const PanelCSR &pc, int l, frpca_dtype dt);
+cudaError_t launch_fused_sweep(const DeviceCSR &Pm, const SpmmPlan &prod, const PanelCSR &pc, int l, const void *Q,
+                               int64_t ldq, void *ring, int64_t ldr, void *Z, int64_t ldz, frpca_dtype dt,
+                               void *scratch, cudaStream_t s);
 size_t spmm_scratch_bytes(const SpmmPlan &plan, int l, frpca_dtype dt);
 cudaError_t launch_spmm(const DeviceCSR &A, const void *vals, const SpmmPlan &plan, int l, const void *X,
                         int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *scratch, cudaStream_t s, bool accumulate = false);

@@ -24,9 +24,14 @@ namespace {
 // warps resident (0.602 vs 0.650 ms per pass with 8-warp blocks).
 constexpr int kThreads = 64;
 constexpr int kDefaultSeg = 1024;
+// Blocks per SM the register allocation is sized for (occupancy of a
+// latency-bound gather loop).
+#ifndef FRPCA_SPMM_MIN_BLOCKS
+#define FRPCA_SPMM_MIN_BLOCKS 1
+#endif
 
 template <typename T, int NV>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, FRPCA_SPMM_MIN_BLOCKS)
 spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, const T *__restrict__ vals,
             const int32_t *__restrict__ short_rows, int64_t n_short, const int64_t *__restrict__ seg_start,
             const int32_t *__restrict__ seg_len, int64_t n_segs, int nvec, const T *__restrict__ X, int64_t ldx,
@@ -317,13 +322,13 @@ __global__ void plan_fill_kernel(int64_t m, const int64_t *__restrict__ rowptr, 
 }
 
 // First entry of each panel in the plan's sorted row lists: short rows and
-// long rows of panel b are those with virtual row in [b rows, (b + 1) rows).
-__global__ void panel_offsets_kernel(int64_t npanels, int64_t rows, const int32_t *__restrict__ short_rows,
+// long rows of panel b are those with row in [b stride, (b + 1) stride).
+__global__ void panel_offsets_kernel(int64_t npanels, int64_t stride, const int32_t *__restrict__ short_rows,
                                      int64_t n_short, const int32_t *__restrict__ long_rows, int64_t n_long,
                                      const int64_t *__restrict__ long_first, int64_t *__restrict__ out) {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b > npanels) return;
-    const int64_t key = b * rows;
+    const int64_t key = b * stride;
     int64_t lo = 0, hi = n_short;
     while (lo < hi) {
         const int64_t mid = (lo + hi) / 2;
@@ -430,39 +435,59 @@ cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *cons
     return cudaSuccess;
 }
 
+// Per panel b (npanels + 1 entries each, copied to the host): first short row,
+// first long row and first segment of `plan` whose row is >= b stride.
+cudaError_t plan_panel_offsets(const SpmmPlan &plan, int64_t npanels, int64_t stride, std::vector<int64_t> &so,
+                               std::vector<int64_t> &lo, std::vector<int64_t> &go, cudaStream_t s) {
+    const int64_t np1 = npanels + 1;
+    DevBuf offs;
+    offs.stream = s;
+    cudaError_t e = offs.ensure(sizeof(int64_t) * 3 * (size_t)np1);
+    if (e != cudaSuccess) return e;
+    panel_offsets_kernel<<<(unsigned)ceil_div(np1, 128), 128, 0, s>>>(npanels, stride, plan.short_rows, plan.n_short,
+                                                                     plan.long_rows, plan.n_long, plan.long_first,
+                                                                     (int64_t *)offs.ptr);
+    count_launch();
+    std::vector<int64_t> h(3 * (size_t)np1);
+    if ((e = cudaGetLastError()) == cudaSuccess &&
+        (e = cudaMemcpyAsync(h.data(), offs.ptr, sizeof(int64_t) * h.size(), cudaMemcpyDeviceToHost, s)) ==
+            cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    offs.release();
+    if (e != cudaSuccess) return e;
+    so.assign(h.begin(), h.begin() + np1);
+    lo.assign(h.begin() + np1, h.begin() + 2 * np1);
+    go.assign(h.begin() + 2 * np1, h.end());
+    return cudaSuccess;
+}
+
 cudaError_t build_panel_plan(PanelCSR &pc, DevBuf &scratch, DevBuf &scan_scratch, cudaStream_t s, std::string &err) {
     pc.plan.skip_empty = true;
     const DeviceCSR *mats[1] = {&pc.virt};
     SpmmPlan *plans[1] = {&pc.plan};
     cudaError_t e = build_spmm_plans_device(mats, plans, 1, scratch, scan_scratch, s, err);
     if (e != cudaSuccess) return e;
-    const int64_t np1 = pc.npanels + 1;
-    DevBuf offs;
-    offs.stream = s;
-    if ((e = offs.ensure(sizeof(int64_t) * 3 * (size_t)np1)) != cudaSuccess) {
-        err = "spmm plan: scratch allocation failed";
-        return e;
-    }
-    panel_offsets_kernel<<<(unsigned)ceil_div(np1, 128), 128, 0, s>>>(
-        pc.npanels, pc.src_rows, pc.plan.short_rows, pc.plan.n_short, pc.plan.long_rows, pc.plan.n_long,
-        pc.plan.long_first, (int64_t *)offs.ptr);
-    count_launch();
-    std::vector<int64_t> h(3 * (size_t)np1);
-    if ((e = cudaGetLastError()) != cudaSuccess ||
-        (e = cudaMemcpyAsync(h.data(), offs.ptr, sizeof(int64_t) * h.size(), cudaMemcpyDeviceToHost, s)) !=
-            cudaSuccess ||
-        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
-        offs.release();
+    if ((e = plan_panel_offsets(pc.plan, pc.npanels, pc.src_rows, pc.short_off, pc.long_off, pc.seg_off, s)) !=
+        cudaSuccess) {
         err = "spmm plan: panel offsets failed";
         return e;
     }
-    offs.release();
-    pc.short_off.assign(h.begin(), h.begin() + np1);
-    pc.long_off.assign(h.begin() + np1, h.begin() + 2 * np1);
-    pc.seg_off.assign(h.begin() + 2 * np1, h.end());
     pc.max_panel_segs = 0;
     for (int64_t b = 0; b < pc.npanels; ++b)
         pc.max_panel_segs = std::max(pc.max_panel_segs, pc.seg_off[b + 1] - pc.seg_off[b]);
+    return cudaSuccess;
+}
+
+cudaError_t build_fused_offsets(PanelCSR &pc, const SpmmPlan &prod, cudaStream_t s, std::string &err) {
+    cudaError_t e = plan_panel_offsets(prod, pc.npanels, pc.panel_rows, pc.prod_short_off, pc.prod_long_off,
+                                       pc.prod_seg_off, s);
+    if (e != cudaSuccess) {
+        err = "spmm plan: fused offsets failed";
+        return e;
+    }
+    pc.prod_max_segs = 0;
+    for (int64_t b = 0; b < pc.npanels; ++b)
+        pc.prod_max_segs = std::max(pc.prod_max_segs, pc.prod_seg_off[b + 1] - pc.prod_seg_off[b]);
     return cudaSuccess;
 }
 
@@ -471,26 +496,69 @@ size_t panel_scratch_bytes(const PanelCSR &pc, int l, frpca_dtype dt) {
     return (size_t)pc.max_panel_segs * (size_t)ceil_div(l, W) * 16;
 }
 
+namespace {
+
+// Panel b of C times the panel of X that starts at Xb (row b P of X), added
+// onto Y.
+cudaError_t panel_launch(const PanelCSR &pc, int64_t b, int l, const void *Xb, int64_t ldx, void *Y, int64_t ldy,
+                         frpca_dtype dt, void *scratch, cudaStream_t s) {
+    const SpmmPlan &p = pc.plan;
+    const int64_t s0 = pc.short_off[b], s1 = pc.short_off[b + 1];
+    const int64_t l0 = pc.long_off[b], l1 = pc.long_off[b + 1];
+    const int64_t g0 = pc.seg_off[b], g1 = pc.seg_off[b + 1];
+    if (s1 == s0 && l1 == l0) return cudaSuccess;
+    const SpmmWork w{p.short_rows + s0, s1 - s0, p.seg_start + g0, p.seg_len + g0, g1 - g0, g0,
+                     p.long_rows + l0, p.long_first + l0, l1 - l0, b * pc.src_rows};
+    if (dt == FRPCA_F32)
+        return launch_typed<float>(pc.virt, (const float *)pc.virt.vals, w, l, (const float *)Xb, ldx, (float *)Y,
+                                   ldy, (float *)scratch, true, s);
+    return launch_typed<double>(pc.virt, (const double *)pc.virt.vals, w, l, (const double *)Xb, ldx, (double *)Y,
+                                ldy, (double *)scratch, true, s);
+}
+
+}  // namespace
+
 cudaError_t launch_spmm_panels(const PanelCSR &pc, int l, const void *X, int64_t ldx, void *Y, int64_t ldy,
                                frpca_dtype dt, void *scratch, cudaStream_t s) {
     const size_t es = dt == FRPCA_F32 ? 4 : 8;
     cudaError_t e = cudaMemsetAsync(Y, 0, es * (size_t)pc.src_rows * (size_t)ldy, s);
     if (e != cudaSuccess) return e;
     for (int64_t b = 0; b < pc.npanels; ++b) {
-        const SpmmPlan &p = pc.plan;
-        const int64_t s0 = pc.short_off[b], s1 = pc.short_off[b + 1];
-        const int64_t l0 = pc.long_off[b], l1 = pc.long_off[b + 1];
-        const int64_t g0 = pc.seg_off[b], g1 = pc.seg_off[b + 1];
-        if (s1 == s0 && l1 == l0) continue;
-        const SpmmWork w{p.short_rows + s0, s1 - s0, p.seg_start + g0, p.seg_len + g0, g1 - g0, g0,
-                         p.long_rows + l0, p.long_first + l0, l1 - l0, b * pc.src_rows};
+        const void *Xb = (const char *)X + es * (size_t)(b * pc.panel_rows) * (size_t)ldx;
+        if ((e = panel_launch(pc, b, l, Xb, ldx, Y, ldy, dt, scratch, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+size_t fused_scratch_bytes(const PanelCSR &pc, int l, frpca_dtype dt) {
+    const int W = dt == FRPCA_F32 ? 4 : 2;
+    return (size_t)std::max(pc.max_panel_segs, pc.prod_max_segs) * (size_t)ceil_div(l, W) * 16;
+}
+
+cudaError_t launch_fused_sweep(const DeviceCSR &Pm, const SpmmPlan &prod, const PanelCSR &pc, int l, const void *Q,
+                               int64_t ldq, void *ring, int64_t ldr, void *Z, int64_t ldz, frpca_dtype dt,
+                               void *scratch, cudaStream_t s) {
+    const size_t es = dt == FRPCA_F32 ? 4 : 8;
+    cudaError_t e = cudaMemsetAsync(Z, 0, es * (size_t)pc.src_rows * (size_t)ldz, s);
+    if (e != cudaSuccess) return e;
+    for (int64_t b = 0; b < pc.npanels; ++b) {
+        void *slot = (char *)ring + es * (size_t)((b & 1) * pc.panel_rows) * (size_t)ldr;
+        // Rows b P .. b P + P-1 of P Q into the slot (every row written: the
+        // producing plan keeps empty rows).
+        const int64_t s0 = pc.prod_short_off[b], s1 = pc.prod_short_off[b + 1];
+        const int64_t l0 = pc.prod_long_off[b], l1 = pc.prod_long_off[b + 1];
+        const int64_t g0 = pc.prod_seg_off[b], g1 = pc.prod_seg_off[b + 1];
+        const SpmmWork w{prod.short_rows + s0, s1 - s0, prod.seg_start + g0, prod.seg_len + g0, g1 - g0, g0,
+                         prod.long_rows + l0, prod.long_first + l0, l1 - l0, b * pc.panel_rows};
         if (dt == FRPCA_F32)
-            e = launch_typed<float>(pc.virt, (const float *)pc.virt.vals, w, l, (const float *)X, ldx, (float *)Y,
-                                    ldy, (float *)scratch, true, s);
+            e = launch_typed<float>(Pm, (const float *)Pm.vals, w, l, (const float *)Q, ldq, (float *)slot, ldr,
+                                    (float *)scratch, false, s);
         else
-            e = launch_typed<double>(pc.virt, (const double *)pc.virt.vals, w, l, (const double *)X, ldx,
-                                     (double *)Y, ldy, (double *)scratch, true, s);
+            e = launch_typed<double>(Pm, (const double *)Pm.vals, w, l, (const double *)Q, ldq, (double *)slot, ldr,
+                                     (double *)scratch, false, s);
         if (e != cudaSuccess) return e;
+        // Panel b of C gathers the slot while it is in L2.
+        if ((e = panel_launch(pc, b, l, slot, ldr, Z, ldz, dt, scratch, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

@@ -440,13 +440,17 @@ __global__ void panel_keys_kernel(const int32_t *__restrict__ colidx, int64_t nn
 }
 
 // After the stable sort by panel: the virtual row b * rows + j of every entry
-// (b its panel, j its row of C) and the entry of A it came from.
+// (b its panel, j its row of C), its column made local to the panel
+// (column - b P), and the entry of A it came from.
 __global__ void panel_vkeys_kernel(const uint32_t *__restrict__ bkeys, const int32_t *__restrict__ ids,
                                    const int32_t *__restrict__ row_of, const int32_t *__restrict__ mapC, int64_t nnz,
-                                   int64_t rows, uint32_t *__restrict__ vkeys, int32_t *__restrict__ permP) {
+                                   int64_t rows, int64_t P, uint32_t *__restrict__ vkeys, int32_t *__restrict__ cols,
+                                   int32_t *__restrict__ permP) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p = ids[q];
-        vkeys[q] = (uint32_t)((int64_t)bkeys[q] * rows + row_of[p]);
+        const int64_t b = bkeys[q];
+        vkeys[q] = (uint32_t)(b * rows + row_of[p]);
+        cols[q] = (int32_t)(cols[q] - b * P);
         permP[q] = mapC ? mapC[p] : p;
     }
 }
@@ -565,7 +569,7 @@ cudaError_t build_panel_csr(const DeviceCSR &C, const int32_t *mapC, int64_t P, 
         (e = pc.b_perm.ensure(4 * (size_t)nnz)) != cudaSuccess)
         return e;
     pc.virt.rows = vrows;
-    pc.virt.cols = C.cols;
+    pc.virt.cols = P;  // columns are local to their panel
     pc.virt.nnz = nnz;
     pc.virt.dtype = C.dtype;
     pc.virt.rowptr = (int64_t *)pc.b_rowptr.ptr;
@@ -623,7 +627,8 @@ cudaError_t build_panel_csr(const DeviceCSR &C, const int32_t *mapC, int64_t P, 
         iin = iout;
     }
     // keys0 is free again: it holds the virtual row keys.
-    panel_vkeys_kernel<<<g, 256, 0, s>>>(kin, iin, row_of, mapC, nnz, C.rows, keys0, (int32_t *)pc.b_perm.ptr);
+    panel_vkeys_kernel<<<g, 256, 0, s>>>(kin, iin, row_of, mapC, nnz, C.rows, P, keys0, pc.virt.colidx,
+                                         (int32_t *)pc.b_perm.ptr);
     rowptr_from_sorted_kernel<<<(unsigned)std::min<int64_t>(ceil_div(nnz + 1, 256), 1 << 20), 256, 0, s>>>(
         keys0, nnz, vrows, pc.virt.rowptr);
     count_launch(2);

@@ -99,6 +99,27 @@ def test_frpca_panels(prec, shape):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", ["tall", "wide"])
+def test_fused_sweep_matches_two_passes(prec, shape):
+    """Alg. 6's loop body M = A^T (A Q) (Alg. 5: A (A^T Q)) as one sweep: panel b of A Q is made into an L2-resident slot and gathered from
+    there at once.  Every row is formed by the same kernel in the same order
+    as in the two-pass form, so U, S and V agree bit for bit."""
+    A = SMALL_TALL if shape == "tall" else SMALL_WIDE
+    A = A.astype(np.float64 if prec == "fp64" else np.float32)
+    m1 = frpca.FrPCA.from_csr(A, device=DEV, panel_rows=250)
+    m2 = frpca.FrPCA.from_csr(A, device=DEV, panel_rows=250, fused_sweep=-1)
+    for q in (3, 5, 6):
+        m1.reset_stats()
+        r1 = [t.clone() for t in m1.run(10, 24, q, seed=5, precision=prec)]
+        r2 = [t.clone() for t in m2.run(10, 24, q, seed=5, precision=prec)]
+        for a, b in zip(r1, r2):
+            assert torch.equal(a, b)
+        assert m1.stats()["fused_sweeps"] == (q - 1) // 2
+    m1.close()
+    m2.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_frpca_uniform_2000x1000(prec):
     """The uniform 2,000 x 1,000 workload, k = 10, l = 20, 3 passes, seed 0."""
     w = synthetic.WORKLOADS["uniform_2000x1000_nnz20000"]
