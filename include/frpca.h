@@ -108,10 +108,12 @@ typedef struct frpca_create_opts {
                                  one after the other into the output, so a panel stays in
                                  L2: 0 = automatic (131,072 rows when the block has at least
                                  three times that many), -1 = off, > 0 = that many rows   */
-    int fused_sweep;          /* with panels: 0 = each power-iteration pair of passes
+    int fused_sweep;          /* with panels: 1 = each power-iteration pair of passes
                                  (A^T (A Q) for Alg. 6) runs as one sweep, panel by panel,
                                  the intermediate panel of A Q staying in L2 instead of
-                                 being written to and read back from HBM; -1 = two passes */
+                                 being written to and read back from HBM; 0 = two passes
+                                 (the default: on the 12M x 320K workload the sweep took
+                                 60 ms against 48 ms for the two passes)                   */
 } frpca_create_opts;
 
 /* Creates a handle.  csr may be NULL: the handle then serves only the

@@ -284,8 +284,8 @@ class FrPCA:
     of each pass runs on the tensor cores.  ``max_device_bytes`` caps the
     device memory the handle allocates for itself (0: no cap).  ``panel_rows``:
     the panel height of the pass that gathers rows of the larger dense block
-    (0 automatic, -1 off); ``fused_sweep`` -1 keeps the power iteration's two
-    passes apart instead of one panel-by-panel sweep.
+    (0 automatic, -1 off); ``fused_sweep`` 1 runs each power-iteration pair of
+    passes as one panel-by-panel sweep (0: two passes).
     """
 
     def __init__(self, indptr, indices, values, shape, stream=None, borrow=True, validate=True, hot_columns=0,

@@ -32,7 +32,7 @@ struct frpca_ctx {
     PanelCSR pan;  // the pass that gathers rows of the larger block, by panels of those rows
     int pan_trans = 1;           // which pass uses it: 1 = A^T X (m >= n), 0 = A X (m < n)
     bool at_vals_stale = false;  // A^T's values wait for a refresh (the panel pass had its own)
-    bool fused = true;           // the power iteration's pass pairs as one sweep when it applies
+    bool fused = false;          // the power iteration's pass pairs as one sweep when it applies
     MemBudget budget;                            // frpca_create_opts.max_device_bytes
     long long wait_limit = kBarrierLimitCycles;  // frpca_set_wait_limit
     std::string err;
@@ -594,7 +594,7 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
         const int64_t big = std::max(m, n);
         const int pr = opts ? opts->panel_rows : 0;
         const int64_t P = pr > 0 ? (int64_t)pr : (int64_t)131072;
-        h->fused = opts ? opts->fused_sweep >= 0 : true;
+        h->fused = opts && opts->fused_sweep > 0;
         h->pan_trans = m >= n ? 1 : 0;
         const DeviceCSR &C = m >= n ? h->AT : h->A;
         const bool want = pr > 0 ? big > P : (pr == 0 && big >= 3 * P);

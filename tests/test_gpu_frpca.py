@@ -92,7 +92,7 @@ def test_frpca_panels(prec, shape):
     each, so a dozen panels at this size)."""
     A = SMALL_TALL if shape == "tall" else SMALL_WIDE
     A = A.astype(np.float64 if prec == "fp64" else np.float32)
-    mat = frpca.FrPCA.from_csr(A, device=DEV, panel_rows=250)
+    mat = frpca.FrPCA.from_csr(A, device=DEV, panel_rows=250, fused_sweep=1)
     for q in (3, 4, 5):
         _compare(A, 10, 24, q, 7, prec, mat=mat)
     mat.close()
@@ -106,8 +106,8 @@ def test_fused_sweep_matches_two_passes(prec, shape):
     as in the two-pass form, so U, S and V agree bit for bit."""
     A = SMALL_TALL if shape == "tall" else SMALL_WIDE
     A = A.astype(np.float64 if prec == "fp64" else np.float32)
-    m1 = frpca.FrPCA.from_csr(A, device=DEV, panel_rows=250)
-    m2 = frpca.FrPCA.from_csr(A, device=DEV, panel_rows=250, fused_sweep=-1)
+    m1 = frpca.FrPCA.from_csr(A, device=DEV, panel_rows=250, fused_sweep=1)
+    m2 = frpca.FrPCA.from_csr(A, device=DEV, panel_rows=250)
     for q in (3, 5, 6):
         m1.reset_stats()
         r1 = [t.clone() for t in m1.run(10, 24, q, seed=5, precision=prec)]
