@@ -73,10 +73,8 @@ spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ coli
         int32_t my_col = 0;
         T my_val = T(0);
         if (lane < cnt) {
-            // The CSR arrays are read once per pass: streaming loads, so they
-            // do not push the gathered block's rows out of L2.
-            my_col = __ldcs(colidx + start + base + lane);
-            my_val = __ldcs(vals + start + base + lane);
+            my_col = __ldg(colidx + start + base + lane);
+            my_val = __ldg(vals + start + base + lane);
         }
         if (cnt == 32) {
 #pragma unroll
