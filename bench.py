@@ -361,6 +361,51 @@ def _side_workload(dev, stream, args, peak, peak_kind, with_ref: bool) -> dict:
     return out
 
 
+SHAPE_WORKLOADS = ("powerlaw_647789x323896_deg16", "powerlaw_647789x107966_cols", "powerlaw_107966x323896_rows")
+
+
+def _shape_rule(dev, stream) -> dict:
+    """The shape comparison of Table 3 on its stand-ins: device time per step
+    (A^T rebuild + run, FP32, k = 100, s = 5, q = 11) of Alg. 5 and of Alg. 6
+    forced on each matrix.  Sec. 3.3 predicts Alg. 5 to be the faster one
+    exactly when m < n."""
+    import torch
+
+    import paper_1810_06825_gb300 as frpca
+    import synthetic
+
+    out = {"note": "Alg. 5 vs Alg. 6 forced, device ms per step (refresh + run); Sec. 3.3 / Table 3 predict "
+                   "Alg. 5 faster iff m < n"}
+    for name in SHAPE_WORKLOADS:
+        w = synthetic.WORKLOADS[name]
+        A = synthetic.make_workload(name, seed=1, dtype=np.float32)
+        mat = frpca.FrPCA.from_csr(A, device=dev, stream=stream)
+        k, l, q = w["k"], w["l"], w["q"]
+        U = torch.empty((A.m, k), dtype=torch.float32, device=dev)
+        S = torch.empty((k,), dtype=torch.float64, device=dev)
+        V = torch.empty((A.n, k), dtype=torch.float32, device=dev)
+        entry = {"m": A.m, "n": A.n, "nnz": int(A.nnz), "k": k, "l": l, "q": q}
+        for alg in (5, 6):
+            def step():
+                mat.refresh()
+                mat.run(k, l, q, seed=0, precision="fp32", alg=alg, out=(U, S, V), sync=False)
+            for _ in range(2):
+                step()
+            frpca.frpca_sync(mat.handle)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(5):
+                step()
+            a1.record(stream)
+            frpca.frpca_sync(mat.handle)
+            entry[f"alg{alg}_ms"] = a0.elapsed_time(a1) / 5
+        entry["faster"] = 5 if entry["alg5_ms"] < entry["alg6_ms"] else 6
+        entry["shape_rule"] = 6 if A.m >= A.n else 5
+        mat.close()
+        out[name] = entry
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -468,6 +513,10 @@ def run_ours(args, world, rank, local):
     if rank == 0 and not args.no_fwd_bwd:
         fwd_bwd = _fwd_bwd(dev, with_ref=not args.no_cpu_baseline)
 
+    shapes = None
+    if rank == 0 and not args.no_forms:
+        shapes = _shape_rule(dev, stream)
+
     if rank == 0:
         line = {
             "metric": "frpca_seconds", "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -477,6 +526,7 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(st["kernel_launches"]), "clocks": clk, "phases_ms_per_step": phases,
             "nnz": int(gathered // (l * vsize)), "workload_200000x50000": side, "fwd_bwd": fwd_bwd,
+            "shape_rule_table3": shapes,
         }
         print(json.dumps(line), flush=True)
     return 0

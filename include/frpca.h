@@ -139,7 +139,8 @@ typedef struct frpca_run_opts {
     int q;                      /* passes over A, q >= 2 (Alg. 5/6 "pass parameter")        */
     uint64_t seed;              /* Philox key of the Gaussian test matrix                   */
     frpca_precision precision;
-    int alg;                    /* 0: shape rule (Alg. 6 if m >= n else Alg. 5); 5 or 6     */
+    int alg;                    /* 0: shape rule (Alg. 6 if m >= n else Alg. 5); 5 or 6
+                                   forces one, for either shape (Table 3)                   */
 } frpca_run_opts;
 
 /* The method (Alg. 5 / Alg. 6).  Outputs are device buffers owned by the

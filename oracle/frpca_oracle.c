@@ -399,9 +399,9 @@ int or_frpca(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int32_t
 int or_frpca_ex(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
                 const double *vals, int64_t k, int64_t l, int64_t q, uint64_t seed, int stabilize,
                 double *U, double *S, double *V) {
+    /* Either algorithm is defined for either shape (Table 3 runs both on tall
+     * and wide matrices); the shape rule of Sec. 3.3 only picks the faster. */
     if (alg != 5 && alg != 6) return OR_ERR_INVALID_ARG;
-    if (alg == 6 && m < n) return OR_ERR_INVALID_ARG;
-    if (alg == 5 && m > n) return OR_ERR_INVALID_ARG;
     const int64_t mn = m < n ? m : n;
     if (k < 1 || l < k || l > mn || q < 2) return OR_ERR_INVALID_ARG;
     const int64_t s = l - k;

@@ -376,9 +376,10 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
     // float precisions unless the double-float form is asked for or l > 128.
     const bool split_gram = o->precision != FRPCA_PREC_FP64 && o->precision != FRPCA_PREC_FP32_DFGRAM &&
                             l <= gram_tc_max_l();
+    // Both algorithms are defined for either shape (Table 3 runs each on tall
+    // and wide matrices); the shape rule of Sec. 3.3 picks the default.
     int alg = o->alg ? o->alg : (m >= n ? 6 : 5);
-    if ((alg != 5 && alg != 6) || (alg == 6 && m < n) || (alg == 5 && m > n))
-        return fail(h, FRPCA_ERR_INVALID_ARG, "Alg. 6 needs m >= n and Alg. 5 needs m <= n");
+    if (alg != 5 && alg != 6) return fail(h, FRPCA_ERR_INVALID_ARG, "alg must be 0, 5 or 6");
     const frpca_dtype dt = o->precision == FRPCA_PREC_FP64 ? FRPCA_F64 : FRPCA_F32;
     const int fwd_trans = (alg == 6) ? 0 : 1;  // F = A for Alg. 6, A^T for Alg. 5
     const int bwd_trans = 1 - fwd_trans;
@@ -447,8 +448,9 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
     PhaseTimer fin(h, PH_FINISH);
     void *thin = (alg == 6) ? V : U;  // Q V^(:, ind), rq x k
     void *wide = (alg == 6) ? U : V;  // U^(:, ind),   rw x k
-    // Signs follow the factor of length min(m, n): v when m >= n, else u.
-    const bool sign_on_thin = (alg == 6) || (m < n);
+    // Signs follow the factor of length min(m, n): v when m >= n, else u.  The
+    // thin factor is V for Alg. 6 and U for Alg. 5.
+    const bool sign_on_thin = (alg == 6) == (m >= n);
     CK(h->ws_sign.ensure(sign_workspace_bytes(k, h->num_sms)), "alloc sign workspace");
     CK(launch_make_w(l, k, sm.w, sm.V, 1, 0, nullptr, dt, sm.W1, S, h->d_status, h->stream), "make_w thin");
     if ((st = apply_block(h, rq, l, Q, ld, sm.W1, k, thin, k, dt, "apply thin")) != FRPCA_OK) return st;

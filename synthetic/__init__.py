@@ -189,7 +189,29 @@ WORKLOADS = {
                                         values="tfidf", k=32, l=48, q=4, dtype="f32"),
     "powerlaw_12000000x320000_deg40": dict(kind="powerlaw", m=12_000_000, n=320_000, deg_mean=40, zipf_s=1.05,
                                            values="binary_tfidf", k=100, l=120, q=5, dtype="f32"),
+    # Stand-ins for the matrices of the shape comparison (Table 3): an
+    # AMiner-sized 647,789 x 323,896 matrix with 16 entries per row (Matrix 4's
+    # density), its first 107,966 columns (as Matrix 7 is cut from Matrix 6)
+    # and its first 107,966 rows (as Matrix 8); k = 100, s = 5, q = 11.
+    "powerlaw_647789x323896_deg16": dict(kind="powerlaw", m=647_789, n=323_896, deg_mean=16, zipf_s=1.05,
+                                         values="tfidf", k=100, l=105, q=11, dtype="f32"),
+    "powerlaw_647789x107966_cols": dict(kind="slice", base="powerlaw_647789x323896_deg16", m=647_789, n=107_966,
+                                        k=100, l=105, q=11, dtype="f32"),
+    "powerlaw_107966x323896_rows": dict(kind="slice", base="powerlaw_647789x323896_deg16", m=107_966, n=323_896,
+                                        k=100, l=105, q=11, dtype="f32"),
 }
+
+
+def leading_block(A: CSR, m: int, n: int) -> CSR:
+    """The first m rows and first n columns of A (entries keep their values)."""
+    indptr = A.indptr[: m + 1]
+    cols = A.indices[: indptr[-1]]
+    vals = A.data[: indptr[-1]]
+    keep = cols < n
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(indptr))[keep]
+    out_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=m), out=out_ptr[1:])
+    return CSR(m, n, out_ptr, np.ascontiguousarray(cols[keep]), np.ascontiguousarray(vals[keep]))
 
 
 def make_workload(name: str, seed: int = 1, dtype=None) -> CSR:
@@ -197,4 +219,6 @@ def make_workload(name: str, seed: int = 1, dtype=None) -> CSR:
     dt = dtype or (np.float64 if w["dtype"] == "f64" else np.float32)
     if w["kind"] == "uniform":
         return uniform_csr(w["m"], w["n"], w["nnz"], seed=seed, dtype=dt)
+    if w["kind"] == "slice":
+        return leading_block(make_workload(w["base"], seed=seed, dtype=dt), w["m"], w["n"])
     return powerlaw_csr(w["m"], w["n"], w["deg_mean"], w["zipf_s"], w["values"], seed=seed, dtype=dt)

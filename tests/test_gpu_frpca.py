@@ -127,6 +127,20 @@ def test_frpca_uniform_2000x1000(prec):
     _compare(A if prec == "fp64" else A.astype(np.float32), w["k"], w["l"], w["q"], 0, prec)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", ["tall", "wide"])
+@pytest.mark.parametrize("alg", [5, 6])
+def test_frpca_forced_alg_either_shape(prec, shape, alg):
+    """Table 3 runs Alg. 5 and Alg. 6 on tall and on wide matrices: either
+    algorithm, forced on either shape, matches the oracle's same algorithm
+    (and the sign convention follows the shorter factor whatever the
+    algorithm)."""
+    A = SMALL_TALL if shape == "tall" else SMALL_WIDE
+    A = A.astype(np.float64 if prec == "fp64" else np.float32)
+    for q in (4, 5):
+        _compare(A, 10, 24, q, 7, prec, alg=alg)
+
+
 def test_frpca_square_alg5_forced():
     """m == n with Alg. 5 forced: the sign is decided on V, the apply side."""
     A = synthetic.powerlaw_csr(900, 900, 10, 1.1, "tfidf", seed=4, dtype=np.float64)
@@ -165,7 +179,7 @@ def test_frpca_invalid_args():
             mat.run(k, l, q, precision="fp64")
         assert ei.value.status == 1
     with pytest.raises(frpca.FrpcaError) as ei:
-        mat.run(3, 5, 3, alg=5)  # Alg. 5 needs m <= n
+        mat.run(3, 5, 3, alg=7)  # only Alg. 5 and Alg. 6 exist
     assert ei.value.status == 1
     mat.close()
 
