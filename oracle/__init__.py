@@ -38,6 +38,8 @@ PINS = {
     "eig_sym": "numpy.linalg.eigh; orthogonality and residual",
     "eigsvd": "Lemma 1 against numpy.linalg.svd",
     "frpca": "exact-rank closed form, planted spectra, Theorems 1-2 vs the QR scheme, exact identities",
+    "frpca (center)": "the uncentered method on the explicitly centered matrix stored dense; closed form for an "
+                      "exactly rank-l centered matrix",
 }
 
 
@@ -81,7 +83,8 @@ def _load():
     lib.or_gram.argtypes = [I64, I64, P, I64, P]
     lib.or_eigsvd.argtypes = [I64, I64, P, I64, P, I64, P, P]
     lib.or_frpca.argtypes = [ctypes.c_int, I64, I64, P, P, P, I64, I64, I64, U64, P, P, P]
-    lib.or_frpca_ex.argtypes = [ctypes.c_int, I64, I64, P, P, P, I64, I64, I64, U64, ctypes.c_int, P, P, P]
+    lib.or_frpca_ex.argtypes = [ctypes.c_int, I64, I64, P, P, P, I64, I64, I64, U64, ctypes.c_int, ctypes.c_int,
+                                P, P, P]
     lib.or_svd_adjoint_sddmm.argtypes = [I64, I64, P, P, I64, P, P, P, P, P, P, P]
     lib.or_num_threads.argtypes = []
     for name in ("or_gaussian", "or_csr_transpose", "or_spmm", "or_spmm_t", "or_lu_ptl", "or_eig_sym",
@@ -199,11 +202,13 @@ def eigsvd(M: np.ndarray):
 
 
 def frpca(m: int, n: int, indptr, indices, data, k: int, l: int, q: int, seed: int, alg: int | None = None,
-          stabilize: bool = False):
+          stabilize: bool = False, center: bool = False):
     """Alg. 5 / Alg. 6.  ``alg=None`` applies the shape rule (Alg. 6 when m >= n).
 
     ``stabilize=True`` runs the last power-iteration orthonormalization as
     eigSVD(lu(M)) (same range by Lemma 3, same result in exact arithmetic).
+    ``center=True`` factors the column-centered A - 1 mu^T (PCA proper,
+    Sec. 2.1) through rank-1 corrections of every product.
     """
     indptr, indices, data = _csr(indptr, indices, data)
     if alg is None:
@@ -212,7 +217,7 @@ def frpca(m: int, n: int, indptr, indices, data, k: int, l: int, q: int, seed: i
     S = np.empty(k, dtype=np.float64)
     V = np.empty((n, k), dtype=np.float64)
     _check(_load().or_frpca_ex(alg, m, n, _p(indptr), _p(indices), _p(data), k, l, q, seed, int(stabilize),
-                               _p(U), _p(S), _p(V)), "frpca")
+                               int(center), _p(U), _p(S), _p(V)), "frpca")
     return U, S, V
 
 

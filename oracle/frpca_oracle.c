@@ -387,7 +387,41 @@ static int orth_step(int use_eigsvd, int64_t R, int64_t l, double *M) {
 int or_frpca(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
              const double *vals, int64_t k, int64_t l, int64_t q, uint64_t seed,
              double *U, double *S, double *V) {
-    return or_frpca_ex(alg, m, n, rowptr, colidx, vals, k, l, q, seed, 0, U, S, V);
+    return or_frpca_ex(alg, m, n, rowptr, colidx, vals, k, l, q, seed, 0, 0, U, S, V);
+}
+
+/* The products of the method with A or A^T (trans), optionally with the
+ * column-centered matrix Abar = A - 1 mu^T (mu_j = mean of column j, the PCA
+ * of Sec. 2.1 on centered data), through the identities
+ *   Abar X   = A X   - 1 (mu^T X),
+ *   Abar^T Y = A^T Y - mu (1^T Y),
+ * with the row sums taken in ascending row order.                            */
+struct or_mat {
+    int64_t m, n, l;
+    const int64_t *rowptr, *rowptrT;
+    const int32_t *colidx, *colidxT;
+    const double *vals, *valsT, *mu; /* mu: NULL when not centering */
+};
+
+static int or_product(const struct or_mat *A, int trans, const double *X, double *Y) {
+    const int64_t rows = trans ? A->n : A->m, cols = trans ? A->m : A->n, l = A->l;
+    int st = trans ? or_spmm(A->n, A->m, A->rowptrT, A->colidxT, A->valsT, l, X, l, Y, l)
+                   : or_spmm(A->m, A->n, A->rowptr, A->colidx, A->vals, l, X, l, Y, l);
+    if (st != OR_OK || !A->mu) return st;
+    double *v = (double *)calloc((size_t)l, sizeof(double));
+    if (!v) return OR_ERR_OOM;
+    /* v = mu^T X (A X) or 1^T X (A^T X), summed over the rows of X in order. */
+    for (int64_t r = 0; r < cols; ++r) {
+        const double w = trans ? 1.0 : A->mu[r];
+        for (int64_t c = 0; c < l; ++c) v[c] += w * X[r * l + c];
+    }
+    /* Y -= 1 v^T (A X) or mu v^T (A^T X). */
+    for (int64_t r = 0; r < rows; ++r) {
+        const double w = trans ? A->mu[r] : 1.0;
+        for (int64_t c = 0; c < l; ++c) Y[r * l + c] -= w * v[c];
+    }
+    free(v);
+    return OR_OK;
 }
 
 /* stabilize != 0: the last orthonormalization of the power iteration is
@@ -397,7 +431,7 @@ int or_frpca(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int32_t
  * number of the unit-lower factor instead of that of A^T A Q, and the
  * orthonormal basis it returns is correspondingly more accurate. */
 int or_frpca_ex(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
-                const double *vals, int64_t k, int64_t l, int64_t q, uint64_t seed, int stabilize,
+                const double *vals, int64_t k, int64_t l, int64_t q, uint64_t seed, int stabilize, int center,
                 double *U, double *S, double *V) {
     /* Either algorithm is defined for either shape (Table 3 runs both on tall
      * and wide matrices); the shape rule of Sec. 3.3 only picks the faster. */
@@ -416,13 +450,21 @@ int or_frpca_ex(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int3
     int64_t *rowptrT = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
     int32_t *colidxT = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
     double *valsT = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
-    int st = (Q && W && Sh && Vh && rowptrT && colidxT && valsT) ? OR_OK : OR_ERR_OOM;
+    double *mu = center ? (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double)) : NULL;
+    int st = (Q && W && Sh && Vh && rowptrT && colidxT && valsT && (mu || !center)) ? OR_OK : OR_ERR_OOM;
     if (st == OR_OK) st = or_csr_transpose(m, n, rowptr, colidx, vals, rowptrT, colidxT, valsT);
+    if (st == OR_OK && center) {
+        /* Column means: the entries of column j (row j of A^T) over m. */
+        for (int64_t j = 0; j < n; ++j) {
+            double acc = 0.0;
+            for (int64_t e = rowptrT[j]; e < rowptrT[j + 1]; ++e) acc += valsT[e];
+            mu[j] = acc / (double)m;
+        }
+    }
+    const struct or_mat Am = {m, n, l, rowptr, rowptrT, colidx, colidxT, vals, valsT, mu};
     /* "forward" product: A X for Alg. 6, A^T X for Alg. 5 (and the reverse). */
-#define FWD(Xin, Yout) ((alg == 6) ? or_spmm(m, n, rowptr, colidx, vals, l, Xin, l, Yout, l) \
-                                   : or_spmm(n, m, rowptrT, colidxT, valsT, l, Xin, l, Yout, l))
-#define BWD(Xin, Yout) ((alg == 6) ? or_spmm(n, m, rowptrT, colidxT, valsT, l, Xin, l, Yout, l) \
-                                   : or_spmm(m, n, rowptr, colidx, vals, l, Xin, l, Yout, l))
+#define FWD(Xin, Yout) or_product(&Am, alg == 6 ? 0 : 1, Xin, Yout)
+#define BWD(Xin, Yout) or_product(&Am, alg == 6 ? 1 : 0, Xin, Yout)
     if (st == OR_OK) {
         if (q % 2 == 0) {
             /* Alg. 6: Q = randn(k+s, m); Q = (Q A)^T.  Alg. 5: Q = A randn(n, k+s). */
@@ -468,7 +510,7 @@ int or_frpca_ex(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int3
     }
 #undef FWD
 #undef BWD
-    free(Q); free(W); free(Sh); free(Vh); free(rowptrT); free(colidxT); free(valsT);
+    free(Q); free(W); free(Sh); free(Vh); free(rowptrT); free(colidxT); free(valsT); free(mu);
     return st;
 }
 

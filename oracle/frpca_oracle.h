@@ -62,9 +62,10 @@ int or_frpca(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int32_t
 
 /* Same, with stabilize != 0 running the last power-iteration orthonormalization
  * as eigSVD(lu(M)) (Lemma 3 keeps the range, so Alg. 5/6 are unchanged in
- * exact arithmetic). */
+ * exact arithmetic), and center != 0 factoring the column-centered matrix
+ * A - 1 mu^T (mu = column means; the PCA of Sec. 2.1) without forming it. */
 int or_frpca_ex(int alg, int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
-                const double *vals, int64_t k, int64_t l, int64_t q, uint64_t seed, int stabilize,
+                const double *vals, int64_t k, int64_t l, int64_t q, uint64_t seed, int stabilize, int center,
                 double *U, double *S, double *V);
 
 /* Gradient with respect to the CSR values of a loss of the rank-k truncated

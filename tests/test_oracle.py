@@ -342,3 +342,46 @@ def test_frpca_invalid_args(oracle_lib, k, l, q):
     with pytest.raises(oracle.OracleError) as ei:
         oracle_lib.frpca(A.m, A.n, A.indptr, A.indices, A.data, k, l, q, seed=0)
     assert ei.value.status == oracle.ERR_INVALID_ARG
+
+
+# ----------------------------------------------------------------- implicit centering
+@pytest.mark.parametrize("q", [2, 3, 4, 5])
+@pytest.mark.parametrize("tall", [True, False])
+def test_frpca_centered_equals_explicit_centering(oracle_lib, q, tall):
+    """The centered method (rank-1 corrections of every product) equals the
+    plain method run on the centered matrix A - 1 mu^T stored as a dense CSR
+    (every entry kept): the same algorithm on the same matrix and Omega, so
+    the results agree to rounding."""
+    A = synthetic.powerlaw_csr(300, 120, 8, 1.1, "tfidf", seed=11, dtype=np.float64)
+    if not tall:
+        pT, cT, vT = oracle_lib.csr_transpose(A.m, A.n, A.indptr, A.indices, A.data)
+        A = synthetic.CSR(A.n, A.m, pT, cT, vT)
+    Ad = A.to_dense()
+    Ac = Ad - Ad.mean(axis=0, keepdims=True)
+    D = synthetic.from_dense(Ac, keep_zeros=True)
+    k, l = 6, 12
+    U, S, V = oracle_lib.frpca(A.m, A.n, A.indptr, A.indices, A.data, k, l, q, seed=2, center=True)
+    Ue, Se, Ve = oracle_lib.frpca(D.m, D.n, D.indptr, D.indices, D.data, k, l, q, seed=2)
+    assert rel_err(S, Se) <= 1e-10
+    assert max_principal_sine(U, Ue) <= 1e-8 and max_principal_sine(V, Ve) <= 1e-8
+    # Centered columns: U is orthogonal to the all-ones vector (Abar^T 1 = 0,
+    # and U spans part of range(Abar)).
+    assert np.max(np.abs(U.sum(axis=0))) <= 1e-8 * np.sqrt(A.m)
+
+
+def test_frpca_centered_closed_form(oracle_lib):
+    """A matrix whose centered version has rank exactly l: a rank-l matrix plus
+    a constant row added to every row (the offset the centering removes),
+    both sparse patterns stored in full.  Any q returns the exact top-k SVD
+    of the centered matrix."""
+    rng = np.random.default_rng(3)
+    m, n, r, k = 200, 80, 8, 5
+    B = (rng.standard_normal((m, r)) * 0.8 ** np.arange(r)) @ rng.standard_normal((r, n))
+    B -= B.mean(axis=0, keepdims=True)
+    Ad = B + rng.standard_normal(n)[None, :]
+    A = synthetic.from_dense(Ad, keep_zeros=True)
+    Ut, St, Vt = np.linalg.svd(B, full_matrices=False)
+    for q in (2, 3, 4):
+        U, S, V = oracle_lib.frpca(m, n, A.indptr, A.indices, A.data, k, r, q, seed=1, center=True)
+        assert rel_err(S, St[:k]) <= 1e-10
+        assert max_principal_sine(U, Ut[:, :k]) <= 1e-9 and max_principal_sine(V, Vt[:k].T) <= 1e-9
