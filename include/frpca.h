@@ -141,6 +141,10 @@ typedef struct frpca_run_opts {
     frpca_precision precision;
     int alg;                    /* 0: shape rule (Alg. 6 if m >= n else Alg. 5); 5 or 6
                                    forces one, for either shape (Table 3)                   */
+    int center;                 /* 1: PCA proper (Sec. 2.1): factor the column-centered
+                                   A - 1 mu^T (mu = column means of A) without forming it:
+                                   every product gets its rank-1 correction, A X - 1 (mu^T X)
+                                   and A^T Y - mu (1^T Y); 0: factor A as given             */
 } frpca_run_opts;
 
 /* The method (Alg. 5 / Alg. 6).  Outputs are device buffers owned by the

@@ -53,7 +53,7 @@ class frpca_create_opts(ctypes.Structure):
 
 class frpca_run_opts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("l", ctypes.c_int), ("q", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("precision", ctypes.c_int), ("alg", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("alg", ctypes.c_int), ("center", ctypes.c_int)]
 
 
 class frpca_stats(ctypes.Structure):
@@ -372,8 +372,9 @@ class FrPCA:
             pass
 
     def run(self, k: int, l: int, q: int, seed: int = 0, precision: str = "fp32", alg: int = 0, out=None,
-            sync: bool = True):
-        """Rank-k frPCA (Alg. 5/6); returns (U m x k, S k descending float64, V n x k)."""
+            sync: bool = True, center: bool = False):
+        """Rank-k frPCA (Alg. 5/6); returns (U m x k, S k descending float64, V n x k).
+        ``center=True`` factors the column-centered matrix (PCA proper)."""
         torch = _torch()
         dt = torch.float64 if precision == "fp64" else torch.float32
         dev = self.device
@@ -383,7 +384,7 @@ class FrPCA:
             V = torch.empty((self.n, k), dtype=dt, device=dev)
         else:
             U, S, V = out
-        opts = frpca_run_opts(k=k, l=l, q=q, seed=seed, precision=PREC[precision], alg=alg)
+        opts = frpca_run_opts(k=k, l=l, q=q, seed=seed, precision=PREC[precision], alg=alg, center=int(center))
         fn = frpca_run if sync else frpca_run_async
         fn(self.handle, opts, U.data_ptr(), S.data_ptr(), V.data_ptr())
         return U, S, V

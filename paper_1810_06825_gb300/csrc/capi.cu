@@ -33,6 +33,9 @@ struct frpca_ctx {
     int pan_trans = 1;           // which pass uses it: 1 = A^T X (m >= n), 0 = A X (m < n)
     bool at_vals_stale = false;  // A^T's values wait for a refresh (the panel pass had its own)
     bool fused = false;          // the power iteration's pass pairs as one sweep when it applies
+    bool center = false;         // the current run factors A - 1 mu^T (frpca_run_opts.center)
+    bool mu_ready = false;       // column means in ws_center are those of the current values
+    DevBuf ws_center;
     MemBudget budget;                            // frpca_create_opts.max_device_bytes
     long long wait_limit = kBarrierLimitCycles;  // frpca_set_wait_limit
     std::string err;
@@ -177,9 +180,31 @@ frpca_status values_for(frpca_ctx *h, frpca_dtype dt, const void **va, const voi
     return FRPCA_OK;
 }
 
-// One SpMM pass with the handle's matrix (trans selects A^T).
+frpca_status spmm_pass_plain(frpca_ctx *h, int trans, int l, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                             frpca_dtype dt);
+
+// One SpMM pass with the handle's matrix (trans selects A^T); in a centered
+// run, the product with A - 1 mu^T (the pass, then its rank-1 correction).
 frpca_status spmm_pass(frpca_ctx *h, int trans, int l, const void *X, int64_t ldx, void *Y, int64_t ldy,
                        frpca_dtype dt) {
+    frpca_status st = spmm_pass_plain(h, trans, l, X, ldx, Y, ldy, dt);
+    if (st != FRPCA_OK || !h->center) return st;
+    CK(h->ws_center.ensure(center_workspace_bytes(h->A.rows, h->A.cols, l)), "alloc centering workspace");
+    double *mu = (double *)h->ws_center.ptr;
+    if (!h->mu_ready) {
+        if ((st = fresh_at_values(h)) != FRPCA_OK) return st;
+        CK(launch_col_means(h->AT, h->A.rows, mu, h->stream), "column means");
+        h->mu_ready = true;
+    }
+    void *ws = (char *)h->ws_center.ptr + round_up(sizeof(double) * h->A.cols, 256);
+    PhaseTimer t(h, trans ? PH_SPMM_T : PH_SPMM);
+    CK(launch_center_correction(trans, h->A.rows, h->A.cols, l, mu, X, ldx, Y, ldy, dt, ws, h->stream),
+       "centering correction");
+    return FRPCA_OK;
+}
+
+frpca_status spmm_pass_plain(frpca_ctx *h, int trans, int l, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                             frpca_dtype dt) {
     if (h->pan.active() && trans == h->pan_trans && dt == h->A.dtype) {
         // The gathered block is read panel by panel, each panel resident in L2.
         CK(h->ws_spmm.ensure(std::max<size_t>(256, panel_scratch_bytes(h->pan, l, dt))), "alloc spmm scratch");
@@ -392,6 +417,7 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
 
     frpca_status st = reset_status(h);
     if (st != FRPCA_OK) return st;
+    h->center = o->center != 0;
     const size_t qbytes = es * (size_t)rq * ld, wbytes = es * (size_t)rw * ld;
     if (h->ws_q.bytes < qbytes) {
         CK(h->ws_q.ensure(qbytes), "alloc Q");
@@ -424,7 +450,7 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
     // of A^T A Q (about 1e4 here) to that of the unit-lower factor (about 1e2),
     // which float storage of the block can carry.
     const int loops = (q - 1) / 2;
-    const bool fused = h->fused && fused_sweep_applies(h, rq, rw, ld, dt, fwd_trans);
+    const bool fused = h->fused && !h->center && fused_sweep_applies(h, rq, rw, ld, dt, fwd_trans);
     for (int i = 1; i <= loops; ++i) {
         if (fused) {
             if ((st = fused_sweep(h, fwd_trans, l, Q, W, ld, rq, dt)) != FRPCA_OK) return st;
@@ -467,6 +493,7 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
         CK(launch_scale_columns(rq, k, thin, k, dt, sm.sign, h->stream), "flip thin");
     }
     h->acc.runs += 1;
+    h->center = false;
     return FRPCA_OK;
 }
 
@@ -490,7 +517,7 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
     for (DevBuf *b : {&h->own_rowptr, &h->own_colidx, &h->own_vals, &h->t_rowptr, &h->t_colidx, &h->t_vals,
                       &h->t_perm, &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
                       &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot, &h->ws_plan,
-                      &h->hy.b_hot, &h->hy.b_slot, &h->hy.b_dense, &h->hy.b_crow, &h->hy.b_ccol, &h->hy.b_cval}) {
+                      &h->ws_center, &h->hy.b_hot, &h->hy.b_slot, &h->hy.b_dense, &h->hy.b_crow, &h->hy.b_ccol, &h->hy.b_cval}) {
         b->stream = h->stream;
         b->budget = &h->budget;
     }
@@ -642,7 +669,8 @@ frpca_status frpca_destroy(frpca_handle h) {
     h->pan.free_all();
     for (DevBuf *b : {&h->own_rowptr, &h->own_colidx, &h->own_vals, &h->t_rowptr, &h->t_colidx, &h->t_vals,
                       &h->t_perm, &h->alt_A, &h->alt_AT, &h->ws_q, &h->ws_w, &h->ws_spmm, &h->ws_gram, &h->ws_eig, &h->ws_lu,
-                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot, &h->ws_plan})
+                      &h->ws_small, &h->ws_sign, &h->ws_scratch, &h->ws_scan, &h->ws_bwd, &h->ws_hot, &h->ws_plan,
+                      &h->ws_center})
         b->release();
     for (auto &mk : h->marks) {
         cudaEventDestroy(mk.a);
@@ -677,6 +705,7 @@ frpca_status frpca_refresh(frpca_handle h) {
     }
     CK(refresh_hybrid(h->A, h->hy, h->stream), "hot-column block");
     t.done();
+    h->mu_ready = false;
     h->alt_ready = false;
     return FRPCA_OK;
 }
@@ -762,6 +791,7 @@ frpca_status frpca_spmm(frpca_handle h, int trans, int l, const void *X, int64_t
     if (l < 1 || l > 4 * 32 * (dt == FRPCA_F32 ? 4 : 2) || !X || !Y || !ld_ok(ldx, l, dt) || !ld_ok(ldy, l, dt) ||
         !aligned16(X) || !aligned16(Y))
         return fail(h, FRPCA_ERR_INVALID_ARG, "bad spmm arguments (l range, ld multiple of 16 bytes, alignment)");
+    h->center = false;
     return spmm_pass(h, trans, l, X, ldx, Y, ldy, dt);
 }
 

@@ -104,6 +104,14 @@ struct PanelCSR {
     void free_all();
 };
 
+// ---- center.cu (products with the column-centered A - 1 mu^T)
+size_t center_workspace_bytes(int64_t m, int64_t n, int l);  // mu (n) followed by the correction's scratch
+cudaError_t launch_col_means(const DeviceCSR &AT, int64_t m, double *mu, cudaStream_t s);
+// After Y = A X (trans 0) or Y = A^T X (trans 1): Y -= 1 (mu^T X) or
+// mu (1^T X); ws: the scratch part of the centering workspace.
+cudaError_t launch_center_correction(int trans, int64_t m, int64_t n, int l, const double *mu, const void *X,
+                                     int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *ws, cudaStream_t s);
+
 // ---- gaussian.cu
 cudaError_t launch_gaussian(int64_t R, int l, int64_t ld, uint64_t seed, frpca_dtype dt, void *out,
                             cudaStream_t s);
