@@ -406,6 +406,51 @@ def _shape_rule(dev, stream) -> dict:
     return out
 
 
+def _q_sweep(dev, stream, with_ref: bool) -> dict:
+    """Table 2's trade-off on the 200,000 x 50,000 workload (k = 100, l = 120,
+    FP32): device time per run of frPCA and of the basic randomized PCA with
+    QR (CholeskyQR2 after every product) with the same number of passes q,
+    their ratio (Sp1, the paper's speedup over the QR scheme), and, when the
+    oracle runs, both schemes' largest singular-value error against a
+    converged reference (the oracle at q = 12)."""
+    import torch
+
+    import paper_1810_06825_gb300 as frpca
+    import synthetic
+
+    A = synthetic.make_workload(SIDE_WORKLOAD, seed=1, dtype=np.float32)
+    k, l = 100, 120
+    mat = frpca.FrPCA.from_csr(A, device=dev, stream=stream)
+    ref = None
+    if with_ref:
+        import oracle
+        _, ref, _ = oracle.frpca(A.m, A.n, A.indptr, A.indices, A.data.astype(np.float64), k, l, 12, 0)
+    U = torch.empty((A.m, k), dtype=torch.float32, device=dev)
+    S = torch.empty((k,), dtype=torch.float64, device=dev)
+    V = torch.empty((A.n, k), dtype=torch.float32, device=dev)
+    out = {"workload": SIDE_WORKLOAD, "note": "ms per run (no A^T rebuild), same q for both schemes; Sp1 = "
+           "qr_ms / frpca_ms; sigma_err vs the oracle at q = 12"}
+    for q in (2, 3, 4, 6, 9, 11):
+        entry = {}
+        for scheme in ("frpca", "qr"):
+            for _ in range(2):
+                mat.run(k, l, q, seed=0, precision="fp32", out=(U, S, V), sync=False, scheme=scheme)
+            frpca.frpca_sync(mat.handle)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(3):
+                mat.run(k, l, q, seed=0, precision="fp32", out=(U, S, V), sync=False, scheme=scheme)
+            a1.record(stream)
+            frpca.frpca_sync(mat.handle)
+            entry[f"{scheme}_ms"] = a0.elapsed_time(a1) / 3
+            if ref is not None:
+                entry[f"{scheme}_sigma_err"] = float(np.max(np.abs(S.cpu().numpy() - ref) / ref))
+        entry["Sp1"] = entry["qr_ms"] / entry["frpca_ms"]
+        out[f"q{q}"] = entry
+    mat.close()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -513,9 +558,10 @@ def run_ours(args, world, rank, local):
     if rank == 0 and not args.no_fwd_bwd:
         fwd_bwd = _fwd_bwd(dev, with_ref=not args.no_cpu_baseline)
 
-    shapes = None
+    shapes, qsweep = None, None
     if rank == 0 and not args.no_forms:
         shapes = _shape_rule(dev, stream)
+        qsweep = _q_sweep(dev, stream, with_ref=not args.no_cpu_baseline)
 
     if rank == 0:
         line = {
@@ -526,7 +572,7 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(st["kernel_launches"]), "clocks": clk, "phases_ms_per_step": phases,
             "nnz": int(gathered // (l * vsize)), "workload_200000x50000": side, "fwd_bwd": fwd_bwd,
-            "shape_rule_table3": shapes,
+            "shape_rule_table3": shapes, "q_sweep_table2": qsweep,
         }
         print(json.dumps(line), flush=True)
     return 0

@@ -145,6 +145,12 @@ typedef struct frpca_run_opts {
                                    A - 1 mu^T (mu = column means of A) without forming it:
                                    every product gets its rank-1 correction, A X - 1 (mu^T X)
                                    and A^T Y - mu (1^T Y); 0: factor A as given             */
+    int scheme;                 /* 0: frPCA (Alg. 5/6).  1: the basic randomized PCA it is
+                                   compared with (Alg. 1/4, Theorems 1-2, Table 2): orth()
+                                   (CholeskyQR2) after every product, same q passes (even q:
+                                   power parameter p = (q-2)/2; odd q: the modified start
+                                   Q = Omega of Sec. 3.2), same final step; alg 4 / 6 = the
+                                   random matrix on the left, 1 / 5 = on the right          */
 } frpca_run_opts;
 
 /* The method (Alg. 5 / Alg. 6).  Outputs are device buffers owned by the
@@ -188,6 +194,9 @@ typedef struct frpca_stats {
     double spmm_a_ms, spmm_t_ms;          /* their device time (sum: spmm_ms); a
                                              fused sweep's time goes to spmm_t_ms */
     int64_t fused_sweeps;                 /* pass pairs run as one sweep        */
+    int64_t qr_calls;                     /* orth() calls of the QR scheme (their
+                                             Gram time counts as gram_ms, the
+                                             Cholesky and R^-1 product as lu_ms) */
 } frpca_stats;
 
 /* enable != 0 records events around every phase (adds a few microseconds per

@@ -53,7 +53,8 @@ class frpca_create_opts(ctypes.Structure):
 
 class frpca_run_opts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("l", ctypes.c_int), ("q", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("precision", ctypes.c_int), ("alg", ctypes.c_int), ("center", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("alg", ctypes.c_int), ("center", ctypes.c_int),
+                ("scheme", ctypes.c_int)]
 
 
 class frpca_stats(ctypes.Structure):
@@ -63,7 +64,7 @@ class frpca_stats(ctypes.Structure):
                 ("gram_ms", ctypes.c_double), ("eig_ms", ctypes.c_double), ("apply_ms", ctypes.c_double),
                 ("gaussian_ms", ctypes.c_double), ("transpose_ms", ctypes.c_double), ("finish_ms", ctypes.c_double),
                 ("spmm_a_passes", ctypes.c_int64), ("spmm_t_passes", ctypes.c_int64), ("spmm_a_ms", ctypes.c_double),
-                ("spmm_t_ms", ctypes.c_double), ("fused_sweeps", ctypes.c_int64)]
+                ("spmm_t_ms", ctypes.c_double), ("fused_sweeps", ctypes.c_int64), ("qr_calls", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -372,9 +373,10 @@ class FrPCA:
             pass
 
     def run(self, k: int, l: int, q: int, seed: int = 0, precision: str = "fp32", alg: int = 0, out=None,
-            sync: bool = True, center: bool = False):
+            sync: bool = True, center: bool = False, scheme: str = "frpca"):
         """Rank-k frPCA (Alg. 5/6); returns (U m x k, S k descending float64, V n x k).
-        ``center=True`` factors the column-centered matrix (PCA proper)."""
+        ``center=True`` factors the column-centered matrix (PCA proper);
+        ``scheme="qr"`` runs the basic randomized PCA with QR (Alg. 1/4)."""
         torch = _torch()
         dt = torch.float64 if precision == "fp64" else torch.float32
         dev = self.device
@@ -384,7 +386,8 @@ class FrPCA:
             V = torch.empty((self.n, k), dtype=dt, device=dev)
         else:
             U, S, V = out
-        opts = frpca_run_opts(k=k, l=l, q=q, seed=seed, precision=PREC[precision], alg=alg, center=int(center))
+        opts = frpca_run_opts(k=k, l=l, q=q, seed=seed, precision=PREC[precision], alg=alg, center=int(center),
+                              scheme={"frpca": 0, "qr": 1}[scheme])
         fn = frpca_run if sync else frpca_run_async
         fn(self.handle, opts, U.data_ptr(), S.data_ptr(), V.data_ptr())
         return U, S, V

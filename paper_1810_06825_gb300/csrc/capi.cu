@@ -383,6 +383,32 @@ frpca_status eigsvd_inplace(frpca_ctx *h, int64_t R, int l, void *M, int64_t ld,
     return apply_block(h, R, l, M, ld, s.W1, l, M, ld, dt, "apply");
 }
 
+// orth() of the basic randomized PCA (Alg. 1 / Alg. 4) by CholeskyQR2: twice
+// B = M^T M, R^T R = B, M <- M R^{-1} (in place).  The Gram runs on the tensor
+// cores for float blocks with l <= 128 (CholeskyQR2's second pass repairs the
+// first pass's loss of orthogonality), in double-float or double otherwise.
+frpca_status orth_qr(frpca_ctx *h, int64_t R, int l, void *M, int64_t ld, frpca_dtype dt, Small &sm) {
+    const bool tc = dt == FRPCA_F32 && l <= gram_tc_max_l();
+    CK(h->ws_gram.ensure(tc ? gram_tc_workspace_bytes(R, l, h->num_sms) : gram_workspace_bytes(R, l, h->num_sms)),
+       "alloc gram workspace");
+    for (int pass = 0; pass < 2; ++pass) {
+        {
+            PhaseTimer t(h, PH_GRAM);
+            if (tc)
+                CK(launch_gram_tc(R, l, (const float *)M, ld, sm.B, h->ws_gram.ptr, h->num_sms, h->d_status,
+                                  h->stream), "tensor-core gram launch");
+            else
+                CK(launch_gram(R, l, M, ld, dt, sm.B, h->ws_gram.ptr, h->num_sms, h->stream), "gram launch");
+        }
+        PhaseTimer t(h, PH_LU);
+        CK(launch_chol_inv(l, sm.B, sm.V, (double *)sm.W2, dt, sm.W1, h->d_status, h->stream), "cholesky");
+        frpca_status st = apply_block(h, R, l, M, ld, sm.W1, l, M, ld, dt, "apply R^-1");
+        if (st != FRPCA_OK) return st;
+    }
+    h->acc.qr_calls += 1;
+    return FRPCA_OK;
+}
+
 frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S, void *V) {
     if (!h) return fail(nullptr, FRPCA_ERR_INVALID_ARG, "null handle");
     if (!h->has_matrix) return fail(h, FRPCA_ERR_INVALID_ARG, "handle has no matrix");
@@ -402,9 +428,14 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
     const bool split_gram = o->precision != FRPCA_PREC_FP64 && o->precision != FRPCA_PREC_FP32_DFGRAM &&
                             l <= gram_tc_max_l();
     // Both algorithms are defined for either shape (Table 3 runs each on tall
-    // and wide matrices); the shape rule of Sec. 3.3 picks the default.
+    // and wide matrices); the shape rule of Sec. 3.3 picks the default.  The
+    // QR scheme (basic randomized PCA) runs Alg. 4 on the Alg. 6 driver (the
+    // random matrix on the left of A) and Alg. 1 on the Alg. 5 driver.
+    if (o->scheme != 0 && o->scheme != 1) return fail(h, FRPCA_ERR_INVALID_ARG, "scheme must be 0 or 1");
+    const bool qr = o->scheme == 1;
     int alg = o->alg ? o->alg : (m >= n ? 6 : 5);
-    if (alg != 5 && alg != 6) return fail(h, FRPCA_ERR_INVALID_ARG, "alg must be 0, 5 or 6");
+    if (qr && (alg == 1 || alg == 4)) alg = (alg == 4) ? 6 : 5;
+    if (alg != 5 && alg != 6) return fail(h, FRPCA_ERR_INVALID_ARG, "alg must be 0, 5 or 6 (1 or 4 for the QR scheme)");
     const frpca_dtype dt = o->precision == FRPCA_PREC_FP64 ? FRPCA_F64 : FRPCA_F32;
     const int fwd_trans = (alg == 6) ? 0 : 1;  // F = A for Alg. 6, A^T for Alg. 5
     const int bwd_trans = 1 - fwd_trans;
@@ -440,7 +471,8 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
     }
     if (q % 2 == 0) {
         if ((st = spmm_pass(h, bwd_trans, l, W, ld, Q, ld, dt)) != FRPCA_OK) return st;
-        st = (q == 2) ? eigsvd_inplace(h, rq, l, Q, ld, dt, sm, nullptr) : lu_step(h, rq, l, Q, ld, dt, nullptr);
+        st = qr ? orth_qr(h, rq, l, Q, ld, dt, sm)
+                : (q == 2) ? eigsvd_inplace(h, rq, l, Q, ld, dt, sm, nullptr) : lu_step(h, rq, l, Q, ld, dt, nullptr);
         if (st != FRPCA_OK) return st;
     }
     // The power iteration: one orthonormalization per A, A^T pair (Sec. 3.1),
@@ -450,8 +482,16 @@ frpca_status run_impl(frpca_ctx *h, const frpca_run_opts *o, void *U, double *S,
     // of A^T A Q (about 1e4 here) to that of the unit-lower factor (about 1e2),
     // which float storage of the block can carry.
     const int loops = (q - 1) / 2;
-    const bool fused = h->fused && !h->center && fused_sweep_applies(h, rq, rw, ld, dt, fwd_trans);
-    for (int i = 1; i <= loops; ++i) {
+    const bool fused = h->fused && !h->center && !qr && fused_sweep_applies(h, rq, rw, ld, dt, fwd_trans);
+    for (int i = 1; qr && i <= loops; ++i) {
+        // Basic randomized PCA: orth() after every product, G = orth(A Q),
+        // Q = orth(A^T G) (Alg. 4; Alg. 1 with A and A^T exchanged).
+        if ((st = spmm_pass(h, fwd_trans, l, Q, ld, W, ld, dt)) != FRPCA_OK) return st;
+        if ((st = orth_qr(h, rw, l, W, ld, dt, sm)) != FRPCA_OK) return st;
+        if ((st = spmm_pass(h, bwd_trans, l, W, ld, Q, ld, dt)) != FRPCA_OK) return st;
+        if ((st = orth_qr(h, rq, l, Q, ld, dt, sm)) != FRPCA_OK) return st;
+    }
+    for (int i = 1; !qr && i <= loops; ++i) {
         if (fused) {
             if ((st = fused_sweep(h, fwd_trans, l, Q, W, ld, rq, dt)) != FRPCA_OK) return st;
         } else {

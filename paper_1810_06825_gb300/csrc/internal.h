@@ -112,6 +112,11 @@ cudaError_t launch_col_means(const DeviceCSR &AT, int64_t m, double *mu, cudaStr
 cudaError_t launch_center_correction(int trans, int64_t m, int64_t n, int l, const double *mu, const void *X,
                                      int64_t ldx, void *Y, int64_t ldy, frpca_dtype dt, void *ws, cudaStream_t s);
 
+// ---- qr.cu: R (upper) with R^T R = B and W = R^{-1} in dt (l x l, ld l);
+// R and X are l x l double scratch; FRPCA_ERR_RANK_DEFICIENT on a bad pivot.
+cudaError_t launch_chol_inv(int l, const double *B, double *R, double *X, frpca_dtype dt, void *W, int *d_status,
+                            cudaStream_t s);
+
 // ---- gaussian.cu
 cudaError_t launch_gaussian(int64_t R, int l, int64_t ld, uint64_t seed, frpca_dtype dt, void *out,
                             cudaStream_t s);
