@@ -11,8 +11,6 @@
 // summed in segment order by a fix-up kernel, so the result is deterministic
 // and no float atomics are used.  The lists of whole rows and segments (the
 // plan) are built once per matrix, on the device.
-#include <cstdlib>
-#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -26,8 +24,9 @@ namespace {
 // warps resident (0.602 vs 0.650 ms per pass with 8-warp blocks).
 constexpr int kThreads = 64;
 constexpr int kDefaultSeg = 1024;
-// Blocks per SM the register allocation is sized for (occupancy of a
-// latency-bound gather loop).
+// Blocks per SM the register allocation is sized for: the gather loop is
+// latency-bound, and 18 two-warp blocks (56 registers, no spills) ran the
+// 12M x 320K passes in 108 ms per step against 119 ms with 16 (64 registers).
 #ifndef FRPCA_SPMM_MIN_BLOCKS
 #define FRPCA_SPMM_MIN_BLOCKS 18
 #endif
@@ -135,98 +134,6 @@ spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ coli
     }
 }
 
-// The same pass for FP32 blocks with l <= 128 (one float4 per lane), with the
-// gathered rows landing in a per-lane shared-memory ring by cp.async instead
-// of registers: 16 gathers stay in flight per warp (two groups of eight: the
-// next group is issued as soon as the previous one is consumed) at no register
-// cost.  A lane copies and later reads only its own 16-byte slots, so no
-// synchronization beyond its own cp.async groups is needed.  The sum runs in
-// CSR order, bit-identical with spmm_kernel.
-constexpr int kRing = 16;   // slots per lane
-constexpr int kGroup8 = 8;  // gathers per cp.async group
-
-__device__ inline void cp_async16(uint32_t dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ inline void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ inline void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-__global__ void __launch_bounds__(kThreads, FRPCA_SPMM_MIN_BLOCKS)
-spmm_ring_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx,
-                 const float *__restrict__ vals, const int32_t *__restrict__ short_rows, int64_t n_short,
-                 const int64_t *__restrict__ seg_start, const int32_t *__restrict__ seg_len, int64_t n_segs,
-                 int nvec, const float *__restrict__ X, int64_t ldx, float *__restrict__ Y, int64_t ldy,
-                 float *__restrict__ partial, int accumulate, int64_t out_row_offset) {
-    extern __shared__ float4 ring_all[];  // kThreads x kRing float4: slot s of thread t at [s * kThreads + t]
-    const int lane = threadIdx.x & 31;
-    const int64_t w = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
-    int64_t start;
-    int len;
-    float4 *out;
-    if (w < n_short) {
-        const int32_t row = short_rows[w];
-        start = rowptr[row];
-        len = (int)(rowptr[row + 1] - start);
-        out = reinterpret_cast<float4 *>(Y + ((int64_t)row - out_row_offset) * ldy);
-    } else if (w - n_short < n_segs) {
-        const int64_t sidx = w - n_short;
-        start = seg_start[sidx];
-        len = seg_len[sidx];
-        out = reinterpret_cast<float4 *>(partial + sidx * (int64_t)nvec * 4);
-    } else {
-        return;
-    }
-    const bool active = lane < nvec;
-    const float4 *Xv = reinterpret_cast<const float4 *>(X) + lane;
-    const int64_t ldxv = ldx / 4;
-    float4 *ring = ring_all + threadIdx.x;
-    const uint32_t ring_addr = (uint32_t)__cvta_generic_to_shared(ring);
-    float4 acc = (accumulate && w < n_short && active) ? out[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-
-    for (int base = 0; base < len; base += 32) {
-        const int cnt = min(32, len - base);
-        int32_t my_col = 0;
-        float my_val = 0.f;
-        if (lane < cnt) {
-            my_col = __ldg(colidx + start + base + lane);
-            my_val = __ldg(vals + start + base + lane);
-        }
-        const int ngroups = (cnt + kGroup8 - 1) / kGroup8;
-        // Group g (entries 8 g .. 8 g + 7) goes to slots 8 (g % 2) .. + 7.
-        auto issue = [&](int g) {
-#pragma unroll
-            for (int u = 0; u < kGroup8; ++u) {
-                const int t = g * kGroup8 + u;
-                const int32_t c = __shfl_sync(0xffffffffu, my_col, t & 31);
-                if (g < ngroups && t < cnt && active)
-                    cp_async16(ring_addr + (uint32_t)(((g & 1) * kGroup8 + u) * kThreads * 16), Xv + (int64_t)c * ldxv);
-            }
-            cp_async_commit();
-        };
-        issue(0);
-        issue(1);
-        for (int g = 0; g < ngroups; ++g) {
-            cp_async_wait1();  // every group but the newest is complete, so group g is
-#pragma unroll
-            for (int u = 0; u < kGroup8; ++u) {
-                const int t = g * kGroup8 + u;
-                const float v = __shfl_sync(0xffffffffu, my_val, t & 31);
-                if (t < cnt && active) {
-                    const float4 x = ring[((g & 1) * kGroup8 + u) * kThreads];
-                    acc.x = fmaf(v, x.x, acc.x);
-                    acc.y = fmaf(v, x.y, acc.y);
-                    acc.z = fmaf(v, x.z, acc.z);
-                    acc.w = fmaf(v, x.w, acc.w);
-                }
-            }
-            issue(g + 2);  // into the slots just read (empty past the chunk)
-        }
-        cp_async_wait0();
-    }
-    if (active) out[lane] = acc;
-}
-
 // partial holds the segments seg_base, seg_base + 1, ... (long_first values
 // are absolute segment indices); output row = long row - out_row_offset.
 template <typename T>
@@ -262,17 +169,6 @@ struct SpmmWork {
     int64_t out_row_offset;
 };
 
-// The cp.async-ring kernel is the default for FP32 blocks with l <= 128;
-// FRPCA_SPMM_RING=0 in the environment selects the register kernel (for
-// comparisons).
-bool use_ring_kernel() {
-    static const bool on = [] {
-        const char *e = getenv("FRPCA_SPMM_RING");
-        return !(e && e[0] == '0');
-    }();
-    return on;
-}
-
 SpmmWork whole_plan(const SpmmPlan &p) {
     return SpmmWork{p.short_rows, p.n_short, p.seg_start, p.seg_len, p.n_segs, 0, p.long_rows, p.long_first,
                     p.n_long, 0};
@@ -287,15 +183,6 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmWork &p, i
     const int64_t warps = p.n_short + p.n_segs;
     if (warps > 0) {
         const int64_t blocks = ceil_div(warps * 32, kThreads);
-        if (std::is_same<T, float>::value && nv == 1 && use_ring_kernel()) {
-            spmm_ring_kernel<<<(unsigned)blocks, kThreads, kThreads * kRing * 16, s>>>(
-                A.rowptr, A.colidx, (const float *)vals, p.short_rows, p.n_short, p.seg_start, p.seg_len, p.n_segs,
-                nvec, (const float *)X, ldx, (float *)Y, ldy, (float *)partial, accumulate, p.out_row_offset);
-            count_launch();
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-            goto fixup;
-        }
 #define FRPCA_SPMM_CASE(NVV)                                                                                  \
     case NVV:                                                                                                 \
         spmm_kernel<T, NVV><<<(unsigned)blocks, kThreads, 0, s>>>(A.rowptr, A.colidx, vals, p.short_rows,     \
@@ -315,7 +202,6 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmWork &p, i
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-fixup:
     if (p.n_long > 0) {
         spmm_fixup_kernel<T><<<(unsigned)ceil_div(p.n_long * 32, 256), 256, 0, s>>>(
             p.n_long, p.long_rows, p.long_first, nvec, partial, Y, ldy, accumulate, p.seg_base, p.out_row_offset);
