@@ -10,8 +10,8 @@
 // Every BF16 x BF16 product is exact in the FP32 accumulator; H^T H and the
 // corrections go to two separate TMEM accumulators, so the corrections'
 // rounding is relative to their own (2^-8 smaller) size.  A persistent CTA per
-// SM takes 128-row chunks of M: the chunk is split into one of two shared-
-// memory operand stages while the previous chunk's MMAs run, one thread issues
+// SM takes 128-row chunks of M: raw chunks arrive in shared memory by cp.async
+// two ahead, a chunk is split into the BF16 operand stage, one thread issues
 // 8 K-steps x 6 MMAs (M = N = 128, K = 16), and groups of 4 chunks accumulate
 // into one of two TMEM accumulator pairs.  A finished group's pair is read back
 // with tcgen05.ld during the next group's MMAs and added into the CTA's copy
@@ -41,59 +41,66 @@ using namespace tc;
 constexpr int kTcThreads = 256;
 constexpr int kTile = 128;                         // l padded to 128; rows per chunk
 constexpr int kOpBytes = kTile * kTile * 2;        // one BF16 operand, 32 KiB
-constexpr int kStages = 2;                         // operand stages (H, M, S splits of one chunk)
-constexpr int kStageBytes = 3 * kOpBytes;          // 96 KiB
+constexpr int kOpStage = 3 * kOpBytes;             // the H, M, S splits of one chunk: 96 KiB
+constexpr int kRawBytes = kTile * kTile * 4;       // one raw FP32 chunk (128 rows x 128 columns): 64 KiB
+constexpr int kRawStages = 2;                      // raw chunks in flight
 constexpr int kGroup = 4;                          // chunks accumulated in TMEM between drains (512 rows)
-constexpr int kSmemBytes = kStages * kStageBytes + 64;
+constexpr int kSmemBytes = kOpStage + kRawStages * kRawBytes + 64;
 constexpr uint32_t kTmemCols = 512;                // two pairs of 128-column FP32 accumulators
-// Thread t loads column group j4 = t % 32 (4 columns) of the 8-row groups
-// rg = t / 32 and rg + 8 of a chunk: 16 float4 loads, rows coalesced per warp.
-struct ChunkRegs {
-    float4 v[2][8];
-};
 
-__device__ inline void load_chunk(const float *__restrict__ M, int64_t ld, int64_t R, int l, int64_t row0,
-                                  ChunkRegs &c) {
+__device__ inline void cp_async16_zfill(uint32_t dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+// Thread t copies column group j4 = t % 32 (4 floats) of the 8-row groups
+// rg = t / 32 and rg + 8 of the chunk starting at row0 into raw (row-major,
+// 128 floats per row): 16 asynchronous 16-byte copies, the parts past row R
+// or column l zero-filled; one commit group per chunk.
+__device__ inline void fetch_chunk(const float *__restrict__ M, int64_t ld, int64_t R, int l, int64_t row0,
+                                   uint32_t raw) {
     const int t = threadIdx.x, j4 = t & 31, rg = t >> 5;
     const int j = j4 * 4;
+    const int valid = j < l ? min(4, l - j) : 0;
 #pragma unroll
     for (int g = 0; g < 2; ++g)
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const int64_t r = row0 + (rg + 8 * g) * 8 + u;
-            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r < R && j < l) x = __ldcs(reinterpret_cast<const float4 *>(M + r * ld + j));
-            if (j + 3 >= l) {  // columns l .. 127 are zero
-                if (j + 0 >= l) x.x = 0.f;
-                if (j + 1 >= l) x.y = 0.f;
-                if (j + 2 >= l) x.z = 0.f;
-                if (j + 3 >= l) x.w = 0.f;
-            }
-            c.v[g][u] = x;
+            const int rr = (rg + 8 * g) * 8 + u;
+            const int64_t r = row0 + rr;
+            const bool in = r < R && valid > 0;
+            cp_async16_zfill(raw + (uint32_t)(rr * kTile + j) * 4, in ? (const void *)(M + r * ld + j) : (const void *)M,
+                             in ? 4 * valid : 0);
         }
 }
 
-// Writes the three BF16 splits of the chunk held in registers: for each of
-// its 4 columns and 2 row groups a thread owns one full 16-byte core-matrix row.
-__device__ inline void store_chunk(const ChunkRegs &c, unsigned char *opH, unsigned char *opM, unsigned char *opS) {
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ inline void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ inline void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Splits the raw chunk into the three BF16 operands: for each of its 4 columns
+// and 2 row groups a thread writes one full 16-byte core-matrix row.
+__device__ inline void split_chunk(const float *__restrict__ raw, unsigned char *opH, unsigned char *opM,
+                                   unsigned char *opS) {
     const int t = threadIdx.x, j4 = t & 31, rg = t >> 5;
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
         const int r = (rg + 8 * g) * 8;
+        float4 x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = *reinterpret_cast<const float4 *>(raw + (r + u) * kTile + j4 * 4);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int j = j4 * 4 + e;
-            __align__(16) __nv_bfloat16 h[8], m[8], s[8];
+            __align__(16) __nv_bfloat16 h[8], m[8], sp[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const float4 x = c.v[g][u];
-                const float xv = e == 0 ? x.x : e == 1 ? x.y : e == 2 ? x.z : x.w;
-                split3(xv, h[u], m[u], s[u]);
+                const float xv = e == 0 ? x[u].x : e == 1 ? x[u].y : e == 2 ? x[u].z : x[u].w;
+                split3(xv, h[u], m[u], sp[u]);
             }
             const int off = op_offset(j, r);
             *reinterpret_cast<uint4 *>(opH + off) = *reinterpret_cast<const uint4 *>(h);
             *reinterpret_cast<uint4 *>(opM + off) = *reinterpret_cast<const uint4 *>(m);
-            *reinterpret_cast<uint4 *>(opS + off) = *reinterpret_cast<const uint4 *>(s);
+            *reinterpret_cast<uint4 *>(opS + off) = *reinterpret_cast<const uint4 *>(sp);
         }
     }
 }
@@ -154,25 +161,30 @@ __device__ inline void drain_pair(uint32_t tmem, int pair, float *__restrict__ a
 }
 
 // One CTA per SM, persistent over the 128-row chunks c = blockIdx.x + i G.
-// Chunk i is split into operand stage i % 2 while the MMAs of chunk i - 1 run
-// (the stage is reused once the commit of chunk i - 2 has arrived), and its
-// MMAs accumulate into TMEM pair (i / kGroup) % 2 (main and correction, 128
-// columns each; 512 columns in all).  When a group of kGroup chunks is
-// complete, its pair is drained into the CTA's double-float copy of B during
-// the next chunk's MMAs, so FP32 accumulation spans at most kGroup * 128 rows.
+// Raw chunks arrive by cp.async two ahead (raw stage i % 2) without holding
+// registers; once the MMAs of chunk i - 1 are done, chunk i is split into the
+// operand stage and its MMAs accumulate into TMEM pair (i / kGroup) % 2 (main
+// and correction, 128 columns each; 512 columns in all).  When a group of
+// kGroup chunks is complete, its pair is drained into the CTA's double-float
+// copy of B during the next chunk's MMAs, so FP32 accumulation spans at most
+// kGroup * 128 rows.  Chunk i's commit completes phase i of the one mbarrier;
+// each phase is waited on before the next commit is issued, so a parity wait
+// never meets a barrier two phases ahead.
 __global__ void __launch_bounds__(kTcThreads, 1)
 gram_tc_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, float *__restrict__ accws,
                double *__restrict__ partial, int *status, long long limit_cycles) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + kStages);
+    unsigned char *opH = smem, *opM = smem + kOpBytes, *opS = smem + 2 * kOpBytes;
+    float *raw = reinterpret_cast<float *>(smem + kOpStage);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + kOpStage + kRawStages * kRawBytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
     const int warp = threadIdx.x >> 5;
     float *acc_hi = accws + (size_t)blockIdx.x * 2 * kTile * kTile;
     float *acc_lo = acc_hi + kTile * kTile;
 
     if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
     if (threadIdx.x == 0) {
-        for (int st = 0; st < kStages; ++st) mbar_init(smem_u32(mbar + st), 1);
+        mbar_init(smem_u32(mbar), 1);
         fence_mbar_init();
     }
     for (int i = threadIdx.x; i < kTile * kTile / 4; i += kTcThreads) {
@@ -183,15 +195,20 @@ gram_tc_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, float 
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
+    const uint32_t raw_addr = smem_u32(raw);
 
     const int64_t nchunks = ceil_div(R, kTile);
     const int64_t G = gridDim.x;
     const int64_t nmine = nchunks > blockIdx.x ? (nchunks - blockIdx.x + G - 1) / G : 0;
-    ChunkRegs regs;
-    if (nmine > 0) load_chunk(M, ld, R, l, (int64_t)blockIdx.x * kTile, regs);
-    // Waits for the commit of local chunk j (stage j % 2, its (j / 2)-th use).
+    auto row_of_chunk = [&](int64_t i) { return ((int64_t)blockIdx.x + i * G) * kTile; };
+    // Two chunks in flight from the start (an empty group when there is none).
+    for (int64_t i = 0; i < 2; ++i) {
+        if (i < nmine) fetch_chunk(M, ld, R, l, row_of_chunk(i), raw_addr + (uint32_t)(i * kRawBytes));
+        cp_async_commit();
+    }
+    // Waits for the commit of local chunk j (phase j of the barrier).
     auto wait_commit = [&](int64_t j) -> bool {
-        const bool done = mbar_wait_bounded(smem_u32(mbar + (j & 1)), (uint32_t)((j >> 1) & 1), limit_cycles);
+        const bool done = mbar_wait_bounded(smem_u32(mbar), (uint32_t)(j & 1), limit_cycles);
         const bool all = __syncthreads_and(done) != 0;
         fence_after();
         return all;
@@ -201,9 +218,10 @@ gram_tc_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, float 
     int64_t issued = -1;   // last chunk whose MMAs were issued
     for (int64_t i = 0; i < nmine && ok; ++i) {
         const int st = (int)(i & 1);
-        unsigned char *opH = smem + st * kStageBytes, *opM = opH + kOpBytes, *opS = opM + kOpBytes;
-        if (i >= 2 && !(ok = wait_commit(i - 2))) break;
-        store_chunk(regs, opH, opM, opS);
+        cp_async_wait1();  // chunk i has landed (chunk i + 1 may still be in flight)
+        __syncthreads();
+        if (i >= 1 && !(ok = wait_commit(i - 1))) break;  // the operand stage is free
+        split_chunk(raw + st * (kRawBytes / 4), opH, opM, opS);
         fence_async_smem();
         fence_before();
         __syncthreads();
@@ -219,13 +237,15 @@ gram_tc_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, float 
                 const uint64_t h = make_desc(aH + koff), m = make_desc(aM + koff), sd = make_desc(aS + koff);
                 mma_split6(d_main, d_corr, h, m, sd, h, m, sd, !(first && ks == 0));
             }
-            mma_commit(smem_u32(mbar + st));
+            mma_commit(smem_u32(mbar));
         }
         issued = i;
-        // Prefetch the next chunk while the tensor cores run.
-        if (i + 1 < nmine) load_chunk(M, ld, R, l, (blockIdx.x + (i + 1) * G) * kTile, regs);
+        // Raw stage st has been split: chunk i + 2 goes there.
+        if (i + 2 < nmine) fetch_chunk(M, ld, R, l, row_of_chunk(i + 2), raw_addr + (uint32_t)(st * kRawBytes));
+        cp_async_commit();
+        // The previous group's pair (its MMAs are done: chunk i - 1 was waited
+        // on above) is drained while this chunk's MMAs run.
         if (pending >= 0) {
-            if (!(ok = wait_commit(pending))) break;
             drain_pair(tmem, (int)((pending / kGroup) & 1), acc_hi, acc_lo);
             fence_before();
             pending = -1;
@@ -233,7 +253,7 @@ gram_tc_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, float 
         if (i % kGroup == kGroup - 1) pending = i;
     }
     if (ok && issued >= 0) {
-        // The last group (complete or not) and any pending one.
+        // The last group (complete or not) and a pending one.
         if ((ok = wait_commit(issued))) {
             if (pending >= 0 && pending != issued) drain_pair(tmem, (int)((pending / kGroup) & 1), acc_hi, acc_lo);
             drain_pair(tmem, (int)((issued / kGroup) & 1), acc_hi, acc_lo);
@@ -242,8 +262,9 @@ gram_tc_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, float 
     } else if (!ok && issued >= 0) {
         // A wait ran out: give the MMAs already issued a bounded chance to
         // finish before the TMEM is released.
-        (void)mbar_wait_bounded(smem_u32(mbar + (issued & 1)), (uint32_t)((issued >> 1) & 1), limit_cycles);
+        (void)mbar_wait_bounded(smem_u32(mbar), (uint32_t)(issued & 1), limit_cycles);
     }
+    cp_async_wait0();
     if (!ok && threadIdx.x == 0) set_status(status, FRPCA_ERR_TIMEOUT);
     __syncthreads();
     // This CTA's partial B (l x l) in FP64, written even when it had no chunk.
