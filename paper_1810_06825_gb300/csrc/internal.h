@@ -37,6 +37,8 @@ struct SpmmPlan {
     int64_t n_segs = 0;           // segments of long rows
     int64_t n_long = 0;           // long rows
     int32_t *short_rows = nullptr;
+    int64_t *short_start = nullptr; // first entry and length of each whole row (read with the
+    int32_t *short_len = nullptr;   // row id, so the row's entries are one load away)
     int64_t *seg_start = nullptr; // first entry of each segment
     int32_t *seg_len = nullptr;
     int32_t *long_rows = nullptr; // row of each long row

@@ -34,7 +34,8 @@ constexpr int kDefaultSeg = 1024;
 template <typename T, int NV>
 __global__ void __launch_bounds__(kThreads, FRPCA_SPMM_MIN_BLOCKS)
 spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, const T *__restrict__ vals,
-            const int32_t *__restrict__ short_rows, int64_t n_short, const int64_t *__restrict__ seg_start,
+            const int32_t *__restrict__ short_rows, const int64_t *__restrict__ short_start,
+            const int32_t *__restrict__ short_len, int64_t n_short, const int64_t *__restrict__ seg_start,
             const int32_t *__restrict__ seg_len, int64_t n_segs, int nvec, const T *__restrict__ X, int64_t ldx,
             T *__restrict__ Y, int64_t ldy, T *__restrict__ partial, int accumulate, int64_t out_row_offset) {
     using V = typename Vec<T>::type;
@@ -46,8 +47,8 @@ spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ coli
     V *out;
     if (w < n_short) {
         const int32_t row = short_rows[w];
-        start = rowptr[row];
-        len = (int)(rowptr[row + 1] - start);
+        start = short_start[w];
+        len = short_len[w];
         out = reinterpret_cast<V *>(Y + ((int64_t)row - out_row_offset) * ldy);
     } else if (w - n_short < n_segs) {
         const int64_t sidx = w - n_short;
@@ -159,6 +160,8 @@ __global__ void spmm_fixup_kernel(int64_t n_long, const int32_t *__restrict__ lo
 // of long rows, long rows for the fix-up).
 struct SpmmWork {
     const int32_t *short_rows;
+    const int64_t *short_start;
+    const int32_t *short_len;
     int64_t n_short;
     const int64_t *seg_start;
     const int32_t *seg_len;
@@ -170,8 +173,8 @@ struct SpmmWork {
 };
 
 SpmmWork whole_plan(const SpmmPlan &p) {
-    return SpmmWork{p.short_rows, p.n_short, p.seg_start, p.seg_len, p.n_segs, 0, p.long_rows, p.long_first,
-                    p.n_long, 0};
+    return SpmmWork{p.short_rows, p.short_start, p.short_len, p.n_short, p.seg_start, p.seg_len, p.n_segs, 0,
+                    p.long_rows, p.long_first, p.n_long, 0};
 }
 
 template <typename T>
@@ -186,6 +189,7 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmWork &p, i
 #define FRPCA_SPMM_CASE(NVV)                                                                                  \
     case NVV:                                                                                                 \
         spmm_kernel<T, NVV><<<(unsigned)blocks, kThreads, 0, s>>>(A.rowptr, A.colidx, vals, p.short_rows,     \
+                                                                  p.short_start, p.short_len,                 \
                                                                   p.n_short, p.seg_start, p.seg_len,          \
                                                                   p.n_segs, nvec, X, ldx, Y, ldy, partial,    \
                                                                   accumulate, p.out_row_offset);              \
@@ -215,6 +219,8 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmWork &p, i
 
 void SpmmPlan::free_all() {
     dev_free(short_rows, stream);
+    dev_free(short_start, stream);
+    dev_free(short_len, stream);
     dev_free(seg_start, stream);
     dev_free(seg_len, stream);
     dev_free(long_rows, stream);
@@ -222,6 +228,8 @@ void SpmmPlan::free_all() {
     if (budget) budget->give(charged);
     charged = 0;
     short_rows = nullptr;
+    short_start = nullptr;
+    short_len = nullptr;
     seg_start = nullptr;
     seg_len = nullptr;
     long_rows = nullptr;
@@ -241,7 +249,8 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
         err = "spmm plan: reading row pointers failed";
         return e;
     }
-    std::vector<int32_t> shorts, lrows, slen;
+    std::vector<int32_t> shorts, lrows, slen, shlen;
+    std::vector<int64_t> shstart;
     std::vector<int64_t> sstart, lfirst;
     shorts.reserve((size_t)A.rows);
     for (int64_t i = 0; i < A.rows; ++i) {
@@ -249,6 +258,8 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
         const int64_t len = rp[i + 1] - rp[i];
         if (len <= plan.seg) {
             shorts.push_back((int32_t)i);
+            shstart.push_back(rp[i]);
+            shlen.push_back((int32_t)len);
         } else {
             lrows.push_back((int32_t)i);
             lfirst.push_back((int64_t)sstart.size());
@@ -270,6 +281,8 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
         return cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s);
     };
     if ((e = up((void **)&plan.short_rows, shorts.data(), 4 * shorts.size())) != cudaSuccess ||
+        (e = up((void **)&plan.short_start, shstart.data(), 8 * shstart.size())) != cudaSuccess ||
+        (e = up((void **)&plan.short_len, shlen.data(), 4 * shlen.size())) != cudaSuccess ||
         (e = up((void **)&plan.long_rows, lrows.data(), 4 * lrows.size())) != cudaSuccess ||
         (e = up((void **)&plan.long_first, lfirst.data(), 8 * lfirst.size())) != cudaSuccess ||
         (e = up((void **)&plan.seg_start, sstart.data(), 8 * sstart.size())) != cudaSuccess ||
@@ -302,13 +315,17 @@ __global__ void plan_fill_kernel(int64_t m, const int64_t *__restrict__ rowptr, 
                                  const int32_t *__restrict__ is_short, const int32_t *__restrict__ is_long,
                                  const int64_t *__restrict__ short_pos, const int64_t *__restrict__ long_pos,
                                  const int64_t *__restrict__ seg_off, int32_t *__restrict__ short_rows,
+                                 int64_t *__restrict__ short_start, int32_t *__restrict__ short_len,
                                  int32_t *__restrict__ long_rows, int64_t *__restrict__ long_first,
                                  int64_t *__restrict__ seg_start, int32_t *__restrict__ seg_len) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i == 0) long_first[long_pos[m]] = seg_off[m];
     if (i >= m) return;
     if (is_short[i]) {
-        short_rows[short_pos[i]] = (int32_t)i;
+        const int64_t pos = short_pos[i];
+        short_rows[pos] = (int32_t)i;
+        short_start[pos] = rowptr[i];
+        short_len[pos] = (int32_t)(rowptr[i + 1] - rowptr[i]);
         return;
     }
     if (!is_long[i]) return;  // an empty row left out
@@ -416,6 +433,8 @@ cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *cons
             return r;
         };
         if ((e = alloc((void **)&plan.short_rows, 4 * (size_t)plan.n_short)) != cudaSuccess ||
+            (e = alloc((void **)&plan.short_start, 8 * (size_t)plan.n_short)) != cudaSuccess ||
+            (e = alloc((void **)&plan.short_len, 4 * (size_t)plan.n_short)) != cudaSuccess ||
             (e = alloc((void **)&plan.long_rows, 4 * (size_t)plan.n_long)) != cudaSuccess ||
             (e = alloc((void **)&plan.long_first, 8 * ((size_t)plan.n_long + 1))) != cudaSuccess ||
             (e = alloc((void **)&plan.seg_start, 8 * (size_t)plan.n_segs)) != cudaSuccess ||
@@ -426,7 +445,7 @@ cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *cons
         const Parts q = parts(c);
         plan_fill_kernel<<<(unsigned)ceil_div(A.rows, 256), 256, 0, s>>>(
             A.rows, A.rowptr, kDefaultSeg, q.is_short, q.is_long, q.short_pos, q.long_pos, q.seg_off, plan.short_rows,
-            plan.long_rows, plan.long_first, plan.seg_start, plan.seg_len);
+            plan.short_start, plan.short_len, plan.long_rows, plan.long_first, plan.seg_start, plan.seg_len);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) {
             err = "spmm plan: fill failed";
@@ -508,7 +527,8 @@ cudaError_t panel_launch(const PanelCSR &pc, int64_t b, int l, const void *Xb, i
     const int64_t l0 = pc.long_off[b], l1 = pc.long_off[b + 1];
     const int64_t g0 = pc.seg_off[b], g1 = pc.seg_off[b + 1];
     if (s1 == s0 && l1 == l0) return cudaSuccess;
-    const SpmmWork w{p.short_rows + s0, s1 - s0, p.seg_start + g0, p.seg_len + g0, g1 - g0, g0,
+    const SpmmWork w{p.short_rows + s0, p.short_start + s0, p.short_len + s0, s1 - s0, p.seg_start + g0,
+                     p.seg_len + g0, g1 - g0, g0,
                      p.long_rows + l0, p.long_first + l0, l1 - l0, b * pc.src_rows};
     if (dt == FRPCA_F32)
         return launch_typed<float>(pc.virt, (const float *)pc.virt.vals, w, l, (const float *)Xb, ldx, (float *)Y,
@@ -549,7 +569,8 @@ cudaError_t launch_fused_sweep(const DeviceCSR &Pm, const SpmmPlan &prod, const 
         const int64_t s0 = pc.prod_short_off[b], s1 = pc.prod_short_off[b + 1];
         const int64_t l0 = pc.prod_long_off[b], l1 = pc.prod_long_off[b + 1];
         const int64_t g0 = pc.prod_seg_off[b], g1 = pc.prod_seg_off[b + 1];
-        const SpmmWork w{prod.short_rows + s0, s1 - s0, prod.seg_start + g0, prod.seg_len + g0, g1 - g0, g0,
+        const SpmmWork w{prod.short_rows + s0, prod.short_start + s0, prod.short_len + s0, s1 - s0,
+                         prod.seg_start + g0, prod.seg_len + g0, g1 - g0, g0,
                          prod.long_rows + l0, prod.long_first + l0, l1 - l0, b * pc.panel_rows};
         if (dt == FRPCA_F32)
             e = launch_typed<float>(Pm, (const float *)Pm.vals, w, l, (const float *)Q, ldq, (float *)slot, ldr,
