@@ -126,8 +126,15 @@ typedef struct frpca_create_opts {
  * Synchronizes the stream. */
 frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, frpca_handle *out);
 
-/* Frees every device buffer the handle owns.  Accepts NULL. */
+/* Frees every device buffer the handle owns.  Accepts NULL.  The memory goes
+ * back to this library's own stream-ordered pool on the device, which keeps
+ * up to 64 GiB of freed blocks mapped for the next handle (so a create after
+ * a destroy maps nothing new); frpca_trim_memory returns them. */
 frpca_status frpca_destroy(frpca_handle h);
+
+/* Returns the unused memory that the library's pool on the current device
+ * keeps mapped (handles still alive keep theirs).  Synchronizes the device. */
+frpca_status frpca_trim_memory(void);
 
 /* Message of the last failure on h (h == NULL: the calling thread's last
  * failure of frpca_create).  Valid until the next call on the same handle. */

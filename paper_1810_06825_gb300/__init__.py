@@ -30,6 +30,7 @@ EXPORTED = [
     "frpca_refresh", "frpca_set_timing", "frpca_get_stats", "frpca_reset_stats",
     "frpca_gaussian", "frpca_spmm", "frpca_get_transpose", "frpca_lu", "frpca_gram", "frpca_eig",
     "frpca_eigsvd", "frpca_backward", "frpca_gram_splitbf16", "frpca_lu_tournament", "frpca_set_wait_limit",
+    "frpca_trim_memory",
 ]
 
 
@@ -93,6 +94,7 @@ def library() -> ctypes.CDLL:
         "frpca_get_stats": [P, P],
         "frpca_reset_stats": [P],
         "frpca_set_wait_limit": [P, I64],
+        "frpca_trim_memory": [],
         "frpca_gaussian": [P, I64, I, I64, U64, I, P],
         "frpca_spmm": [P, I, I, P, I64, P, I64, I],
         "frpca_get_transpose": [P, P, P, P],
@@ -166,6 +168,11 @@ def frpca_get_stats(h) -> frpca_stats:
 
 def frpca_reset_stats(h) -> None:
     _check(library().frpca_reset_stats(h), h)
+
+
+def frpca_trim_memory() -> None:
+    """Give back the device memory the library's pool keeps for later handles."""
+    _check(library().frpca_trim_memory(), None)
 
 
 def frpca_set_wait_limit(h, cycles: int) -> None:

@@ -756,6 +756,14 @@ frpca_status frpca_set_timing(frpca_handle h, int enable) {
     return FRPCA_OK;
 }
 
+frpca_status frpca_trim_memory(void) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = trim_library_pool(dev);
+    if (e != cudaSuccess) return fail(nullptr, FRPCA_ERR_CUDA, std::string("trim: ") + cudaGetErrorString(e));
+    return FRPCA_OK;
+}
+
 frpca_status frpca_set_wait_limit(frpca_handle h, int64_t cycles) {
     if (!h) return FRPCA_ERR_INVALID_ARG;
     h->wait_limit = cycles > 0 ? (long long)cycles : kBarrierLimitCycles;

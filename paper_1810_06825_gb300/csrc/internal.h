@@ -62,10 +62,12 @@ struct MemBudget {
 
 // Device memory from this library's own stream-ordered pool on the current
 // device (not the device's default pool, whose attributes belong to the
-// process), on the stream of its owner: up to 8 GiB of freed blocks stay cached
-// in the pool, so creating and destroying handles neither maps memory again
-// nor synchronizes the device.  bytes are charged to budget when given.
+// process), on the stream of its owner: up to 64 GiB of freed blocks stay
+// cached in the pool, so creating and destroying handles neither maps memory
+// again nor synchronizes the device.  bytes are charged to budget when given.
 cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t s, MemBudget *budget = nullptr);
+// Returns the pool's unused mapped memory on device dev to the system.
+cudaError_t trim_library_pool(int dev);
 void dev_free(void *p, cudaStream_t s, MemBudget *budget = nullptr, size_t bytes = 0);
 
 // Grow-only device buffer.

@@ -161,3 +161,22 @@ def test_bounded_waits_time_out_then_recover():
     mat.set_wait_limit(0)
     _check_against_oracle(mat, A64.astype(np.float32), "fp32")
     mat.close()
+
+
+def test_trim_memory_returns_the_pool():
+    """A destroyed handle's memory stays mapped in the library's pool for the
+    next handle; frpca_trim_memory gives it back to the device."""
+    A = synthetic.powerlaw_csr(200_000, 50_000, 20, 1.1, "tfidf", seed=2, dtype=np.float32)
+    mat = frpca.FrPCA.from_csr(A, device=DEV)
+    mat.run(10, 24, 3, seed=1, precision="fp32")
+    mat.close()
+    torch.cuda.synchronize()
+    free_kept, _ = torch.cuda.mem_get_info()
+    frpca.frpca_trim_memory()
+    free_trimmed, _ = torch.cuda.mem_get_info()
+    assert free_trimmed > free_kept
+    # A handle created after the trim works as before.
+    mat = frpca.FrPCA.from_csr(A, device=DEV)
+    U, S, V = mat.run(10, 24, 3, seed=1, precision="fp32")
+    assert torch.all(S > 0)
+    mat.close()
