@@ -11,8 +11,6 @@
 // summed in segment order by a fix-up kernel, so the result is deterministic
 // and no float atomics are used.  The lists of whole rows and segments (the
 // plan) are built once per matrix, on the device.
-#include <cstdlib>
-#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -137,84 +135,6 @@ spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ coli
     }
 }
 
-// Whole rows of FP32 blocks with l <= 128, two rows per warp: half-warp h
-// (lanes 16 h .. 16 h + 15) owns row 2 w + h, each of its lanes the float4
-// vectors lane16 and lane16 + 16 of the row.  Both rows' index loads, gathers
-// and stores proceed side by side, so the warp keeps two rows' latency chains
-// in flight; each row is still summed in CSR order (bit-identical with
-// spmm_kernel).  Four entries of each row are gathered per step.
-__global__ void __launch_bounds__(kThreads, FRPCA_SPMM_MIN_BLOCKS)
-spmm_pair_kernel(const int64_t *__restrict__ colidx_start_unused, const int32_t *__restrict__ colidx,
-                 const float *__restrict__ vals, const int32_t *__restrict__ short_rows,
-                 const int64_t *__restrict__ short_start, const int32_t *__restrict__ short_len, int64_t n_short,
-                 int nvec, const float *__restrict__ X, int64_t ldx, float *__restrict__ Y, int64_t ldy,
-                 int accumulate, int64_t out_row_offset) {
-    (void)colidx_start_unused;
-    const int lane = threadIdx.x & 31, half = lane >> 4, l16 = lane & 15;
-    const int64_t w = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
-    const int64_t r = 2 * w + half;
-    if (2 * w >= n_short) return;  // both halves out of range: the whole warp leaves
-    const bool has = r < n_short;
-    int64_t start = 0;
-    int len = 0;
-    float4 *out = nullptr;
-    if (has) {
-        start = short_start[r];
-        len = short_len[r];
-        out = reinterpret_cast<float4 *>(Y + ((int64_t)short_rows[r] - out_row_offset) * ldy);
-    }
-    const float4 *Xv = reinterpret_cast<const float4 *>(X);
-    const int64_t ldxv = ldx / 4;
-    const bool a0 = has && l16 < nvec, a1 = has && l16 + 16 < nvec;
-    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
-    if (accumulate) {
-        if (a0) acc0 = out[l16];
-        if (a1) acc1 = out[l16 + 16];
-    }
-    const int other = __shfl_xor_sync(0xffffffffu, len, 16);
-    const int steps = max(len, other);  // the loop runs for the longer of the two rows
-    for (int base = 0; base < steps; base += 16) {
-        const int cnt = min(16, len - base);  // <= 0 once this half's row is done
-        int32_t my_col = 0;
-        float my_val = 0.f;
-        if (l16 < cnt) {
-            my_col = __ldg(colidx + start + base + l16);
-            my_val = __ldg(vals + start + base + l16);
-        }
-        for (int t0 = 0; t0 < 16 && base + t0 < steps; t0 += 4) {
-            int32_t c[4];
-            float v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                c[u] = __shfl_sync(0xffffffffu, my_col, t0 + u, 16);
-                v[u] = __shfl_sync(0xffffffffu, my_val, t0 + u, 16);
-            }
-            float4 x0[4], x1[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const bool ok = t0 + u < cnt;
-                x0[u] = (ok && a0) ? __ldg(Xv + (int64_t)c[u] * ldxv + l16) : make_float4(0.f, 0.f, 0.f, 0.f);
-                x1[u] = (ok && a1) ? __ldg(Xv + (int64_t)c[u] * ldxv + l16 + 16) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (t0 + u < cnt) {
-                    acc0.x = fmaf(v[u], x0[u].x, acc0.x);
-                    acc0.y = fmaf(v[u], x0[u].y, acc0.y);
-                    acc0.z = fmaf(v[u], x0[u].z, acc0.z);
-                    acc0.w = fmaf(v[u], x0[u].w, acc0.w);
-                    acc1.x = fmaf(v[u], x1[u].x, acc1.x);
-                    acc1.y = fmaf(v[u], x1[u].y, acc1.y);
-                    acc1.z = fmaf(v[u], x1[u].z, acc1.z);
-                    acc1.w = fmaf(v[u], x1[u].w, acc1.w);
-                }
-            }
-        }
-    }
-    if (a0) out[l16] = acc0;
-    if (a1) out[l16 + 16] = acc1;
-}
-
 // partial holds the segments seg_base, seg_base + 1, ... (long_first values
 // are absolute segment indices); output row = long row - out_row_offset.
 template <typename T>
@@ -252,16 +172,6 @@ struct SpmmWork {
     int64_t out_row_offset;
 };
 
-// Two whole rows per warp for FP32 blocks with l <= 128 (spmm_pair_kernel);
-// FRPCA_SPMM_PAIR=0 in the environment keeps one row per warp.
-bool pair_rows_enabled() {
-    static const bool on = [] {
-        const char *e = getenv("FRPCA_SPMM_PAIR");
-        return !(e && e[0] == '0');
-    }();
-    return on;
-}
-
 SpmmWork whole_plan(const SpmmPlan &p) {
     return SpmmWork{p.short_rows, p.short_start, p.short_len, p.n_short, p.seg_start, p.seg_len, p.n_segs, 0,
                     p.long_rows, p.long_first, p.n_long, 0};
@@ -276,24 +186,6 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmWork &p, i
     const int64_t warps = p.n_short + p.n_segs;
     if (warps > 0) {
         const int64_t blocks = ceil_div(warps * 32, kThreads);
-        if (std::is_same<T, float>::value && nv == 1 && pair_rows_enabled()) {
-            // Whole rows two per warp; segments of long rows one per warp.
-            if (p.n_short > 0) {
-                spmm_pair_kernel<<<(unsigned)ceil_div(ceil_div(p.n_short, 2) * 32, kThreads), kThreads, 0, s>>>(
-                    A.rowptr, A.colidx, (const float *)vals, p.short_rows, p.short_start, p.short_len, p.n_short,
-                    nvec, (const float *)X, ldx, (float *)Y, ldy, accumulate, p.out_row_offset);
-                count_launch();
-            }
-            if (p.n_segs > 0) {
-                spmm_kernel<float, 1><<<(unsigned)ceil_div(p.n_segs * 32, kThreads), kThreads, 0, s>>>(
-                    A.rowptr, A.colidx, (const float *)vals, nullptr, nullptr, nullptr, 0, p.seg_start, p.seg_len,
-                    p.n_segs, nvec, (const float *)X, ldx, (float *)Y, ldy, (float *)partial, accumulate,
-                    p.out_row_offset);
-                count_launch();
-            }
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-        } else {
 #define FRPCA_SPMM_CASE(NVV)                                                                                  \
     case NVV:                                                                                                 \
         spmm_kernel<T, NVV><<<(unsigned)blocks, kThreads, 0, s>>>(A.rowptr, A.colidx, vals, p.short_rows,     \
@@ -313,7 +205,6 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmWork &p, i
 #undef FRPCA_SPMM_CASE
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        }
     }
     if (p.n_long > 0) {
         spmm_fixup_kernel<T><<<(unsigned)ceil_div(p.n_long * 32, 256), 256, 0, s>>>(
