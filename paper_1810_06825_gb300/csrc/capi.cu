@@ -651,9 +651,15 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
     if ((e = csr_transpose(h->A, h->AT, (int32_t *)h->t_perm.ptr, h->ws_scratch, h->ws_scan, h->stream)) != cudaSuccess)
         return bail(cuda_fail(h, e, "transpose"));
     std::string perr;
+    // Rows of the larger dense block per panel of the gathering pass.
+    const int pr = opts ? opts->panel_rows : 0;
+    const int64_t P = pr > 0 ? (int64_t)pr : (int64_t)131072;
     {
         const DeviceCSR *mats[2] = {&h->A, &h->AT};
         SpmmPlan *plans[2] = {&h->planA, &h->planAT};
+        // Groups end at panel boundaries, so the fused sweep can run the
+        // producing pass one panel at a time.
+        for (SpmmPlan *p : plans) p->group_stride = P;
         if ((e = build_spmm_plans_device(mats, plans, 2, h->ws_plan, h->ws_scan, h->stream, perr)) != cudaSuccess)
             return bail(cuda_fail(h, e, perr.c_str()));
     }
@@ -661,8 +667,6 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
         // Panels over the rows of the larger dense block when it is well
         // beyond L2: 131,072 rows (64 MiB of float rows at l <= 128) each.
         const int64_t big = std::max(m, n);
-        const int pr = opts ? opts->panel_rows : 0;
-        const int64_t P = pr > 0 ? (int64_t)pr : (int64_t)131072;
         h->fused = opts && opts->fused_sweep > 0;
         h->pan_trans = m >= n ? 1 : 0;
         const DeviceCSR &C = m >= n ? h->AT : h->A;

@@ -26,6 +26,12 @@ template <> struct Vec<float> {
     __device__ static inline void add(float4 &acc, const float4 &x) {
         acc.x += x.x; acc.y += x.y; acc.z += x.z; acc.w += x.w;
     }
+    // *p += x as one vector reduction in L2 (result unused).
+    __device__ static inline void red_add(float4 *p, const float4 &x) {
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x.x), "f"(x.y), "f"(x.z),
+                     "f"(x.w)
+                     : "memory");
+    }
 };
 template <> struct Vec<double> {
     using type = double2;
@@ -37,6 +43,10 @@ template <> struct Vec<double> {
     }
     __device__ static inline void add(double2 &acc, const double2 &x) {
         acc.x += x.x; acc.y += x.y;
+    }
+    __device__ static inline void red_add(double2 *p, const double2 &x) {
+        asm volatile("red.global.add.f64 [%0], %1;" ::"l"(&p->x), "d"(x.x) : "memory");
+        asm volatile("red.global.add.f64 [%0], %1;" ::"l"(&p->y), "d"(x.y) : "memory");
     }
 };
 

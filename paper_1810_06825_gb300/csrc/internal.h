@@ -28,12 +28,15 @@ struct DeviceCSR {
 };
 
 // Work split of one SpMM over a CSR.  Rows with at most `seg` entries are
-// handled whole by one warp (list `short_rows`); longer rows are cut into
-// segments of `seg` entries whose partial rows go to scratch and are summed
-// in segment order by a fix-up pass.
+// handled whole (list `short_rows`), in groups of consecutive list entries,
+// one warp per group; longer rows are cut into segments of `seg` entries
+// whose partial rows go to scratch and are summed in segment order by a
+// fix-up pass.
 struct SpmmPlan {
     int seg = 0;
     int64_t n_short = 0;          // rows handled whole
+    int64_t n_groups = 0;         // groups of whole rows
+    int64_t *group_first = nullptr; // first list entry of each group (n_groups + 1 entries, the last n_short)
     int64_t n_segs = 0;           // segments of long rows
     int64_t n_long = 0;           // long rows
     int32_t *short_rows = nullptr;
@@ -47,6 +50,7 @@ struct SpmmPlan {
     MemBudget *budget = nullptr;    // allocation cap the arrays are charged to
     size_t charged = 0;             // bytes charged to budget
     bool skip_empty = false;        // leave empty rows out (their output rows are not written)
+    int64_t group_stride = 0;       // no group holds rows r, r' with r / stride != r' / stride (0: no limit)
     void free_all();
 };
 
@@ -96,12 +100,12 @@ struct PanelCSR {
     SpmmPlan plan;            // over virt, empty virtual rows left out
     // per panel b (npanels + 1 entries): first short row, first long row and
     // first segment of the plan that belong to panel b
-    std::vector<int64_t> short_off, long_off, seg_off;
+    std::vector<int64_t> short_off, long_off, seg_off, group_off;
     int64_t max_panel_segs = 0;
     // The same per-panel offsets into the plan of the product that writes the
     // gathered block (A X for A^T panels, rows b P .. b P + P-1 of panel b),
     // for the fused sweep; empty when not built.
-    std::vector<int64_t> prod_short_off, prod_long_off, prod_seg_off;
+    std::vector<int64_t> prod_short_off, prod_long_off, prod_seg_off, prod_group_off;
     int64_t prod_max_segs = 0;
     DevBuf b_rowptr, b_colidx, b_vals, b_perm;  // perm: entry of A at each position of virt
     bool active() const { return npanels > 0; }

@@ -2,15 +2,18 @@
 // (A*Q and A^T*G; Sec. 3.3 counts the method's cost in these passes, q of
 // them, each C_mul * nnz(A) * l flops).
 //
-// Y(rows x l) = A X with A in CSR and X, Y row-major.  A warp owns one output
-// row (or one segment of a long row): each lane owns 16-byte vectors of the
-// l-wide row (lane, lane + 32, ...), the warp reads 32 (column, value) pairs
-// coalesced, broadcasts them with shuffles and gathers the X rows as 16-byte
-// loads through the read-only path, accumulating in registers in CSR order.
-// Rows longer than `seg` entries are cut into segments whose partial rows are
+// Y(rows x l) = A X with A in CSR and X, Y row-major.  A warp takes a group of
+// consecutive rows (or one segment of a long row): each lane owns 16-byte
+// vectors of the l-wide rows (lane, lane + 32, ...), the warp reads 32
+// (column, value) pairs of the group's entries at a time, coalesced,
+// broadcasts them with shuffles and gathers the X rows as 16-byte loads
+// through the read-only path, accumulating in registers in CSR order.  Rows
+// longer than `seg` entries are cut into segments whose partial rows are
 // summed in segment order by a fix-up kernel, so the result is deterministic
-// and no float atomics are used.  The lists of whole rows and segments (the
-// plan) are built once per matrix, on the device.
+// and no float atomics are used.  The work lists (the plan) are built once
+// per matrix, on the device.
+#include <climits>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -19,120 +22,241 @@
 namespace frpca {
 namespace {
 
-// Two warps per block: a warp owns a row of log-normal length, and a block's
-// slot frees only when its longest row is done, so small blocks keep more
-// warps resident (0.602 vs 0.650 ms per pass with 8-warp blocks).
+// Two warps per block: a block's slot frees only when both of its warps are
+// done, so small blocks keep more warps resident (0.602 vs 0.650 ms per pass
+// with 8-warp blocks).
 constexpr int kThreads = 64;
 constexpr int kDefaultSeg = 1024;
-// Blocks per SM the register allocation is sized for: the gather loop is
-// latency-bound, and 18 two-warp blocks (56 registers, no spills) ran the
-// 12M x 320K passes in 108 ms per step against 119 ms with 16 (64 registers).
+// The gather loop is latency-bound: resident warps (blocks per SM, which size
+// the register allocation: 65,536 / (64 x blocks) registers per thread) are
+// traded against the entries whose gathers a warp issues together (the
+// batch, l <= 128 in FP32; fewer for wider rows, the same bytes in flight).
+// On the 12M x 320K power-law passes the writing kernel ran best with 22
+// blocks of batch 4 (the A X pass: 41.8 vs 44.1 ms for three passes with 18
+// blocks of batch 8) and the accumulating one with 18 blocks of batch 8 (the
+// panel passes: 50.5 vs 51.8 ms for two).
 #ifndef FRPCA_SPMM_MIN_BLOCKS
-#define FRPCA_SPMM_MIN_BLOCKS 18
+#define FRPCA_SPMM_MIN_BLOCKS 22
 #endif
+#ifndef FRPCA_SPMM_BATCH
+#define FRPCA_SPMM_BATCH 4
+#endif
+#ifndef FRPCA_SPMM_MIN_BLOCKS_ACC
+#define FRPCA_SPMM_MIN_BLOCKS_ACC 18
+#endif
+#ifndef FRPCA_SPMM_BATCH_ACC
+#define FRPCA_SPMM_BATCH_ACC 8
+#endif
+static_assert(FRPCA_SPMM_BATCH == 4 || FRPCA_SPMM_BATCH == 8 || FRPCA_SPMM_BATCH == 16, "batch must divide 32");
+static_assert(FRPCA_SPMM_BATCH_ACC == 4 || FRPCA_SPMM_BATCH_ACC == 8 || FRPCA_SPMM_BATCH_ACC == 16,
+              "batch must divide 32");
+// A warp's share of the whole rows: consecutive rows of the plan whose
+// entries, plus kRowCost per row, come to about kGroupTarget (at most 32
+// rows, because every row costs at least kRowCost).  512: 123.3 ms per step
+// against 125.4 with 256 and 128.5 with 128.
+#ifndef FRPCA_SPMM_GROUP
+#define FRPCA_SPMM_GROUP 512
+#endif
+constexpr int kGroupTarget = FRPCA_SPMM_GROUP;
+constexpr int kRowCost = kGroupTarget / 32;
+static_assert(kGroupTarget % 32 == 0 && kRowCost >= 1, "group target must be a positive multiple of 32");
 
-template <typename T, int NV>
-__global__ void __launch_bounds__(kThreads, FRPCA_SPMM_MIN_BLOCKS)
-spmm_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, const T *__restrict__ vals,
-            const int32_t *__restrict__ short_rows, const int64_t *__restrict__ short_start,
-            const int32_t *__restrict__ short_len, int64_t n_short, const int64_t *__restrict__ seg_start,
+// Batches of a full 32-entry chunk unrolled into straight-line code: more
+// unrolling saves the loop's index arithmetic but grows the kernel past what
+// the instruction cache holds.
+#ifndef FRPCA_SPMM_FULL_UNROLL
+#define FRPCA_SPMM_FULL_UNROLL 1
+#endif
+constexpr int kFullUnroll = FRPCA_SPMM_FULL_UNROLL;
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ inline int64_t shfl_i64(int64_t v, int src) { return (int64_t)__shfl_sync(kFull, (long long)v, src); }
+
+// One warp per work item: a group of whole rows, or one segment of a long
+// row (a group of one row whose output is its slot of `partial`).  Segments
+// come first in the grid, so the longest items start first and the groups
+// fill in around them.  The item's entries are walked as one stream (row 0's
+// entries, then row 1's, ...): 32 (column, value) pairs loaded per chunk, the
+// next chunk's loads issued before the current one is used, and B gathers of
+// 16-byte vectors per lane in flight whatever the row lengths.  Where the
+// stream enters a new row, the finished row is stored.  Every row is summed
+// from zero in CSR order.  A writing launch stores the sums; an accumulating
+// one (ACC) adds each sum to its row of Y (a segment's to its slot of
+// partial, which the launcher has zeroed) with one reduction per vector in
+// L2, and no load on the warp's path: each row belongs to one warp of the
+// launch, so every element takes exactly one addition and the result is
+// deterministic.
+template <typename T, int NV, bool ACC>
+__global__ void __launch_bounds__(kThreads, ACC ? FRPCA_SPMM_MIN_BLOCKS_ACC : FRPCA_SPMM_MIN_BLOCKS)
+spmm_kernel(const int32_t *__restrict__ colidx, const T *__restrict__ vals, const int32_t *__restrict__ short_rows,
+            const int64_t *__restrict__ short_start, const int32_t *__restrict__ short_len,
+            const int64_t *__restrict__ group_first, int64_t n_groups, const int64_t *__restrict__ seg_start,
             const int32_t *__restrict__ seg_len, int64_t n_segs, int nvec, const T *__restrict__ X, int64_t ldx,
-            T *__restrict__ Y, int64_t ldy, T *__restrict__ partial, int accumulate, int64_t out_row_offset) {
+            T *__restrict__ Y, int64_t ldy, T *__restrict__ partial, int64_t out_row_offset) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::width;
+    // Gathers in flight per lane: B x NV vectors (B divides 32).
+    constexpr int kBatch = ACC ? FRPCA_SPMM_BATCH_ACC : FRPCA_SPMM_BATCH;
+    constexpr int B = NV == 1 ? kBatch : (NV == 2 ? kBatch / 2 : (kBatch / 4 > 0 ? kBatch / 4 : 1));
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
-    int64_t start;
-    int len;
-    V *out;
-    if (w < n_short) {
-        const int32_t row = short_rows[w];
-        start = short_start[w];
-        len = short_len[w];
-        out = reinterpret_cast<V *>(Y + ((int64_t)row - out_row_offset) * ldy);
-    } else if (w - n_short < n_segs) {
-        const int64_t sidx = w - n_short;
-        start = seg_start[sidx];
-        len = seg_len[sidx];
-        out = reinterpret_cast<V *>(partial + sidx * (int64_t)nvec * W);
+    // Lane i < nrows holds row i of the item: its first entry, its length and
+    // its output row (of Y, relative to out_row_offset; of partial for a
+    // segment).
+    int nrows;
+    int64_t my_start = 0;
+    int my_len = 0, my_out = 0;
+    bool seg = false;
+    if (w < n_segs) {
+        nrows = 1;
+        seg = true;
+        if (lane == 0) {
+            my_start = seg_start[w];
+            my_len = seg_len[w];
+            my_out = (int)w;
+        }
+    } else if (w - n_segs < n_groups) {
+        const int64_t g0 = group_first[w - n_segs];
+        nrows = (int)(group_first[w - n_segs + 1] - g0);
+        if (lane < nrows) {
+            my_start = short_start[g0 + lane];
+            my_len = short_len[g0 + lane];
+            my_out = (int)((int64_t)short_rows[g0 + lane] - out_row_offset);
+        }
     } else {
         return;
     }
+    // Row i covers stream positions [vbeg_i, vbeg_i + len_i).
+    int vend = my_len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, vend, o);
+        if (lane >= o) vend += t;
+    }
+    const int total = __shfl_sync(kFull, vend, 31);
+    const int vbeg = lane < nrows ? vend - my_len : INT_MAX;
+    // The row holding stream position e: the last row that starts at or
+    // before e (rows before it that start there too are empty).
+    auto row_of = [&](int e) {
+        int r = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int vb = __shfl_sync(kFull, vbeg, r + step);
+            if (vb <= e) r += step;
+        }
+        return r;
+    };
+    // Column and value at stream position base + lane, and the chunk's mask
+    // of positions where a row starts.
+    auto fetch = [&](int base, int32_t &col, T &val, unsigned &starts) {
+        const int e = base + lane;
+        const int r = row_of(e);
+        const int64_t st = shfl_i64(my_start, r);
+        const int vb = __shfl_sync(kFull, vbeg, r);
+        col = 0;
+        val = T(0);
+        if (e < total) {
+            col = __ldg(colidx + st + (e - vb));
+            val = __ldg(vals + st + (e - vb));
+        }
+        starts = __ballot_sync(kFull, e < total && e == vb);
+    };
+    auto store_row = [&](int i, const V(&src)[NV]) {
+        const int orow = __shfl_sync(kFull, my_out, i);
+        V *o = seg ? reinterpret_cast<V *>(partial + (int64_t)orow * nvec * W)
+                   : reinterpret_cast<V *>(Y + (int64_t)orow * ldy);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const int vi = lane + 32 * k;
+            if (vi < nvec) {
+                if (ACC)
+                    Vec<T>::red_add(o + vi, src[k]);
+                else
+                    o[vi] = src[k];
+            }
+        }
+    };
+    V acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = Vec<T>::zero();
+    // Empty rows: zero when writing, left as they are when accumulating.
+    if (!ACC) {
+        for (unsigned empty = __ballot_sync(kFull, lane < nrows && my_len == 0); empty; empty &= empty - 1)
+            store_row(__ffs(empty) - 1, acc);
+    }
+    int cur = -1;
+    // At stream position e a row starts: store row cur, start that row.
+    auto advance = [&](int e) {
+        if (cur >= 0) store_row(cur, acc);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = Vec<T>::zero();
+        cur = __ffs(__ballot_sync(kFull, vbeg == e && my_len > 0)) - 1;
+    };
+
     const V *Xv = reinterpret_cast<const V *>(X);
     const int64_t ldxv = ldx / W;
-    V acc[NV];
-    // accumulate: add to the row already in Y (whole rows only; segments of
-    // long rows are added to Y by the fix-up).
-    const bool add_y = accumulate && w < n_short;
+    int32_t col = 0;
+    T val = T(0);
+    unsigned starts = 0;
+    // Entries t0 .. t0 + B - 1 of the current chunk (those below cnt): B
+    // gathers issued, then the products added in order, a row's store
+    // wherever one starts.  FULL: all B entries are there (a full chunk,
+    // t0 known at compile time).
+    auto batch = [&](auto full, int base, int t0, int cnt) {
+        constexpr bool FULL = decltype(full)::value;
+        int32_t c[B];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const int vi = lane + 32 * k;
-        acc[k] = (add_y && vi < nvec) ? out[vi] : Vec<T>::zero();
-    }
-
-    for (int base = 0; base < len; base += 32) {
-        const int cnt = min(32, len - base);
-        int32_t my_col = 0;
-        T my_val = T(0);
-        if (lane < cnt) {
-            my_col = __ldg(colidx + start + base + lane);
-            my_val = __ldg(vals + start + base + lane);
+        for (int u = 0; u < B; ++u) c[u] = __shfl_sync(kFull, col, (t0 + u) & 31);
+        V x[NV][B];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const int vi = lane + 32 * k;
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                x[k][u] = (vi < nvec && (FULL || t0 + u < cnt)) ? __ldg(Xv + (int64_t)c[u] * ldxv + vi)
+                                                                : Vec<T>::zero();
         }
-        if (cnt == 32) {
+        const unsigned here = (starts >> t0) & ((1u << B) - 1u);
+        if (here == 0u) {
 #pragma unroll
-            for (int t0 = 0; t0 < 32; t0 += 8) {
-                int32_t c[8];
-                T v[8];
+            for (int u = 0; u < B; ++u) {
+                const T v = __shfl_sync(kFull, val, (t0 + u) & 31);
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    c[u] = __shfl_sync(0xffffffffu, my_col, t0 + u);
-                    v[u] = __shfl_sync(0xffffffffu, my_val, t0 + u);
-                }
-#pragma unroll
-                for (int k = 0; k < NV; ++k) {
-                    const int vi = lane + 32 * k;
-                    if (vi < nvec) {
-                        V x[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) x[u] = __ldg(Xv + (int64_t)c[u] * ldxv + vi);
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) Vec<T>::fma(acc[k], v[u], x[u]);
-                    }
-                }
+                for (int k = 0; k < NV; ++k) Vec<T>::fma(acc[k], v, x[k][u]);
             }
         } else {
-            // A partial chunk, still eight gathers in flight at a time: the
-            // entries past cnt are skipped (their loads are not issued), and
-            // the valid ones are added in CSR order.
-            for (int t0 = 0; t0 < cnt; t0 += 8) {
-                int32_t c[8];
-                T v[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    c[u] = __shfl_sync(0xffffffffu, my_col, (t0 + u) & 31);
-                    v[u] = __shfl_sync(0xffffffffu, my_val, (t0 + u) & 31);
-                }
+            for (int u = 0; u < B; ++u) {
+                const T v = __shfl_sync(kFull, val, (t0 + u) & 31);
+                if (FULL || t0 + u < cnt) {
+                    if ((here >> u) & 1u) advance(base + t0 + u);
 #pragma unroll
-                for (int k = 0; k < NV; ++k) {
-                    const int vi = lane + 32 * k;
-                    if (vi < nvec) {
-                        V x[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            x[u] = (t0 + u < cnt) ? __ldg(Xv + (int64_t)c[u] * ldxv + vi) : Vec<T>::zero();
-#pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            if (t0 + u < cnt) Vec<T>::fma(acc[k], v[u], x[u]);
-                    }
+                    for (int k = 0; k < NV; ++k) Vec<T>::fma(acc[k], v, x[k][u]);
                 }
             }
         }
+    };
+    if (total > 0) {
+        fetch(0, col, val, starts);
+        for (int base = 0; base < total; base += 32) {
+            const int cnt = min(32, total - base);
+            int32_t ncol = 0;
+            T nval = T(0);
+            unsigned nstarts = 0;
+            if (base + 32 < total) fetch(base + 32, ncol, nval, nstarts);
+            if (cnt == 32) {
+#pragma unroll kFullUnroll
+                for (int t0 = 0; t0 < 32; t0 += B) batch(std::true_type{}, base, t0, 32);
+            } else {
+                for (int t0 = 0; t0 < cnt; t0 += B) batch(std::false_type{}, base, t0, cnt);
+            }
+            col = ncol;
+            val = nval;
+            starts = nstarts;
+        }
     }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const int vi = lane + 32 * k;
-        if (vi < nvec) out[vi] = acc[k];
-    }
+    if (cur >= 0) store_row(cur, acc);
 }
 
 // partial holds the segments seg_base, seg_base + 1, ... (long_first values
@@ -156,13 +280,15 @@ __global__ void spmm_fixup_kernel(int64_t n_long, const int32_t *__restrict__ lo
     }
 }
 
-// The rows of one launch: a sub-range of a plan's lists (whole rows, segments
-// of long rows, long rows for the fix-up).
+// The rows of one launch: a range of a plan's groups of whole rows, of its
+// segments of long rows and of its long rows for the fix-up.  The whole-row
+// arrays are the plan's own (group_first holds indices into them).
 struct SpmmWork {
     const int32_t *short_rows;
     const int64_t *short_start;
     const int32_t *short_len;
-    int64_t n_short;
+    const int64_t *group_first;
+    int64_t n_groups;
     const int64_t *seg_start;
     const int32_t *seg_len;
     int64_t n_segs, seg_base;
@@ -173,39 +299,50 @@ struct SpmmWork {
 };
 
 SpmmWork whole_plan(const SpmmPlan &p) {
-    return SpmmWork{p.short_rows, p.short_start, p.short_len, p.n_short, p.seg_start, p.seg_len, p.n_segs, 0,
-                    p.long_rows, p.long_first, p.n_long, 0};
+    return SpmmWork{p.short_rows, p.short_start, p.short_len, p.group_first, p.n_groups, p.seg_start, p.seg_len,
+                    p.n_segs, 0, p.long_rows, p.long_first, p.n_long, 0};
+}
+
+// One launch of spmm_kernel<T, NV, ACC> over groups [0, n_groups) and
+// segments [0, n_segs) of p.
+template <typename T, bool ACC>
+cudaError_t launch_items(const int32_t *colidx, const T *vals, const SpmmWork &p, int64_t n_groups, int64_t n_segs,
+                         int nvec, const T *X, int64_t ldx, T *Y, int64_t ldy, T *partial, cudaStream_t s) {
+    const int64_t warps = n_groups + n_segs;
+    if (warps == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)ceil_div(warps * 32, kThreads);
+    switch ((int)ceil_div(nvec, 32)) {
+#define FRPCA_SPMM_CASE(NVV)                                                                                  \
+    case NVV:                                                                                                 \
+        spmm_kernel<T, NVV, ACC><<<blocks, kThreads, 0, s>>>(colidx, vals, p.short_rows, p.short_start,       \
+                                                             p.short_len, p.group_first, n_groups, p.seg_start, \
+                                                             p.seg_len, n_segs, nvec, X, ldx, Y, ldy, partial,  \
+                                                             p.out_row_offset);                                \
+        break;
+        FRPCA_SPMM_CASE(1)
+        FRPCA_SPMM_CASE(2)
+        FRPCA_SPMM_CASE(3)  // l <= 160: at most 80 vectors (double2) per row
+#undef FRPCA_SPMM_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmWork &p, int l, const T *X, int64_t ldx, T *Y,
-                         int64_t ldy, T *partial, bool accumulate, cudaStream_t s) {
+cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmWork &p, int l, const T *X, int64_t ldx,
+                         T *Y, int64_t ldy, T *partial, bool accumulate, cudaStream_t s) {
     constexpr int W = Vec<T>::width;
     const int nvec = (int)ceil_div(l, W);
-    const int nv = (int)ceil_div(nvec, 32);
-    const int64_t warps = p.n_short + p.n_segs;
-    if (warps > 0) {
-        const int64_t blocks = ceil_div(warps * 32, kThreads);
-#define FRPCA_SPMM_CASE(NVV)                                                                                  \
-    case NVV:                                                                                                 \
-        spmm_kernel<T, NVV><<<(unsigned)blocks, kThreads, 0, s>>>(A.rowptr, A.colidx, vals, p.short_rows,     \
-                                                                  p.short_start, p.short_len,                 \
-                                                                  p.n_short, p.seg_start, p.seg_len,          \
-                                                                  p.n_segs, nvec, X, ldx, Y, ldy, partial,    \
-                                                                  accumulate, p.out_row_offset);              \
-        count_launch();                                                                                       \
-        break;
-        switch (nv) {
-            FRPCA_SPMM_CASE(1)
-            FRPCA_SPMM_CASE(2)
-            FRPCA_SPMM_CASE(3)
-            FRPCA_SPMM_CASE(4)
-            default: return cudaErrorInvalidValue;
-        }
-#undef FRPCA_SPMM_CASE
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e;
+    if (accumulate && p.n_segs > 0 &&
+        (e = cudaMemsetAsync(partial, 0, sizeof(T) * (size_t)p.n_segs * (size_t)nvec * W, s)) != cudaSuccess)
+        return e;
+    if (accumulate)
+        e = launch_items<T, true>(A.colidx, vals, p, p.n_groups, p.n_segs, nvec, X, ldx, Y, ldy, partial, s);
+    else
+        e = launch_items<T, false>(A.colidx, vals, p, p.n_groups, p.n_segs, nvec, X, ldx, Y, ldy, partial, s);
+    if (e != cudaSuccess) return e;
     if (p.n_long > 0) {
         spmm_fixup_kernel<T><<<(unsigned)ceil_div(p.n_long * 32, 256), 256, 0, s>>>(
             p.n_long, p.long_rows, p.long_first, nvec, partial, Y, ldy, accumulate, p.seg_base, p.out_row_offset);
@@ -225,6 +362,7 @@ void SpmmPlan::free_all() {
     dev_free(seg_len, stream);
     dev_free(long_rows, stream);
     dev_free(long_first, stream);
+    dev_free(group_first, stream);
     if (budget) budget->give(charged);
     charged = 0;
     short_rows = nullptr;
@@ -234,7 +372,8 @@ void SpmmPlan::free_all() {
     seg_len = nullptr;
     long_rows = nullptr;
     long_first = nullptr;
-    n_short = n_segs = n_long = 0;
+    group_first = nullptr;
+    n_short = n_segs = n_long = n_groups = 0;
 }
 
 cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, std::string &err,
@@ -270,6 +409,20 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
         }
     }
     lfirst.push_back((int64_t)sstart.size());
+    // Groups: a new one wherever the running cost (entries + kRowCost per
+    // row) enters a new multiple of kGroupTarget, or the row enters a new
+    // stride block.
+    std::vector<int64_t> gfirst;
+    int64_t cost = 0, prev = 0;  // running cost before row i and before row i - 1
+    for (size_t i = 0; i < shorts.size(); ++i) {
+        const int64_t g = plan.group_stride;
+        if (i == 0 || cost / kGroupTarget != prev / kGroupTarget || (g > 0 && shorts[i] / g != shorts[i - 1] / g))
+            gfirst.push_back((int64_t)i);
+        prev = cost;
+        cost += shlen[i] + kRowCost;
+    }
+    plan.n_groups = (int64_t)gfirst.size();
+    gfirst.push_back((int64_t)shorts.size());
     plan.n_short = (int64_t)shorts.size();
     plan.n_long = (int64_t)lrows.size();
     plan.n_segs = (int64_t)sstart.size();
@@ -286,7 +439,8 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
         (e = up((void **)&plan.long_rows, lrows.data(), 4 * lrows.size())) != cudaSuccess ||
         (e = up((void **)&plan.long_first, lfirst.data(), 8 * lfirst.size())) != cudaSuccess ||
         (e = up((void **)&plan.seg_start, sstart.data(), 8 * sstart.size())) != cudaSuccess ||
-        (e = up((void **)&plan.seg_len, slen.data(), 4 * slen.size())) != cudaSuccess) {
+        (e = up((void **)&plan.seg_len, slen.data(), 4 * slen.size())) != cudaSuccess ||
+        (e = up((void **)&plan.group_first, gfirst.data(), 8 * gfirst.size())) != cudaSuccess) {
         err = "spmm plan: device allocation failed";
         return e;
     }
@@ -339,11 +493,38 @@ __global__ void plan_fill_kernel(int64_t m, const int64_t *__restrict__ rowptr, 
     }
 }
 
+// Groups of whole rows.  Cost of list entry i: its entries plus kRowCost.
+__global__ void group_cost_kernel(int64_t n, const int32_t *__restrict__ short_len, int32_t *__restrict__ cost) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) cost[i] = short_len[i] + kRowCost;
+}
+
+// 1 where a group starts: the running cost V (exclusive scan of the costs)
+// enters a new multiple of kGroupTarget, or the row a new stride block.
+__global__ void group_flag_kernel(int64_t n, const int64_t *__restrict__ V, const int32_t *__restrict__ short_rows,
+                                  int64_t stride, int32_t *__restrict__ flag) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool f = i == 0 || V[i] / kGroupTarget != V[i - 1] / kGroupTarget;
+    if (stride > 0 && i > 0) f = f || short_rows[i] / stride != short_rows[i - 1] / stride;
+    flag[i] = f ? 1 : 0;
+}
+
+__global__ void group_fill_kernel(int64_t n, const int32_t *__restrict__ flag, const int64_t *__restrict__ pos,
+                                  int64_t *__restrict__ group_first) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) group_first[pos[i]] = i;
+    if (i == n) group_first[pos[n]] = n;
+}
+
 // First entry of each panel in the plan's sorted row lists: short rows and
-// long rows of panel b are those with row in [b stride, (b + 1) stride).
+// long rows of panel b are those with row in [b stride, (b + 1) stride); the
+// first group of panel b is the one that starts at its first short row
+// (groups end at panel boundaries).
 __global__ void panel_offsets_kernel(int64_t npanels, int64_t stride, const int32_t *__restrict__ short_rows,
                                      int64_t n_short, const int32_t *__restrict__ long_rows, int64_t n_long,
-                                     const int64_t *__restrict__ long_first, int64_t *__restrict__ out) {
+                                     const int64_t *__restrict__ long_first, const int64_t *__restrict__ group_first,
+                                     int64_t n_groups, int64_t *__restrict__ out) {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b > npanels) return;
     const int64_t key = b * stride;
@@ -361,6 +542,14 @@ __global__ void panel_offsets_kernel(int64_t npanels, int64_t stride, const int3
     }
     out[(npanels + 1) + b] = lo;
     out[2 * (npanels + 1) + b] = long_first[lo];
+    const int64_t sb = out[b];
+    lo = 0;
+    hi = n_groups;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (group_first[mid] < sb) lo = mid + 1; else hi = mid;
+    }
+    out[3 * (npanels + 1) + b] = lo;
 }
 
 }  // namespace
@@ -452,23 +641,79 @@ cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *cons
             return e;
         }
     }
+    // Groups of whole rows, from the filled lists (each matrix's flag and scan
+    // scratch is free again).
+    std::vector<int64_t> ngroups((size_t)count, 0);
+    for (int c = 0; c < count; ++c) {
+        SpmmPlan &plan = *plans[c];
+        const Parts q = parts(c);
+        const int64_t n = plan.n_short;
+        if (n == 0) continue;
+        const unsigned g = (unsigned)ceil_div(n, 256);
+        group_cost_kernel<<<g, 256, 0, s>>>(n, plan.short_len, q.is_short);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess ||
+            (e = exclusive_scan_i32_to_i64(q.is_short, q.short_pos, n, scan_scratch, s)) != cudaSuccess) {
+            err = "spmm plan: group pass failed";
+            return e;
+        }
+        group_flag_kernel<<<g, 256, 0, s>>>(n, q.short_pos, plan.short_rows, plan.group_stride, q.is_long);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess ||
+            (e = exclusive_scan_i32_to_i64(q.is_long, q.long_pos, n, scan_scratch, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&ngroups[c], q.long_pos + n, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+            err = "spmm plan: group pass failed";
+            return e;
+        }
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        err = "spmm plan: synchronize failed";
+        return e;
+    }
+    for (int c = 0; c < count; ++c) {
+        SpmmPlan &plan = *plans[c];
+        const Parts q = parts(c);
+        const int64_t n = plan.n_short;
+        plan.n_groups = ngroups[c];
+        const size_t bytes = 8 * ((size_t)plan.n_groups + 1);
+        if ((e = dev_malloc((void **)&plan.group_first, bytes, s, plan.budget)) != cudaSuccess) {
+            err = "spmm plan: device allocation failed";
+            return e;
+        }
+        plan.charged += bytes;
+        if (n == 0) {
+            e = cudaMemsetAsync(plan.group_first, 0, bytes, s);
+        } else {
+            group_fill_kernel<<<(unsigned)ceil_div(n + 1, 256), 256, 0, s>>>(n, q.is_long, q.long_pos,
+                                                                             plan.group_first);
+            count_launch();
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            err = "spmm plan: group fill failed";
+            return e;
+        }
+    }
     return cudaSuccess;
 }
 
 // Per panel b (npanels + 1 entries each, copied to the host): first short row,
-// first long row and first segment of `plan` whose row is >= b stride.
+// first long row, first segment and first group of `plan` whose row is >= b
+// stride (the plan's groups must end at multiples of stride).
 cudaError_t plan_panel_offsets(const SpmmPlan &plan, int64_t npanels, int64_t stride, std::vector<int64_t> &so,
-                               std::vector<int64_t> &lo, std::vector<int64_t> &go, cudaStream_t s) {
+                               std::vector<int64_t> &lo, std::vector<int64_t> &go, std::vector<int64_t> &gr,
+                               cudaStream_t s) {
     const int64_t np1 = npanels + 1;
     DevBuf offs;
     offs.stream = s;
-    cudaError_t e = offs.ensure(sizeof(int64_t) * 3 * (size_t)np1);
+    cudaError_t e = offs.ensure(sizeof(int64_t) * 4 * (size_t)np1);
     if (e != cudaSuccess) return e;
     panel_offsets_kernel<<<(unsigned)ceil_div(np1, 128), 128, 0, s>>>(npanels, stride, plan.short_rows, plan.n_short,
                                                                      plan.long_rows, plan.n_long, plan.long_first,
+                                                                     plan.group_first, plan.n_groups,
                                                                      (int64_t *)offs.ptr);
     count_launch();
-    std::vector<int64_t> h(3 * (size_t)np1);
+    std::vector<int64_t> h(4 * (size_t)np1);
     if ((e = cudaGetLastError()) == cudaSuccess &&
         (e = cudaMemcpyAsync(h.data(), offs.ptr, sizeof(int64_t) * h.size(), cudaMemcpyDeviceToHost, s)) ==
             cudaSuccess)
@@ -477,18 +722,20 @@ cudaError_t plan_panel_offsets(const SpmmPlan &plan, int64_t npanels, int64_t st
     if (e != cudaSuccess) return e;
     so.assign(h.begin(), h.begin() + np1);
     lo.assign(h.begin() + np1, h.begin() + 2 * np1);
-    go.assign(h.begin() + 2 * np1, h.end());
+    go.assign(h.begin() + 2 * np1, h.begin() + 3 * np1);
+    gr.assign(h.begin() + 3 * np1, h.end());
     return cudaSuccess;
 }
 
 cudaError_t build_panel_plan(PanelCSR &pc, DevBuf &scratch, DevBuf &scan_scratch, cudaStream_t s, std::string &err) {
     pc.plan.skip_empty = true;
+    pc.plan.group_stride = pc.src_rows;
     const DeviceCSR *mats[1] = {&pc.virt};
     SpmmPlan *plans[1] = {&pc.plan};
     cudaError_t e = build_spmm_plans_device(mats, plans, 1, scratch, scan_scratch, s, err);
     if (e != cudaSuccess) return e;
-    if ((e = plan_panel_offsets(pc.plan, pc.npanels, pc.src_rows, pc.short_off, pc.long_off, pc.seg_off, s)) !=
-        cudaSuccess) {
+    if ((e = plan_panel_offsets(pc.plan, pc.npanels, pc.src_rows, pc.short_off, pc.long_off, pc.seg_off,
+                                pc.group_off, s)) != cudaSuccess) {
         err = "spmm plan: panel offsets failed";
         return e;
     }
@@ -499,8 +746,12 @@ cudaError_t build_panel_plan(PanelCSR &pc, DevBuf &scratch, DevBuf &scan_scratch
 }
 
 cudaError_t build_fused_offsets(PanelCSR &pc, const SpmmPlan &prod, cudaStream_t s, std::string &err) {
+    if (prod.group_stride != pc.panel_rows) {
+        err = "spmm plan: the product's groups do not end at panel boundaries";
+        return cudaErrorInvalidValue;
+    }
     cudaError_t e = plan_panel_offsets(prod, pc.npanels, pc.panel_rows, pc.prod_short_off, pc.prod_long_off,
-                                       pc.prod_seg_off, s);
+                                       pc.prod_seg_off, pc.prod_group_off, s);
     if (e != cudaSuccess) {
         err = "spmm plan: fused offsets failed";
         return e;
@@ -526,8 +777,9 @@ cudaError_t panel_launch(const PanelCSR &pc, int64_t b, int l, const void *Xb, i
     const int64_t s0 = pc.short_off[b], s1 = pc.short_off[b + 1];
     const int64_t l0 = pc.long_off[b], l1 = pc.long_off[b + 1];
     const int64_t g0 = pc.seg_off[b], g1 = pc.seg_off[b + 1];
+    const int64_t r0 = pc.group_off[b], r1 = pc.group_off[b + 1];
     if (s1 == s0 && l1 == l0) return cudaSuccess;
-    const SpmmWork w{p.short_rows + s0, p.short_start + s0, p.short_len + s0, s1 - s0, p.seg_start + g0,
+    const SpmmWork w{p.short_rows, p.short_start, p.short_len, p.group_first + r0, r1 - r0, p.seg_start + g0,
                      p.seg_len + g0, g1 - g0, g0,
                      p.long_rows + l0, p.long_first + l0, l1 - l0, b * pc.src_rows};
     if (dt == FRPCA_F32)
@@ -566,10 +818,10 @@ cudaError_t launch_fused_sweep(const DeviceCSR &Pm, const SpmmPlan &prod, const 
         void *slot = (char *)ring + es * (size_t)((b & 1) * pc.panel_rows) * (size_t)ldr;
         // Rows b P .. b P + P-1 of P Q into the slot (every row written: the
         // producing plan keeps empty rows).
-        const int64_t s0 = pc.prod_short_off[b], s1 = pc.prod_short_off[b + 1];
         const int64_t l0 = pc.prod_long_off[b], l1 = pc.prod_long_off[b + 1];
         const int64_t g0 = pc.prod_seg_off[b], g1 = pc.prod_seg_off[b + 1];
-        const SpmmWork w{prod.short_rows + s0, prod.short_start + s0, prod.short_len + s0, s1 - s0,
+        const int64_t r0 = pc.prod_group_off[b], r1 = pc.prod_group_off[b + 1];
+        const SpmmWork w{prod.short_rows, prod.short_start, prod.short_len, prod.group_first + r0, r1 - r0,
                          prod.seg_start + g0, prod.seg_len + g0, g1 - g0, g0,
                          prod.long_rows + l0, prod.long_first + l0, l1 - l0, b * pc.panel_rows};
         if (dt == FRPCA_F32)
@@ -592,6 +844,7 @@ void PanelCSR::free_all() {
     short_off.clear();
     long_off.clear();
     seg_off.clear();
+    group_off.clear();
 }
 
 size_t spmm_scratch_bytes(const SpmmPlan &plan, int l, frpca_dtype dt) {

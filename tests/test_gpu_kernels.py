@@ -73,6 +73,20 @@ def _mats():
     out.append(synthetic.from_coo(m, n, r, c, rng.standard_normal(r.size)))
     out.append(synthetic.powerlaw_csr(20_000, 3_000, 20, 1.1, "tfidf", seed=2, dtype=np.float64))
     out.append(synthetic.uniform_csr(2000, 1000, 20000, seed=1))
+    # Row lengths at the edges of the SpMM work split: runs of empty rows (at
+    # the start, inside and at the end), runs of one-entry rows longer than a
+    # 32-row group, rows of 31-33 entries (one 32-entry chunk and a ragged
+    # tail) and of 1,023-1,025 and 2,049 entries (a whole row at the segment
+    # length, segments and their fix-up).
+    m, n = 1200, 3000
+    lens = np.zeros(m, dtype=np.int64)
+    lens[40:120] = 1
+    lens[130:200] = rng.integers(1, 4, 70)
+    lens[[210, 211, 212, 300, 301, 302, 400]] = [31, 32, 33, 1023, 1024, 1025, 2049]
+    lens[500:1100] = rng.integers(0, 40, 600)
+    r = np.repeat(np.arange(m), lens)
+    c = np.concatenate([np.sort(rng.choice(n, k, replace=False)) for k in lens if k])
+    out.append(synthetic.from_coo(m, n, r, c, rng.standard_normal(r.size)))
     return out
 
 
@@ -369,9 +383,9 @@ def test_lu_tournament_singular_pivot_reports():
 
 # ---------------------------------------------------------------- SpMM by panels of the gathered block
 def _panel_bound(A, X, trans, eps):
-    """Sums continue from one panel to the next in the output itself (a float
-    stored and reloaded exactly), so the only roundings beyond the CSR
-    order's d + 2 are the fix-up's additions of the 1,024-entry segments of a
+    """Each panel's part of a row is summed from zero in CSR order and then
+    added to the row once, so a product passes through at most d + 1
+    additions plus the fix-up's additions of the 1,024-entry segments of a
     long row within a panel: (d + 4 + d / 512) eps (|A| |X|)."""
     Aabs = synthetic.CSR(A.m, A.n, A.indptr, A.indices, np.abs(A.data.astype(np.float64)))
     f = oracle.spmm_t if trans else oracle.spmm
