@@ -25,7 +25,7 @@ struct frpca_ctx {
     DevBuf own_rowptr, own_colidx, own_vals;    // copies of A (when not borrowed)
     DevBuf t_rowptr, t_colidx, t_vals, t_perm;  // A^T and the entry of A at each of its positions
     DevBuf alt_A, alt_AT;                        // values converted to the other dtype
-    bool alt_ready = false;
+    bool alt_ready = false, alt_at_ready = false;
     SpmmPlan planA, planAT;
     DevBuf ws_q, ws_w, ws_spmm, ws_gram, ws_eig, ws_lu, ws_small, ws_sign, ws_scratch, ws_scan, ws_bwd, ws_hot, ws_plan;
     HybridCSR hy;  // the densest columns of A as a dense block (FP32 SpMM on the tensor cores)
@@ -159,24 +159,32 @@ frpca_status fresh_at_values(frpca_ctx *h) {
     return FRPCA_OK;
 }
 
-frpca_status values_for(frpca_ctx *h, frpca_dtype dt, const void **va, const void **vat) {
-    frpca_status st0 = fresh_at_values(h);
-    if (st0 != FRPCA_OK) return st0;
+// *va: A's values; *vat (only when need_at, else null): A^T's, refreshed if
+// stale.  A pass that reads only A's values leaves A^T's stale.
+frpca_status values_for(frpca_ctx *h, frpca_dtype dt, bool need_at, const void **va, const void **vat) {
+    *vat = nullptr;
+    if (need_at) {
+        frpca_status st0 = fresh_at_values(h);
+        if (st0 != FRPCA_OK) return st0;
+    }
     if (dt == h->A.dtype) {
         *va = h->A.vals;
-        *vat = h->AT.vals;
+        if (need_at) *vat = h->AT.vals;
         return FRPCA_OK;
     }
+    const size_t bytes = dsize(dt) * (size_t)std::max<int64_t>(h->A.nnz, 1);
     if (!h->alt_ready) {
-        const size_t bytes = dsize(dt) * (size_t)std::max<int64_t>(h->A.nnz, 1);
         CK(h->alt_A.ensure(bytes), "alloc converted values");
-        CK(h->alt_AT.ensure(bytes), "alloc converted values");
         CK(launch_convert(h->A.vals, h->A.dtype, h->alt_A.ptr, dt, h->A.nnz, h->stream), "convert values");
-        CK(launch_convert(h->AT.vals, h->AT.dtype, h->alt_AT.ptr, dt, h->A.nnz, h->stream), "convert values");
         h->alt_ready = true;
     }
+    if (need_at && !h->alt_at_ready) {
+        CK(h->alt_AT.ensure(bytes), "alloc converted values");
+        CK(launch_convert(h->AT.vals, h->AT.dtype, h->alt_AT.ptr, dt, h->A.nnz, h->stream), "convert values");
+        h->alt_at_ready = true;
+    }
     *va = h->alt_A.ptr;
-    *vat = h->alt_AT.ptr;
+    if (need_at) *vat = h->alt_AT.ptr;
     return FRPCA_OK;
 }
 
@@ -220,12 +228,12 @@ frpca_status spmm_pass_plain(frpca_ctx *h, int trans, int l, const void *X, int6
         h->acc.spmm_flops += 2.0 * (double)C.nnz * (double)l;
         return FRPCA_OK;
     }
-    const void *va, *vat;
-    frpca_status st = values_for(h, dt, &va, &vat);
-    if (st != FRPCA_OK) return st;
     const DeviceCSR &C = trans ? h->AT : h->A;
     const SpmmPlan &P = trans ? h->planAT : h->planA;
     const bool hybrid = dt == FRPCA_F32 && h->hy.h > 0 && l <= 128;
+    const void *va, *vat;
+    frpca_status st = values_for(h, dt, trans != 0, &va, &vat);
+    if (st != FRPCA_OK) return st;
     if (hybrid) {
         const SpmmPlan &Pc = trans ? h->hy.plan_t_cold : h->hy.plan_cold;
         CK(h->ws_spmm.ensure(std::max<size_t>(256, spmm_scratch_bytes(Pc, l, dt))), "alloc spmm scratch");
@@ -275,6 +283,10 @@ frpca_status fused_sweep(frpca_ctx *h, int fwd_trans, int l, void *Q, void *W, i
     void *Z = (char *)W + es * (size_t)(2 * h->pan.panel_rows) * (size_t)ld;
     const DeviceCSR &F = fwd_trans ? h->AT : h->A;
     const SpmmPlan &P = fwd_trans ? h->planAT : h->planA;
+    if (fwd_trans) {  // the producing pass reads A^T's own values
+        frpca_status st = fresh_at_values(h);
+        if (st != FRPCA_OK) return st;
+    }
     CK(h->ws_spmm.ensure(std::max<size_t>(256, fused_scratch_bytes(h->pan, l, dt))), "alloc spmm scratch");
     {
         PhaseTimer t(h, PH_SPMM_T);
@@ -751,6 +763,7 @@ frpca_status frpca_refresh(frpca_handle h) {
     t.done();
     h->mu_ready = false;
     h->alt_ready = false;
+    h->alt_at_ready = false;
     return FRPCA_OK;
 }
 

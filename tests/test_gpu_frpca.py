@@ -119,6 +119,33 @@ def test_fused_sweep_matches_two_passes(prec, shape):
     m2.close()
 
 
+@pytest.mark.parametrize("shape", ["tall", "wide"])
+@pytest.mark.parametrize("fused", [0, 1])
+def test_refresh_then_run_matches_new_handle(shape, fused):
+    """After the values change in place and frpca_refresh, a run reads the
+    new values in every pass: A^T's own values are refreshed for the passes
+    that read them (the producing pass of a wide matrix's fused sweep, the
+    A^T pass without panels) and may be left stale by the others.  The same
+    kernels run on the same data, so U, S and V equal a new handle's bit for
+    bit."""
+    A = (SMALL_TALL if shape == "tall" else SMALL_WIDE).astype(np.float32)
+    vals = torch.tensor(A.data, device=DEV)
+    m1 = frpca.FrPCA(torch.tensor(A.indptr, device=DEV), torch.tensor(A.indices, device=DEV), vals, (A.m, A.n),
+                     panel_rows=250, fused_sweep=fused)
+    m1.run(10, 24, 5, seed=3, precision="fp32")
+    with torch.no_grad():
+        vals.mul_(torch.linspace(0.5, 2.0, vals.numel(), device=DEV))
+    m1.refresh()
+    r1 = [t.clone() for t in m1.run(10, 24, 5, seed=3, precision="fp32")]
+    m2 = frpca.FrPCA(torch.tensor(A.indptr, device=DEV), torch.tensor(A.indices, device=DEV), vals.clone(),
+                     (A.m, A.n), panel_rows=250, fused_sweep=fused)
+    r2 = [t.clone() for t in m2.run(10, 24, 5, seed=3, precision="fp32")]
+    for a, b in zip(r1, r2):
+        assert torch.equal(a, b)
+    m1.close()
+    m2.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_frpca_uniform_2000x1000(prec):
     """The uniform 2,000 x 1,000 workload, k = 10, l = 20, 3 passes, seed 0."""
