@@ -30,8 +30,8 @@ struct DeviceCSR {
 // Work split of one SpMM over a CSR.  Rows with at most `seg` entries are
 // handled whole (list `short_rows`), in groups of consecutive list entries,
 // one warp per group; longer rows are cut into segments of `seg` entries
-// whose partial rows go to scratch and are summed in segment order by a
-// fix-up pass.
+// whose partial rows go to scratch; the warp that finishes a long row's last
+// segment sums its partial rows in segment order.
 struct SpmmPlan {
     int seg = 0;
     int64_t n_short = 0;          // rows handled whole
@@ -46,6 +46,8 @@ struct SpmmPlan {
     int32_t *seg_len = nullptr;
     int32_t *long_rows = nullptr; // row of each long row
     int64_t *long_first = nullptr;// first segment of each long row (n_long + 1 entries)
+    int32_t *seg_owner = nullptr; // long row of each segment
+    int32_t *long_count = nullptr;// segments of each long row finished in the running launch (0 between launches)
     cudaStream_t stream = nullptr;  // stream the arrays were allocated on
     MemBudget *budget = nullptr;    // allocation cap the arrays are charged to
     size_t charged = 0;             // bytes charged to budget

@@ -73,6 +73,66 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __device__ inline int64_t shfl_i64(int64_t v, int src) { return (int64_t)__shfl_sync(kFull, (long long)v, src); }
 
+// In an accumulating launch, after segment w of long row r (w counted from
+// the launch's first segment, seg_base): the warp that finishes the row's
+// last segment (the arrival count says which; no warp waits for another)
+// adds the row's partial rows in segment order and adds that sum to the row.
+// Out of line, so the gather loop's registers are not sized for it.  (A
+// writing launch leaves the sums to spmm_fixup_kernel: the call cost its
+// gather loop more than the extra launch, which runs once per pass.)
+template <typename T, int NV, bool ACC>
+__device__ __noinline__ void finish_segment(int64_t w, const int32_t *__restrict__ seg_owner, int64_t seg_base,
+                                            const int32_t *__restrict__ long_rows,
+                                            const int64_t *__restrict__ long_first, int32_t *__restrict__ long_count,
+                                            int nvec, T *__restrict__ Y, int64_t ldy, const T *__restrict__ partial,
+                                            int64_t out_row_offset) {
+    using V = typename Vec<T>::type;
+    constexpr int W = Vec<T>::width;
+    const int lane = threadIdx.x & 31;
+    const int r = seg_owner[w];
+    const int64_t s0 = long_first[r], s1 = long_first[r + 1];
+    __threadfence();
+    int prev = 0;
+    if (lane == 0) prev = atomicAdd(long_count + r, 1);
+    prev = __shfl_sync(kFull, prev, 0);
+    if ((int64_t)prev + 1 != s1 - s0) return;
+    __threadfence();
+    if (lane == 0) long_count[r] = 0;  // ready for the next launch
+    V acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = Vec<T>::zero();
+    for (int64_t sg = s0; sg < s1; ++sg) {
+        const V *P = reinterpret_cast<const V *>(partial + (sg - seg_base) * (int64_t)nvec * W);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const int vi = lane + 32 * k;
+            if (vi < nvec) Vec<T>::add(acc[k], __ldcg(P + vi));
+        }
+    }
+    V *o = reinterpret_cast<V *>(Y + ((int64_t)long_rows[r] - out_row_offset) * ldy);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int vi = lane + 32 * k;
+        if (vi < nvec) {
+            if (ACC)
+                Vec<T>::red_add(o + vi, acc[k]);
+            else
+                o[vi] = acc[k];
+        }
+    }
+}
+
+// What an accumulating launch's segments need to finish their long rows
+// (the kernel's last parameter: ahead of the others it cost the writing
+// kernel's gather loop registers).
+struct LongRowArgs {
+    const int32_t *seg_owner;
+    int64_t seg_base;
+    const int32_t *long_rows;
+    const int64_t *long_first;
+    int32_t *long_count;
+};
+
 // One warp per work item: a group of whole rows, or one segment of a long
 // row (a group of one row whose output is its slot of `partial`).  Segments
 // come first in the grid, so the longest items start first and the groups
@@ -93,7 +153,7 @@ spmm_kernel(const int32_t *__restrict__ colidx, const T *__restrict__ vals, cons
             const int64_t *__restrict__ short_start, const int32_t *__restrict__ short_len,
             const int64_t *__restrict__ group_first, int64_t n_groups, const int64_t *__restrict__ seg_start,
             const int32_t *__restrict__ seg_len, int64_t n_segs, int nvec, const T *__restrict__ X, int64_t ldx,
-            T *__restrict__ Y, int64_t ldy, T *__restrict__ partial, int64_t out_row_offset) {
+            T *__restrict__ Y, int64_t ldy, T *__restrict__ partial, int64_t out_row_offset, const LongRowArgs la) {
     using V = typename Vec<T>::type;
     constexpr int W = Vec<T>::width;
     // Gathers in flight per lane: B x NV vectors (B divides 32).
@@ -257,32 +317,36 @@ spmm_kernel(const int32_t *__restrict__ colidx, const T *__restrict__ vals, cons
         }
     }
     if (cur >= 0) store_row(cur, acc);
+    if (ACC && seg)
+        finish_segment<T, NV, ACC>((blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5, la.seg_owner, la.seg_base,
+                                   la.long_rows, la.long_first, la.long_count, nvec, Y, ldy, partial, out_row_offset);
 }
 
-// partial holds the segments seg_base, seg_base + 1, ... (long_first values
-// are absolute segment indices); output row = long row - out_row_offset.
+// Writing launches: long row r = the sum of its partial rows in segment
+// order (partial holds the segments seg_base, seg_base + 1, ...).
 template <typename T>
-__global__ void spmm_fixup_kernel(int64_t n_long, const int32_t *__restrict__ long_rows,
+__global__ void spmm_fixup_kernel(int64_t l0, int64_t n_long, const int32_t *__restrict__ long_rows,
                                   const int64_t *__restrict__ long_first, int nvec, const T *__restrict__ partial,
-                                  T *__restrict__ Y, int64_t ldy, int accumulate, int64_t seg_base,
-                                  int64_t out_row_offset) {
+                                  T *__restrict__ Y, int64_t ldy, int64_t seg_base, int64_t out_row_offset) {
     using V = typename Vec<T>::type;
     const int lane = threadIdx.x & 31;
-    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (r >= n_long) return;
+    const int64_t r = l0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (r >= l0 + n_long) return;
     const int64_t s0 = long_first[r] - seg_base, s1 = long_first[r + 1] - seg_base;
     const V *P = reinterpret_cast<const V *>(partial);
     V *out = reinterpret_cast<V *>(Y + ((int64_t)long_rows[r] - out_row_offset) * ldy);
     for (int vi = lane; vi < nvec; vi += 32) {
-        V acc = accumulate ? out[vi] : Vec<T>::zero();
+        V acc = Vec<T>::zero();
         for (int64_t s = s0; s < s1; ++s) Vec<T>::add(acc, P[s * nvec + vi]);
         out[vi] = acc;
     }
 }
 
-// The rows of one launch: a range of a plan's groups of whole rows, of its
-// segments of long rows and of its long rows for the fix-up.  The whole-row
-// arrays are the plan's own (group_first holds indices into them).
+// The rows of one launch: a range of a plan's groups of whole rows and a
+// range of its segments of long rows (segment indices from seg_base; each
+// long row's segments all in the range).  The whole-row and long-row arrays
+// are the plan's own (group_first, seg_owner and long_first hold indices
+// into them).
 struct SpmmWork {
     const int32_t *short_rows;
     const int64_t *short_start;
@@ -291,16 +355,18 @@ struct SpmmWork {
     int64_t n_groups;
     const int64_t *seg_start;
     const int32_t *seg_len;
+    const int32_t *seg_owner;
     int64_t n_segs, seg_base;
     const int32_t *long_rows;
     const int64_t *long_first;
-    int64_t n_long;
+    int32_t *long_count;
+    int64_t long0, n_long;  // the launch's long rows (for the fix-up of a writing launch)
     int64_t out_row_offset;
 };
 
 SpmmWork whole_plan(const SpmmPlan &p) {
     return SpmmWork{p.short_rows, p.short_start, p.short_len, p.group_first, p.n_groups, p.seg_start, p.seg_len,
-                    p.n_segs, 0, p.long_rows, p.long_first, p.n_long, 0};
+                    p.seg_owner, p.n_segs, 0, p.long_rows, p.long_first, p.long_count, 0, p.n_long, 0};
 }
 
 // One launch of spmm_kernel<T, NV, ACC> over groups [0, n_groups) and
@@ -314,10 +380,10 @@ cudaError_t launch_items(const int32_t *colidx, const T *vals, const SpmmWork &p
     switch ((int)ceil_div(nvec, 32)) {
 #define FRPCA_SPMM_CASE(NVV)                                                                                  \
     case NVV:                                                                                                 \
-        spmm_kernel<T, NVV, ACC><<<blocks, kThreads, 0, s>>>(colidx, vals, p.short_rows, p.short_start,       \
-                                                             p.short_len, p.group_first, n_groups, p.seg_start, \
-                                                             p.seg_len, n_segs, nvec, X, ldx, Y, ldy, partial,  \
-                                                             p.out_row_offset);                                \
+        spmm_kernel<T, NVV, ACC><<<blocks, kThreads, 0, s>>>(                                                 \
+            colidx, vals, p.short_rows, p.short_start, p.short_len, p.group_first, n_groups, p.seg_start,     \
+            p.seg_len, n_segs, nvec, X, ldx, Y, ldy, partial, p.out_row_offset,                                \
+            LongRowArgs{p.seg_owner, p.seg_base, p.long_rows, p.long_first, p.long_count});                   \
         break;
         FRPCA_SPMM_CASE(1)
         FRPCA_SPMM_CASE(2)
@@ -339,13 +405,13 @@ cudaError_t launch_typed(const DeviceCSR &A, const T *vals, const SpmmWork &p, i
         (e = cudaMemsetAsync(partial, 0, sizeof(T) * (size_t)p.n_segs * (size_t)nvec * W, s)) != cudaSuccess)
         return e;
     if (accumulate)
-        e = launch_items<T, true>(A.colidx, vals, p, p.n_groups, p.n_segs, nvec, X, ldx, Y, ldy, partial, s);
-    else
-        e = launch_items<T, false>(A.colidx, vals, p, p.n_groups, p.n_segs, nvec, X, ldx, Y, ldy, partial, s);
-    if (e != cudaSuccess) return e;
+        return launch_items<T, true>(A.colidx, vals, p, p.n_groups, p.n_segs, nvec, X, ldx, Y, ldy, partial, s);
+    if ((e = launch_items<T, false>(A.colidx, vals, p, p.n_groups, p.n_segs, nvec, X, ldx, Y, ldy, partial, s)) !=
+        cudaSuccess)
+        return e;
     if (p.n_long > 0) {
         spmm_fixup_kernel<T><<<(unsigned)ceil_div(p.n_long * 32, 256), 256, 0, s>>>(
-            p.n_long, p.long_rows, p.long_first, nvec, partial, Y, ldy, accumulate, p.seg_base, p.out_row_offset);
+            p.long0, p.n_long, p.long_rows, p.long_first, nvec, partial, Y, ldy, p.seg_base, p.out_row_offset);
         count_launch();
         return cudaGetLastError();
     }
@@ -363,6 +429,8 @@ void SpmmPlan::free_all() {
     dev_free(long_rows, stream);
     dev_free(long_first, stream);
     dev_free(group_first, stream);
+    dev_free(seg_owner, stream);
+    dev_free(long_count, stream);
     if (budget) budget->give(charged);
     charged = 0;
     short_rows = nullptr;
@@ -373,6 +441,8 @@ void SpmmPlan::free_all() {
     long_rows = nullptr;
     long_first = nullptr;
     group_first = nullptr;
+    seg_owner = nullptr;
+    long_count = nullptr;
     n_short = n_segs = n_long = n_groups = 0;
 }
 
@@ -388,7 +458,7 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
         err = "spmm plan: reading row pointers failed";
         return e;
     }
-    std::vector<int32_t> shorts, lrows, slen, shlen;
+    std::vector<int32_t> shorts, lrows, slen, shlen, sowner;
     std::vector<int64_t> shstart;
     std::vector<int64_t> sstart, lfirst;
     shorts.reserve((size_t)A.rows);
@@ -405,6 +475,7 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
             for (int64_t p = rp[i]; p < rp[i + 1]; p += plan.seg) {
                 sstart.push_back(p);
                 slen.push_back((int32_t)std::min<int64_t>(plan.seg, rp[i + 1] - p));
+                sowner.push_back((int32_t)(lrows.size() - 1));
             }
         }
     }
@@ -423,6 +494,7 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
     }
     plan.n_groups = (int64_t)gfirst.size();
     gfirst.push_back((int64_t)shorts.size());
+    const std::vector<int32_t> counts(lrows.size(), 0);
     plan.n_short = (int64_t)shorts.size();
     plan.n_long = (int64_t)lrows.size();
     plan.n_segs = (int64_t)sstart.size();
@@ -440,7 +512,9 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
         (e = up((void **)&plan.long_first, lfirst.data(), 8 * lfirst.size())) != cudaSuccess ||
         (e = up((void **)&plan.seg_start, sstart.data(), 8 * sstart.size())) != cudaSuccess ||
         (e = up((void **)&plan.seg_len, slen.data(), 4 * slen.size())) != cudaSuccess ||
-        (e = up((void **)&plan.group_first, gfirst.data(), 8 * gfirst.size())) != cudaSuccess) {
+        (e = up((void **)&plan.group_first, gfirst.data(), 8 * gfirst.size())) != cudaSuccess ||
+        (e = up((void **)&plan.seg_owner, sowner.data(), 4 * sowner.size())) != cudaSuccess ||
+        (e = up((void **)&plan.long_count, counts.data(), 4 * counts.size())) != cudaSuccess) {
         err = "spmm plan: device allocation failed";
         return e;
     }
@@ -471,7 +545,8 @@ __global__ void plan_fill_kernel(int64_t m, const int64_t *__restrict__ rowptr, 
                                  const int64_t *__restrict__ seg_off, int32_t *__restrict__ short_rows,
                                  int64_t *__restrict__ short_start, int32_t *__restrict__ short_len,
                                  int32_t *__restrict__ long_rows, int64_t *__restrict__ long_first,
-                                 int64_t *__restrict__ seg_start, int32_t *__restrict__ seg_len) {
+                                 int64_t *__restrict__ seg_start, int32_t *__restrict__ seg_len,
+                                 int32_t *__restrict__ seg_owner) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i == 0) long_first[long_pos[m]] = seg_off[m];
     if (i >= m) return;
@@ -490,6 +565,7 @@ __global__ void plan_fill_kernel(int64_t m, const int64_t *__restrict__ rowptr, 
     for (int64_t p = start, sidx = first; p < end; p += seg, ++sidx) {
         seg_start[sidx] = p;
         seg_len[sidx] = (int32_t)min((int64_t)seg, end - p);
+        seg_owner[sidx] = (int32_t)j;
     }
 }
 
@@ -627,14 +703,19 @@ cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *cons
             (e = alloc((void **)&plan.long_rows, 4 * (size_t)plan.n_long)) != cudaSuccess ||
             (e = alloc((void **)&plan.long_first, 8 * ((size_t)plan.n_long + 1))) != cudaSuccess ||
             (e = alloc((void **)&plan.seg_start, 8 * (size_t)plan.n_segs)) != cudaSuccess ||
-            (e = alloc((void **)&plan.seg_len, 4 * (size_t)plan.n_segs)) != cudaSuccess) {
+            (e = alloc((void **)&plan.seg_len, 4 * (size_t)plan.n_segs)) != cudaSuccess ||
+            (e = alloc((void **)&plan.seg_owner, 4 * (size_t)plan.n_segs)) != cudaSuccess ||
+            (e = alloc((void **)&plan.long_count, 4 * (size_t)plan.n_long)) != cudaSuccess ||
+            (plan.n_long > 0 &&
+             (e = cudaMemsetAsync(plan.long_count, 0, 4 * (size_t)plan.n_long, s)) != cudaSuccess)) {
             err = "spmm plan: device allocation failed";
             return e;
         }
         const Parts q = parts(c);
         plan_fill_kernel<<<(unsigned)ceil_div(A.rows, 256), 256, 0, s>>>(
             A.rows, A.rowptr, kDefaultSeg, q.is_short, q.is_long, q.short_pos, q.long_pos, q.seg_off, plan.short_rows,
-            plan.short_start, plan.short_len, plan.long_rows, plan.long_first, plan.seg_start, plan.seg_len);
+            plan.short_start, plan.short_len, plan.long_rows, plan.long_first, plan.seg_start, plan.seg_len,
+            plan.seg_owner);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) {
             err = "spmm plan: fill failed";
@@ -780,8 +861,8 @@ cudaError_t panel_launch(const PanelCSR &pc, int64_t b, int l, const void *Xb, i
     const int64_t r0 = pc.group_off[b], r1 = pc.group_off[b + 1];
     if (s1 == s0 && l1 == l0) return cudaSuccess;
     const SpmmWork w{p.short_rows, p.short_start, p.short_len, p.group_first + r0, r1 - r0, p.seg_start + g0,
-                     p.seg_len + g0, g1 - g0, g0,
-                     p.long_rows + l0, p.long_first + l0, l1 - l0, b * pc.src_rows};
+                     p.seg_len + g0, p.seg_owner + g0, g1 - g0, g0, p.long_rows, p.long_first, p.long_count,
+                     l0, l1 - l0, b * pc.src_rows};
     if (dt == FRPCA_F32)
         return launch_typed<float>(pc.virt, (const float *)pc.virt.vals, w, l, (const float *)Xb, ldx, (float *)Y,
                                    ldy, (float *)scratch, true, s);
@@ -818,12 +899,12 @@ cudaError_t launch_fused_sweep(const DeviceCSR &Pm, const SpmmPlan &prod, const 
         void *slot = (char *)ring + es * (size_t)((b & 1) * pc.panel_rows) * (size_t)ldr;
         // Rows b P .. b P + P-1 of P Q into the slot (every row written: the
         // producing plan keeps empty rows).
-        const int64_t l0 = pc.prod_long_off[b], l1 = pc.prod_long_off[b + 1];
         const int64_t g0 = pc.prod_seg_off[b], g1 = pc.prod_seg_off[b + 1];
+        const int64_t l0 = pc.prod_long_off[b], l1 = pc.prod_long_off[b + 1];
         const int64_t r0 = pc.prod_group_off[b], r1 = pc.prod_group_off[b + 1];
         const SpmmWork w{prod.short_rows, prod.short_start, prod.short_len, prod.group_first + r0, r1 - r0,
-                         prod.seg_start + g0, prod.seg_len + g0, g1 - g0, g0,
-                         prod.long_rows + l0, prod.long_first + l0, l1 - l0, b * pc.panel_rows};
+                         prod.seg_start + g0, prod.seg_len + g0, prod.seg_owner + g0, g1 - g0, g0,
+                         prod.long_rows, prod.long_first, prod.long_count, l0, l1 - l0, b * pc.panel_rows};
         if (dt == FRPCA_F32)
             e = launch_typed<float>(Pm, (const float *)Pm.vals, w, l, (const float *)Q, ldq, (float *)slot, ldr,
                                     (float *)scratch, false, s);
