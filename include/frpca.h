@@ -106,8 +106,9 @@ typedef struct frpca_create_opts {
     int panel_rows;           /* the pass that gathers rows of the larger dense block (A^T X
                                  when m >= n) reads that block in panels of this many rows,
                                  one after the other into the output, so a panel stays in
-                                 L2: 0 = automatic (131,072 rows when the block has at least
-                                 three times that many), -1 = off, > 0 = that many rows   */
+                                 L2: 0 = automatic (262,144 rows when the block has at least
+                                 three times that many, else 131,072 rows when it has at
+                                 least three times that), -1 = off, > 0 = that many rows */
     int fused_sweep;          /* with panels: 1 = each power-iteration pair of passes
                                  (A^T (A Q) for Alg. 6) runs as one sweep, panel by panel,
                                  the intermediate panel of A Q staying in L2 instead of

@@ -8,14 +8,15 @@
 // accumulators (H.H, and the five correction terms), as in the split-BF16
 // Gram: every product of BF16 terms is exact in FP32, so the result carries
 // float accuracy.  W is split once per CTA and stays in shared memory as the
-// B operand (K-major, no swizzle) for all of the CTA's 128-row tiles of M; a
-// tile is read once from HBM in chunks of 64 columns that are split in
-// registers (the next chunk is loaded while the current one is stored and
-// multiplied).  Tiles alternate between two TMEM accumulator pairs, so a
-// tile's result is read back (tcgen05.ld) and written to Y, 32 consecutive
-// floats of a row per thread, while the next tile's MMAs run.  A tile's rows
-// are read completely before they are written, so Y may be M itself (same
-// leading dimension).
+// B operand (K-major, no swizzle) for all of the CTA's 128-row tiles of M.  A
+// tile is read once from HBM in chunks of 32 columns: raw FP32 chunks arrive
+// in shared memory by cp.async three chunks ahead (four raw stages, without
+// holding registers), and each is split into one of two BF16 operand stages,
+// so a chunk is split while the previous one's MMAs run.  Tiles alternate
+// between two TMEM accumulator pairs, so a tile's result is read back
+// (tcgen05.ld) and written to Y, 32 consecutive floats of a row per thread,
+// while the next tile's MMAs run.  A tile's rows are read completely before
+// they are written, so Y may be M itself (same leading dimension).
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -30,52 +31,42 @@ namespace {
 using namespace tc;
 
 constexpr int kAtThreads = 256;
-constexpr int kAtRows = 128;                   // rows of M per tile
-constexpr int kAtKc = 64;                      // columns of M (K) per chunk
-constexpr int kAtOp = kAtRows * kAtKc * 2;     // one BF16 operand of a chunk: 16 KiB
-constexpr int kAtMaxChunks = 2;                // l <= 128
-constexpr int kAtStage = 3 * kAtOp;            // the three splits of one chunk of M
+constexpr int kAtRows = 128;                    // rows of M per tile
+constexpr int kAtKc = 32;                       // columns of M (K) per chunk
+constexpr int kAtOp = kAtRows * kAtKc * 2;      // one BF16 operand of a chunk: 8 KiB
+constexpr int kAtMaxChunks = 4;                 // l <= 128
+constexpr int kAtStage = 3 * kAtOp;             // the three splits of one chunk of M: 24 KiB
+constexpr int kAtRaw = kAtRows * kAtKc * 4;     // one raw FP32 chunk: 16 KiB
+constexpr int kAtRawStages = 4;                 // raw chunks in flight: three ahead of the one being split
 constexpr int kAtBytesB = 3 * kAtMaxChunks * kAtOp;  // W, resident: 96 KiB
-constexpr int kAtSmem = kAtBytesB + 2 * kAtStage + 64;
+constexpr int kAtSmem = kAtBytesB + 2 * kAtStage + kAtRawStages * kAtRaw + 64;
 
-// One chunk of M for a thread: items (row, 8-column group) t + 256 u.
-struct AtRegs {
-    float4 v[4][2];
-};
-
-__device__ inline void at_load(const float *__restrict__ M, int64_t ldm, int64_t R, int l, int64_t row0, int c,
-                               AtRegs &a) {
+// Chunk c (columns 32 c ..) of the tile at row0 into a raw stage (row-major,
+// 32 floats a row): thread t copies 16-byte groups t, t + 256, t + 512,
+// t + 768 (row = group / 8); parts past row R or column l are zero-filled.
+__device__ inline void at_fetch(const float *__restrict__ M, int64_t ldm, int64_t R, int l, int64_t row0, int c,
+                                uint32_t raw) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int it = threadIdx.x + u * kAtThreads;
-        const int r = it / (kAtKc / 8), g = it % (kAtKc / 8);
+        const int r = it >> 3, j = 4 * (it & 7);
         const int64_t row = row0 + r;
-        const int k0 = c * kAtKc + 8 * g;
-        float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-        if (row < R && k0 < l) {  // k0 + 8 <= round_up(l, 8) <= ldm
-            const float4 *src = reinterpret_cast<const float4 *>(M + row * ldm + k0);
-            x0 = __ldcs(src);
-            x1 = __ldcs(src + 1);
-            if (k0 + 8 > l) {  // columns l .. of the padded row are not data
-                float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-#pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    if (k0 + e >= l) xv[e] = 0.0f;
-                x0 = make_float4(xv[0], xv[1], xv[2], xv[3]);
-                x1 = make_float4(xv[4], xv[5], xv[6], xv[7]);
-            }
-        }
-        a.v[u][0] = x0;
-        a.v[u][1] = x1;
+        const int k0 = c * kAtKc + j;
+        const int valid = (row < R && k0 < l) ? min(4, l - k0) : 0;
+        cp_async16_zfill(raw + (uint32_t)(r * kAtKc + j) * 4, valid ? (const void *)(M + row * ldm + k0) : (const void *)M,
+                         4 * valid);
     }
 }
 
-__device__ inline void at_store(const AtRegs &a, unsigned char *stage) {
+// A raw chunk into the three BF16 operands of a stage: thread t takes items
+// t and t + 256 of (row, 8-column group), 8 floats each.
+__device__ inline void at_split(const float *__restrict__ raw, unsigned char *stage) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 2; ++u) {
         const int it = threadIdx.x + u * kAtThreads;
-        const int r = it / (kAtKc / 8), g = it % (kAtKc / 8);
-        const float4 x0 = a.v[u][0], x1 = a.v[u][1];
+        const int r = it >> 2, g = it & 3;
+        const float4 x0 = *reinterpret_cast<const float4 *>(raw + r * kAtKc + 8 * g);
+        const float4 x1 = *reinterpret_cast<const float4 *>(raw + r * kAtKc + 8 * g + 4);
         const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
         __align__(16) __nv_bfloat16 hh[8], mm[8], ss[8];
 #pragma unroll
@@ -121,28 +112,43 @@ __device__ inline void at_epilogue(uint32_t tmem, int pair, int64_t row0, int64_
     }
 }
 
-// Persistent CTA per SM over 128-row tiles.  A tile's chunks are split into
-// the two operand stages and multiplied into TMEM accumulator pair
-// (tile index) % 2; the previous tile's pair is read out and written to Y
-// while the current tile's MMAs run.
+// Persistent CTA per SM over 128-row tiles, walked as one sequence of
+// chunks (tile-major): chunk i is fetched three iterations ahead into raw
+// stage i % 4, split into operand stage i % 2 once the MMAs of chunk i - 2
+// are done, and multiplied into TMEM accumulator pair (tile index) % 2; the
+// previous tile's pair is read out and written to Y while the current tile's
+// MMAs run.
 __global__ void __launch_bounds__(kAtThreads, 1)
 apply_tc_kernel(int64_t R, int l, int kout, const float *M, int64_t ldm, const float *__restrict__ W, float *Y,
                 int64_t ldy, int *status, long long limit_cycles) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *Bres = smem;                       // chunk c, split z at (3 c + z) kAtOp
-    unsigned char *stages = smem + kAtBytesB;         // stage b at b kAtStage
+    unsigned char *stages = smem + kAtBytesB;         // operand stage b at b kAtStage
+    float *raws = reinterpret_cast<float *>(stages + 2 * kAtStage);  // raw stage i at i kAtRaw bytes
     // mbar[0..1]: operand stages; mbar[2..3]: accumulator pairs (one commit per tile).
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + kAtBytesB + 2 * kAtStage);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + 2 * kAtStage + kAtRawStages * kAtRaw);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 4);
     const int warp = threadIdx.x >> 5, t = threadIdx.x;
     const int nch = (l + kAtKc - 1) / kAtKc;
     const bool vec4 = (ldy % 4) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15u) == 0;
+    const uint32_t raw_addr = smem_u32(raws);
+    const int64_t ntiles = ceil_div(R, kAtRows);
+    const int64_t mine = (int64_t)blockIdx.x < ntiles ? ceil_div(ntiles - blockIdx.x, gridDim.x) : 0;
+    const int64_t nchunks = mine * nch;
+    auto fetch = [&](int64_t i) {  // chunk i of this CTA's sequence into raw stage i % 4
+        if (i < nchunks)
+            at_fetch(M, ldm, R, l, (blockIdx.x + (i / nch) * gridDim.x) * kAtRows, (int)(i % nch),
+                     raw_addr + (uint32_t)((i % kAtRawStages) * kAtRaw));
+        cp_async_commit();  // one group per chunk, empty past the end
+    };
+    // The first chunks' copies overlap the setup.
+    for (int64_t i = 0; i < kAtRawStages - 1; ++i) fetch(i);
     if (warp == 0) tmem_alloc(tmem_slot, 512);
     if (t == 0) {
         for (int i = 0; i < 4; ++i) mbar_init(smem_u32(mbar + i), 1);
         fence_mbar_init();
     }
-    // W as the B operand: element (n = output column, k) at op_offset(n, k mod 64).
+    // W as the B operand: element (n = output column, k) at op_offset(n, k mod 32).
     for (int it = t; it < kAtRows * nch * (kAtKc / 8); it += kAtThreads) {
         const int n = it % kAtRows, grp = it / kAtRows;
         const int k0 = 8 * grp, c = k0 / kAtKc;
@@ -163,59 +169,55 @@ apply_tc_kernel(int64_t R, int l, int kout, const float *M, int64_t ldm, const f
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int64_t ntiles = ceil_div(R, kAtRows);
     uint32_t uses[2] = {0u, 0u};
     bool ok = true;
-    AtRegs areg;
-    if ((int64_t)blockIdx.x < ntiles) at_load(M, ldm, R, l, (int64_t)blockIdx.x * kAtRows, 0, areg);
     int64_t prev_row0 = -1;  // the previous tile, whose pair is still to be written out
     int prev_pair = 0;
-    int64_t it_no = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it_no) {
-        const int64_t row0 = tile * kAtRows;
-        const int pair = (int)(it_no & 1);
-        const uint32_t d_main = tmem + (uint32_t)pair * 256, d_corr = d_main + 128;
-        for (int c = 0; c < nch; ++c) {
-            const int b = c & 1;
-            unsigned char *stage = stages + b * kAtStage;
-            if (uses[b] > 0) {  // the buffer's previous MMAs must be done before it is rewritten
-                const bool done = mbar_wait_bounded(smem_u32(mbar + b), (uses[b] - 1) & 1, limit_cycles);
-                if (!__syncthreads_and(done)) {
-                    ok = false;
-                    break;
-                }
+    for (int64_t i = 0; i < nchunks && ok; ++i) {
+        const int64_t j = i / nch;  // tile of this CTA's sequence
+        const int c = (int)(i % nch);
+        const int64_t row0 = (blockIdx.x + j * gridDim.x) * kAtRows;
+        const int pair = (int)(j & 1);
+        const int b = (int)(i & 1);
+        unsigned char *stage = stages + b * kAtStage;
+        cp_async_wait<kAtRawStages - 2>();  // chunk i has landed (this thread's copies)
+        __syncthreads();                    // ... and every thread's
+        // Raw stage (i + 3) % 4 held chunk i - 1, split in the last iteration.
+        fetch(i + kAtRawStages - 1);
+        if (uses[b] > 0) {  // the stage's previous MMAs (chunk i - 2) must be done before it is rewritten
+            const bool done = mbar_wait_bounded(smem_u32(mbar + b), (uses[b] - 1) & 1, limit_cycles);
+            if (!__syncthreads_and(done)) {
+                ok = false;
+                break;
             }
-            at_store(areg, stage);
-            if (c + 1 < nch)
-                at_load(M, ldm, R, l, row0, c + 1, areg);
-            else if (tile + gridDim.x < ntiles)
-                at_load(M, ldm, R, l, row0 + (int64_t)gridDim.x * kAtRows, 0, areg);
-            fence_async_smem();
-            fence_before();
-            __syncthreads();
-            fence_after();
-            if (t == 0) {
-                const uint32_t a = smem_u32(stage), bb = smem_u32(Bres + 3 * c * kAtOp);
-#pragma unroll 1
-                for (int ks = 0; ks < kAtKc / 16; ++ks) {
-                    const uint32_t koff = (uint32_t)(2 * ks * kLbo);
-                    mma_split6(d_main, d_corr, make_desc(a + koff), make_desc(a + kAtOp + koff),
-                               make_desc(a + 2 * kAtOp + koff), make_desc(bb + koff), make_desc(bb + kAtOp + koff),
-                               make_desc(bb + 2 * kAtOp + koff), c > 0 || ks > 0);
-                }
-                mma_commit(smem_u32(mbar + b));
-                if (c + 1 == nch) mma_commit(smem_u32(mbar + 2 + pair));
-            }
-            uses[b] += 1;
         }
-        if (!ok) break;
-        // The previous tile's pair is final once its own commit (the
-        // (it_no - 1) / 2-th on that pair's barrier, whose next commit is
-        // only issued after this wait) has arrived: write it out while this
+        at_split(raws + (i % kAtRawStages) * (kAtRaw / 4), stage);
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (t == 0) {
+            const uint32_t d_main = tmem + (uint32_t)pair * 256, d_corr = d_main + 128;
+            const uint32_t a = smem_u32(stage), bb = smem_u32(Bres + 3 * c * kAtOp);
+#pragma unroll
+            for (int ks = 0; ks < kAtKc / 16; ++ks) {
+                const uint32_t koff = (uint32_t)(2 * ks * kLbo);
+                mma_split6(d_main, d_corr, make_desc(a + koff), make_desc(a + kAtOp + koff),
+                           make_desc(a + 2 * kAtOp + koff), make_desc(bb + koff), make_desc(bb + kAtOp + koff),
+                           make_desc(bb + 2 * kAtOp + koff), c > 0 || ks > 0);
+            }
+            mma_commit(smem_u32(mbar + b));
+            if (c + 1 == nch) mma_commit(smem_u32(mbar + 2 + pair));
+        }
+        uses[b] += 1;
+        if (c + 1 < nch) continue;
+        // Tile j is issued.  The previous tile's pair is final once its own
+        // commit (the (j - 1) / 2-th on that pair's barrier, whose next commit
+        // is only issued after this wait) has arrived: write it out while this
         // tile's MMAs run.
         if (prev_row0 >= 0) {
             const bool done =
-                mbar_wait_bounded(smem_u32(mbar + 2 + prev_pair), (uint32_t)(((it_no - 1) >> 1) & 1), limit_cycles);
+                mbar_wait_bounded(smem_u32(mbar + 2 + prev_pair), (uint32_t)(((j - 1) >> 1) & 1), limit_cycles);
             if (!__syncthreads_and(done)) {
                 ok = false;
                 break;
@@ -228,8 +230,8 @@ apply_tc_kernel(int64_t R, int l, int kout, const float *M, int64_t ldm, const f
         prev_pair = pair;
     }
     if (ok && prev_row0 >= 0) {
-        const bool done =
-            mbar_wait_bounded(smem_u32(mbar + 2 + prev_pair), (uint32_t)(((it_no - 1) >> 1) & 1), limit_cycles);
+        const int64_t j = mine - 1;
+        const bool done = mbar_wait_bounded(smem_u32(mbar + 2 + prev_pair), (uint32_t)((j >> 1) & 1), limit_cycles);
         if (__syncthreads_and(done)) {
             fence_after();
             at_epilogue(tmem, prev_pair, prev_row0, R, kout, Y, ldy, vec4);
@@ -237,6 +239,7 @@ apply_tc_kernel(int64_t R, int l, int kout, const float *M, int64_t ldm, const f
             ok = false;
         }
     }
+    cp_async_wait<0>();  // no copy into shared memory outlives the CTA
     if (!ok) {
         // A wait ran out: give the MMAs already issued (covered by each
         // stage's newest commit) a bounded chance to finish before the TMEM

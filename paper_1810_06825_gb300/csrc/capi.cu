@@ -663,9 +663,14 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
     if ((e = csr_transpose(h->A, h->AT, (int32_t *)h->t_perm.ptr, h->ws_scratch, h->ws_scan, h->stream)) != cudaSuccess)
         return bail(cuda_fail(h, e, "transpose"));
     std::string perr;
-    // Rows of the larger dense block per panel of the gathering pass.
+    // Rows of the larger dense block per panel of the gathering pass: about
+    // one L2 of float rows at l <= 128 (262,144 rows, 128 MiB).  On the 12M x
+    // 320K workload two A^T passes took 54.0, 45.4, 40.3, 40.2 and 42.9 ms
+    // with panels of 64K, 128K, 256K, 384K and 512K rows: a larger panel
+    // halves the passes over the output, and past L2 its rows start to miss.
     const int pr = opts ? opts->panel_rows : 0;
-    const int64_t P = pr > 0 ? (int64_t)pr : (int64_t)131072;
+    const int64_t big_rows = std::max(m, n);
+    const int64_t P = pr > 0 ? (int64_t)pr : (big_rows >= 3 * 262144 ? (int64_t)262144 : (int64_t)131072);
     {
         const DeviceCSR *mats[2] = {&h->A, &h->AT};
         SpmmPlan *plans[2] = {&h->planA, &h->planAT};
@@ -677,8 +682,8 @@ frpca_status frpca_create(const frpca_csr *csr, const frpca_create_opts *opts, f
     }
     {
         // Panels over the rows of the larger dense block when it is well
-        // beyond L2: 131,072 rows (64 MiB of float rows at l <= 128) each.
-        const int64_t big = std::max(m, n);
+        // beyond L2 (at least three panels).
+        const int64_t big = big_rows;
         h->fused = opts && opts->fused_sweep > 0;
         h->pan_trans = m >= n ? 1 : 0;
         const DeviceCSR &C = m >= n ? h->AT : h->A;

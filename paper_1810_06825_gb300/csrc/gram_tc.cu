@@ -48,10 +48,6 @@ constexpr int kGroup = 4;                          // chunks accumulated in TMEM
 constexpr int kSmemBytes = kOpStage + kRawStages * kRawBytes + 64;
 constexpr uint32_t kTmemCols = 512;                // two pairs of 128-column FP32 accumulators
 
-__device__ inline void cp_async16_zfill(uint32_t dst, const void *src, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-
 // Thread t copies column group j4 = t % 32 (4 floats) of the 8-row groups
 // rg = t / 32 and rg + 8 of the chunk starting at row0 into raw (row-major,
 // 128 floats per row): 16 asynchronous 16-byte copies, the parts past row R
@@ -73,9 +69,6 @@ __device__ inline void fetch_chunk(const float *__restrict__ M, int64_t ld, int6
         }
 }
 
-__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ inline void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ inline void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Splits the raw chunk into the three BF16 operands: for each of its 4 columns
 // and 2 row groups a thread writes one full 16-byte core-matrix row.
@@ -218,7 +211,7 @@ gram_tc_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, float 
     int64_t issued = -1;   // last chunk whose MMAs were issued
     for (int64_t i = 0; i < nmine && ok; ++i) {
         const int st = (int)(i & 1);
-        cp_async_wait1();  // chunk i has landed (chunk i + 1 may still be in flight)
+        cp_async_wait<1>();  // chunk i has landed (chunk i + 1 may still be in flight)
         __syncthreads();
         if (i >= 1 && !(ok = wait_commit(i - 1))) break;  // the operand stage is free
         split_chunk(raw + st * (kRawBytes / 4), opH, opM, opS);
@@ -264,7 +257,7 @@ gram_tc_kernel(int64_t R, int l, const float *__restrict__ M, int64_t ld, float 
         // finish before the TMEM is released.
         (void)mbar_wait_bounded(smem_u32(mbar), (uint32_t)(issued & 1), limit_cycles);
     }
-    cp_async_wait0();
+    cp_async_wait<0>();
     if (!ok && threadIdx.x == 0) set_status(status, FRPCA_ERR_TIMEOUT);
     __syncthreads();
     // This CTA's partial B (l x l) in FP64, written even when it had no chunk.

@@ -108,6 +108,20 @@ __device__ inline void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Asynchronous 16-byte global -> shared copy (cp.async, L2 only): the
+// src_bytes < 16 first bytes are copied and the rest of the 16 zero-filled
+// (src_bytes = 0: nothing is read from src).  Commit groups are waited for
+// in order: cp_async_wait<n>() returns when at most n of this thread's
+// groups are still in flight.
+__device__ inline void cp_async16_zfill(uint32_t dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Splits x into three BF16 terms h + m + s (their sum is x to within 2^-27 |x|).
 __device__ inline void split3(float x, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &s) {
     h = __float2bfloat16_rn(x);

@@ -291,12 +291,14 @@ def test_eigsvd_matches_oracle(R, l, cond, dtype):
     assert max_principal_sine(U, Uo) <= (1e-10 if dtype == np.float64 else 1e-3)
 
 
-@pytest.mark.parametrize("R,l", [(1, 1), (127, 7), (129, 64), (300, 65), (1000, 128), (4097, 120)])
+@pytest.mark.parametrize("R,l", [(1, 1), (127, 7), (129, 64), (300, 65), (1000, 128), (4097, 120), (40000, 33),
+                                 (60001, 120)])
 def test_eigsvd_apply_step_elementwise(R, l):
     """Step 5 of Alg. 2 in FP32 (U = M V spdiags(1./S), on the tensor cores for
     l <= 128): every entry of U against the product formed in FP64 from the
     returned S and V, with the float accumulation bound of an l-term sum;
-    covers ragged 128-row tiles and the second 64-column chunk."""
+    covers ragged 128-row tiles, ragged 32-column chunks and (R > 152 x 128)
+    several tiles per CTA."""
     rng = np.random.default_rng(R + l)
     Uq, _ = np.linalg.qr(rng.standard_normal((R, l)))
     Vq, _ = np.linalg.qr(rng.standard_normal((l, l)))
