@@ -10,12 +10,12 @@
 // float accuracy.  W is split once per CTA and stays in shared memory as the
 // B operand (K-major, no swizzle) for all of the CTA's 128-row tiles of M.  A
 // tile is read once from HBM in chunks of 32 columns: raw FP32 chunks arrive
-// in shared memory by cp.async three chunks ahead (four raw stages, without
+// in shared memory by cp.async two chunks ahead (three raw stages, without
 // holding registers), and each is split into one of two BF16 operand stages,
 // so a chunk is split while the previous one's MMAs run.  Tiles alternate
 // between two TMEM accumulator pairs, so a tile's result is read back
-// (tcgen05.ld) and written to Y, 32 consecutive floats of a row per thread,
-// while the next tile's MMAs run.  A tile's rows are read completely before
+// (tcgen05.ld), turned around through shared memory and written to Y in
+// 128-byte row segments while the next tile's MMAs run.  A tile's rows are read completely before
 // they are written, so Y may be M itself (same leading dimension).
 #include <algorithm>
 
@@ -37,9 +37,11 @@ constexpr int kAtOp = kAtRows * kAtKc * 2;      // one BF16 operand of a chunk: 
 constexpr int kAtMaxChunks = 4;                 // l <= 128
 constexpr int kAtStage = 3 * kAtOp;             // the three splits of one chunk of M: 24 KiB
 constexpr int kAtRaw = kAtRows * kAtKc * 4;     // one raw FP32 chunk: 16 KiB
-constexpr int kAtRawStages = 4;                 // raw chunks in flight: three ahead of the one being split
+constexpr int kAtRawStages = 3;                 // raw chunks in flight: two ahead of the one being split
 constexpr int kAtBytesB = 3 * kAtMaxChunks * kAtOp;  // W, resident: 96 KiB
-constexpr int kAtSmem = kAtBytesB + 2 * kAtStage + kAtRawStages * kAtRaw + 64;
+constexpr int kAtTpitch = 33;                   // floats per row of a warp's 32 x 32 transpose buffer
+constexpr int kAtTbuf = (kAtThreads / 32) * 32 * kAtTpitch * 4;  // 33 KiB
+constexpr int kAtSmem = kAtBytesB + 2 * kAtStage + kAtRawStages * kAtRaw + kAtTbuf + 64;
 
 // Chunk c (columns 32 c ..) of the tile at row0 into a raw stage (row-major,
 // 32 floats a row): thread t copies 16-byte groups t, t + 256, t + 512,
@@ -78,18 +80,20 @@ __device__ inline void at_split(const float *__restrict__ raw, unsigned char *st
     }
 }
 
-// Writes this thread's part of a finished tile from TMEM accumulator pair
-// `pair` straight to Y: warp w holds rows 32 (w % 4) .. +31 of the tile (its
-// TMEM lanes) and columns 64 (w / 4) .. +63, so every thread writes runs of
-// 32 consecutive floats of one row.
+// Writes a finished tile from TMEM accumulator pair `pair` to Y: warp w
+// holds rows 32 (w % 4) .. +31 of the tile (its TMEM lanes) and columns
+// 64 (w / 4) .. +63.  A 32 x 32 block read from TMEM (a row per thread) is
+// turned around in the warp's shared-memory buffer (pitch 33 floats: no bank
+// conflicts either way), so each store writes four 128-byte row segments
+// instead of 32 scattered 16-byte pieces.
 __device__ inline void at_epilogue(uint32_t tmem, int pair, int64_t row0, int64_t R, int kout, float *Y, int64_t ldy,
-                                   bool vec4) {
+                                   bool vec4, float *tbuf) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = 32 * (warp & 3) + lane;
+    const int rbase = 32 * (warp & 3);
     const int col0 = 64 * (warp >> 2);
-    const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t lane_addr = (uint32_t)rbase << 16;
     const uint32_t d_main = tmem + (uint32_t)pair * 256, d_corr = d_main + 128;
-    const int64_t row = row0 + r;
+    const int cg = 4 * (lane & 7), rsub = lane >> 3;  // this thread's 4 columns, and row within 4
 #pragma unroll 1
     for (int q = 0; q < 2; ++q) {
         const int c0 = col0 + 32 * q;
@@ -97,24 +101,33 @@ __device__ inline void at_epilogue(uint32_t tmem, int pair, int64_t row0, int64_
         float vm[32], vc[32];
         tmem_ld32(d_main + lane_addr + c0, vm);
         tmem_ld32(d_corr + lane_addr + c0, vc);
-        if (row >= R) continue;
-        float *yr = Y + row * ldy + c0;
-        if (vec4 && c0 + 32 <= kout) {
 #pragma unroll
-            for (int i = 0; i < 32; i += 4)
-                *reinterpret_cast<float4 *>(yr + i) =
-                    make_float4(vm[i] + vc[i], vm[i + 1] + vc[i + 1], vm[i + 2] + vc[i + 2], vm[i + 3] + vc[i + 3]);
-        } else {
+        for (int i = 0; i < 32; ++i) tbuf[lane * kAtTpitch + i] = vm[i] + vc[i];
+        __syncwarp();
+        const int col = c0 + cg;
+#pragma unroll 4
+        for (int k = 0; k < 8; ++k) {
+            const int rr = 4 * k + rsub;
+            const int64_t row = row0 + rbase + rr;
+            const float *src = tbuf + rr * kAtTpitch + cg;
+            if (row < R) {
+                float *dst = Y + row * ldy + col;
+                if (vec4 && col + 4 <= kout) {
+                    *reinterpret_cast<float4 *>(dst) = make_float4(src[0], src[1], src[2], src[3]);
+                } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-                if (c0 + i < kout) yr[i] = vm[i] + vc[i];
+                    for (int e = 0; e < 4; ++e)
+                        if (col + e < kout) dst[e] = src[e];
+                }
+            }
         }
+        __syncwarp();
     }
 }
 
 // Persistent CTA per SM over 128-row tiles, walked as one sequence of
-// chunks (tile-major): chunk i is fetched three iterations ahead into raw
-// stage i % 4, split into operand stage i % 2 once the MMAs of chunk i - 2
+// chunks (tile-major): chunk i is fetched two iterations ahead into raw
+// stage i % 3, split into operand stage i % 2 once the MMAs of chunk i - 2
 // are done, and multiplied into TMEM accumulator pair (tile index) % 2; the
 // previous tile's pair is read out and written to Y while the current tile's
 // MMAs run.
@@ -125,8 +138,10 @@ apply_tc_kernel(int64_t R, int l, int kout, const float *M, int64_t ldm, const f
     unsigned char *Bres = smem;                       // chunk c, split z at (3 c + z) kAtOp
     unsigned char *stages = smem + kAtBytesB;         // operand stage b at b kAtStage
     float *raws = reinterpret_cast<float *>(stages + 2 * kAtStage);  // raw stage i at i kAtRaw bytes
+    float *tbufs = reinterpret_cast<float *>(stages + 2 * kAtStage + kAtRawStages * kAtRaw);
+    float *tbuf = tbufs + (threadIdx.x >> 5) * 32 * kAtTpitch;  // this warp's transpose buffer
     // mbar[0..1]: operand stages; mbar[2..3]: accumulator pairs (one commit per tile).
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + 2 * kAtStage + kAtRawStages * kAtRaw);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + 2 * kAtStage + kAtRawStages * kAtRaw + kAtTbuf);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 4);
     const int warp = threadIdx.x >> 5, t = threadIdx.x;
     const int nch = (l + kAtKc - 1) / kAtKc;
@@ -135,7 +150,7 @@ apply_tc_kernel(int64_t R, int l, int kout, const float *M, int64_t ldm, const f
     const int64_t ntiles = ceil_div(R, kAtRows);
     const int64_t mine = (int64_t)blockIdx.x < ntiles ? ceil_div(ntiles - blockIdx.x, gridDim.x) : 0;
     const int64_t nchunks = mine * nch;
-    auto fetch = [&](int64_t i) {  // chunk i of this CTA's sequence into raw stage i % 4
+    auto fetch = [&](int64_t i) {  // chunk i of this CTA's sequence into raw stage i % kAtRawStages
         if (i < nchunks)
             at_fetch(M, ldm, R, l, (blockIdx.x + (i / nch) * gridDim.x) * kAtRows, (int)(i % nch),
                      raw_addr + (uint32_t)((i % kAtRawStages) * kAtRaw));
@@ -182,7 +197,8 @@ apply_tc_kernel(int64_t R, int l, int kout, const float *M, int64_t ldm, const f
         unsigned char *stage = stages + b * kAtStage;
         cp_async_wait<kAtRawStages - 2>();  // chunk i has landed (this thread's copies)
         __syncthreads();                    // ... and every thread's
-        // Raw stage (i + 3) % 4 held chunk i - 1, split in the last iteration.
+        // Raw stage (i + kAtRawStages - 1) % kAtRawStages held chunk i - 1,
+        // split in the last iteration.
         fetch(i + kAtRawStages - 1);
         if (uses[b] > 0) {  // the stage's previous MMAs (chunk i - 2) must be done before it is rewritten
             const bool done = mbar_wait_bounded(smem_u32(mbar + b), (uses[b] - 1) & 1, limit_cycles);
@@ -223,7 +239,7 @@ apply_tc_kernel(int64_t R, int l, int kout, const float *M, int64_t ldm, const f
                 break;
             }
             fence_after();
-            at_epilogue(tmem, prev_pair, prev_row0, R, kout, Y, ldy, vec4);
+            at_epilogue(tmem, prev_pair, prev_row0, R, kout, Y, ldy, vec4, tbuf);
             fence_before();
         }
         prev_row0 = row0;
@@ -234,7 +250,7 @@ apply_tc_kernel(int64_t R, int l, int kout, const float *M, int64_t ldm, const f
         const bool done = mbar_wait_bounded(smem_u32(mbar + 2 + prev_pair), (uint32_t)((j >> 1) & 1), limit_cycles);
         if (__syncthreads_and(done)) {
             fence_after();
-            at_epilogue(tmem, prev_pair, prev_row0, R, kout, Y, ldy, vec4);
+            at_epilogue(tmem, prev_pair, prev_row0, R, kout, Y, ldy, vec4, tbuf);
         } else {
             ok = false;
         }
