@@ -70,26 +70,24 @@ __device__ inline void fetch_chunk(const float *__restrict__ M, int64_t ld, int6
 }
 
 
-// Splits the raw chunk into the three BF16 operands: for each of its 4 columns
-// and 2 row groups a thread writes one full 16-byte core-matrix row.
+// Splits the raw chunk into the three BF16 operands.  Lane c of warp rg
+// takes columns c, c + 32, c + 64, c + 96 of the 8-row groups rg and rg + 8:
+// it reads each column's 8 values (a warp reads 32 consecutive floats of a
+// row: one wavefront) and writes one 16-byte core-matrix row per column and
+// operand, the warp's 32 stores covering 512 contiguous bytes (no bank
+// conflicts; with 4 consecutive columns per thread they were 16-way).
 __device__ inline void split_chunk(const float *__restrict__ raw, unsigned char *opH, unsigned char *opM,
                                    unsigned char *opS) {
-    const int t = threadIdx.x, j4 = t & 31, rg = t >> 5;
+    const int t = threadIdx.x, lane = t & 31, rg = t >> 5;
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
         const int r = (rg + 8 * g) * 8;
-        float4 x[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = *reinterpret_cast<const float4 *>(raw + (r + u) * kTile + j4 * 4);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const int j = j4 * 4 + e;
+            const int j = lane + 32 * e;
             __align__(16) __nv_bfloat16 h[8], m[8], sp[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float xv = e == 0 ? x[u].x : e == 1 ? x[u].y : e == 2 ? x[u].z : x[u].w;
-                split3(xv, h[u], m[u], sp[u]);
-            }
+            for (int u = 0; u < 8; ++u) split3(raw[(r + u) * kTile + j], h[u], m[u], sp[u]);
             const int off = op_offset(j, r);
             *reinterpret_cast<uint4 *>(opH + off) = *reinterpret_cast<const uint4 *>(h);
             *reinterpret_cast<uint4 *>(opM + off) = *reinterpret_cast<const uint4 *>(m);
@@ -126,30 +124,40 @@ __device__ inline void df_add(float &hi, float &lo, float a, float b) {
 // Adds accumulator pair `pair` (main, correction) of TMEM into this CTA's
 // double-float copy of B (acc_hi / acc_lo, 128 x 128 floats each, L2-resident):
 // warp w reads TMEM lanes 32 (w % 4) .. +31 (rows of B) and the 64 columns
-// 64 (w / 4) .. +63, 16 at a time.
+// 64 (w / 4) .. +63, 16 at a time.  All of a thread's loads of the copy are
+// issued before the first is used (one L2 round trip, not four).
 __device__ inline void drain_pair(uint32_t tmem, int pair, float *__restrict__ acc_hi, float *__restrict__ acc_lo) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = 32 * (warp & 3) + lane;
     const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
     const uint32_t d_main = tmem + (uint32_t)pair * 2 * kTile, d_corr = d_main + kTile;
-#pragma unroll 1
+    const int cbase = 64 * (warp >> 2);
+    float4 *ph = reinterpret_cast<float4 *>(acc_hi + row * kTile + cbase);
+    float4 *pl = reinterpret_cast<float4 *>(acc_lo + row * kTile + cbase);
+    float4 h[16], o[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        h[u] = ph[u];
+        o[u] = pl[u];
+    }
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int col0 = 64 * (warp >> 2) + 16 * q;
         float vm[16], vc[16];
-        tmem_ld16(d_main + lane_addr + col0, vm);
-        tmem_ld16(d_corr + lane_addr + col0, vc);
-        float4 *ph = reinterpret_cast<float4 *>(acc_hi + row * kTile + col0);
-        float4 *pl = reinterpret_cast<float4 *>(acc_lo + row * kTile + col0);
+        tmem_ld16(d_main + lane_addr + cbase + 16 * q, vm);
+        tmem_ld16(d_corr + lane_addr + cbase + 16 * q, vc);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            float4 h = ph[u], o = pl[u];
-            df_add(h.x, o.x, vm[4 * u + 0], vc[4 * u + 0]);
-            df_add(h.y, o.y, vm[4 * u + 1], vc[4 * u + 1]);
-            df_add(h.z, o.z, vm[4 * u + 2], vc[4 * u + 2]);
-            df_add(h.w, o.w, vm[4 * u + 3], vc[4 * u + 3]);
-            ph[u] = h;
-            pl[u] = o;
+            float4 &hh = h[4 * q + u], &oo = o[4 * q + u];
+            df_add(hh.x, oo.x, vm[4 * u + 0], vc[4 * u + 0]);
+            df_add(hh.y, oo.y, vm[4 * u + 1], vc[4 * u + 1]);
+            df_add(hh.z, oo.z, vm[4 * u + 2], vc[4 * u + 2]);
+            df_add(hh.w, oo.w, vm[4 * u + 3], vc[4 * u + 3]);
         }
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        ph[u] = h[u];
+        pl[u] = o[u];
     }
 }
 
