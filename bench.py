@@ -40,13 +40,13 @@ PRECISIONS = ("fp32", "fp64", "fp32_dfgram")
 # DRAM traffic of one SpMM pass (dram__bytes_read.sum + dram__bytes_write.sum),
 # averaged over the q = 5 schedule (3 passes with A, 2 with A^T).  The headline
 # workload is too large for a multi-metric capture, so the counters come from
-# the same generator at 1,000,000 x 320,000 (40.0M nnz, the same 320,000-row
-# gathered block): the A pass read 2,387 MB and wrote 475 MB, and each of the
-# A^T pass's 131,072-row panels read ~385 MB and wrote ~135 MB.  Scaled to the
-# full pass (A: by the 12.0x entries; A^T: by 92 panels instead of 8) that is
-# 34.3 GB and 47.8 GB.  Valid only while the SpMM kernels are unchanged since
-# that capture.
-NCU_SPMM_TRAFFIC = {(WORKLOAD, "f32", 5): (3 * 34.3e9 + 2 * 47.8e9) / 5}
+# the same generator at 1,000,000 x 320,000 (40.0M nnz, the same 262,144-row
+# panels of the gathered block): the A pass read 2,450 MB and wrote 496 MB
+# (2,944 MB on average over its two launches), and the A^T pass's four panel
+# launches 6,114 MB in all (~1,665 MB per full panel).  Scaled to the full
+# passes by their entries (x 12.0): 35.3 GB and 73.3 GB.  Valid only while the
+# SpMM kernels are unchanged since that capture.
+NCU_SPMM_TRAFFIC = {(WORKLOAD, "f32", 5): (3 * 35.31e9 + 2 * 73.34e9) / 5}
 # Rows of the headline workload the oracle runs on for the CPU baseline.
 ORACLE_SAMPLE_ROWS = {WORKLOAD: 500_000}
 

@@ -43,9 +43,14 @@ constexpr int kAtTpitch = 33;                   // floats per row of a warp's 32
 constexpr int kAtTbuf = (kAtThreads / 32) * 32 * kAtTpitch * 4;  // 33 KiB
 constexpr int kAtSmem = kAtBytesB + 2 * kAtStage + kAtRawStages * kAtRaw + kAtTbuf + 64;
 
-// Chunk c (columns 32 c ..) of the tile at row0 into a raw stage (row-major,
-// 32 floats a row): thread t copies 16-byte groups t, t + 256, t + 512,
-// t + 768 (row = group / 8); parts past row R or column l are zero-filled.
+// A raw stage holds a chunk row-major, 32 floats (eight 16-byte groups) a
+// row, group j of row r stored in slot j ^ (r % 8) of the row, so that the
+// split's reads of 8 rows x 4 column groups per warp spread over all banks.
+__device__ inline int raw_slot(int r, int j16) { return r * kAtKc + 4 * (j16 ^ (r & 7)); }
+
+// Chunk c (columns 32 c ..) of the tile at row0 into a raw stage: thread t
+// copies 16-byte groups t, t + 256, t + 512, t + 768 (row = group / 8);
+// parts past row R or column l are zero-filled.
 __device__ inline void at_fetch(const float *__restrict__ M, int64_t ldm, int64_t R, int l, int64_t row0, int c,
                                 uint32_t raw) {
 #pragma unroll
@@ -55,8 +60,8 @@ __device__ inline void at_fetch(const float *__restrict__ M, int64_t ldm, int64_
         const int64_t row = row0 + r;
         const int k0 = c * kAtKc + j;
         const int valid = (row < R && k0 < l) ? min(4, l - k0) : 0;
-        cp_async16_zfill(raw + (uint32_t)(r * kAtKc + j) * 4, valid ? (const void *)(M + row * ldm + k0) : (const void *)M,
-                         4 * valid);
+        cp_async16_zfill(raw + (uint32_t)raw_slot(r, it & 7) * 4,
+                         valid ? (const void *)(M + row * ldm + k0) : (const void *)M, 4 * valid);
     }
 }
 
@@ -67,8 +72,8 @@ __device__ inline void at_split(const float *__restrict__ raw, unsigned char *st
     for (int u = 0; u < 2; ++u) {
         const int it = threadIdx.x + u * kAtThreads;
         const int r = it >> 2, g = it & 3;
-        const float4 x0 = *reinterpret_cast<const float4 *>(raw + r * kAtKc + 8 * g);
-        const float4 x1 = *reinterpret_cast<const float4 *>(raw + r * kAtKc + 8 * g + 4);
+        const float4 x0 = *reinterpret_cast<const float4 *>(raw + raw_slot(r, 2 * g));
+        const float4 x1 = *reinterpret_cast<const float4 *>(raw + raw_slot(r, 2 * g + 1));
         const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
         __align__(16) __nv_bfloat16 hh[8], mm[8], ss[8];
 #pragma unroll
