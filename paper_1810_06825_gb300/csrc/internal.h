@@ -53,6 +53,7 @@ struct SpmmPlan {
     size_t charged = 0;             // bytes charged to budget
     bool skip_empty = false;        // leave empty rows out (their output rows are not written)
     int64_t group_stride = 0;       // no group holds rows r, r' with r / stride != r' / stride (0: no limit)
+    int group_target = 0;           // entries per group, a multiple of 32 (0: the writing launches' default)
     void free_all();
 };
 

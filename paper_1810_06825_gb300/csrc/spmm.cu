@@ -51,15 +51,20 @@ static_assert(FRPCA_SPMM_BATCH == 4 || FRPCA_SPMM_BATCH == 8 || FRPCA_SPMM_BATCH
 static_assert(FRPCA_SPMM_BATCH_ACC == 4 || FRPCA_SPMM_BATCH_ACC == 8 || FRPCA_SPMM_BATCH_ACC == 16,
               "batch must divide 32");
 // A warp's share of the whole rows: consecutive rows of the plan whose
-// entries, plus kRowCost per row, come to about kGroupTarget (at most 32
-// rows, because every row costs at least kRowCost).  512: 123.3 ms per step
-// against 125.4 with 256 and 128.5 with 128.
+// entries, plus target / 32 per row, come to about `target` (at most 32 rows,
+// because every row costs at least target / 32); the target is a plan's.
+// Measured on the 12M x 320K workload: 512 entries for the accumulating
+// (panel) plans (123.3 ms per step against 125.4 with 256 and 128.5 with 128;
+// 1,024 made the panels slower), 1,024 for the writing plans (the A passes
+// 39.5 ms against 40.2 with 512).
 #ifndef FRPCA_SPMM_GROUP
-#define FRPCA_SPMM_GROUP 512
+#define FRPCA_SPMM_GROUP 1024
 #endif
-constexpr int kGroupTarget = FRPCA_SPMM_GROUP;
-constexpr int kRowCost = kGroupTarget / 32;
-static_assert(kGroupTarget % 32 == 0 && kRowCost >= 1, "group target must be a positive multiple of 32");
+#ifndef FRPCA_SPMM_GROUP_ACC
+#define FRPCA_SPMM_GROUP_ACC 512
+#endif
+static_assert(FRPCA_SPMM_GROUP % 32 == 0 && FRPCA_SPMM_GROUP_ACC % 32 == 0, "group targets: multiples of 32");
+int group_target_of(const SpmmPlan &p) { return p.group_target > 0 ? p.group_target : FRPCA_SPMM_GROUP; }
 
 // Batches of a full 32-entry chunk unrolled into straight-line code: more
 // unrolling saves the loop's index arithmetic but grows the kernel past what
@@ -480,17 +485,18 @@ cudaError_t build_spmm_plan(const DeviceCSR &A, SpmmPlan &plan, cudaStream_t s, 
         }
     }
     lfirst.push_back((int64_t)sstart.size());
-    // Groups: a new one wherever the running cost (entries + kRowCost per
-    // row) enters a new multiple of kGroupTarget, or the row enters a new
+    // Groups: a new one wherever the running cost (entries + target / 32 per
+    // row) enters a new multiple of the target, or the row enters a new
     // stride block.
     std::vector<int64_t> gfirst;
+    const int64_t T = group_target_of(plan);
     int64_t cost = 0, prev = 0;  // running cost before row i and before row i - 1
     for (size_t i = 0; i < shorts.size(); ++i) {
         const int64_t g = plan.group_stride;
-        if (i == 0 || cost / kGroupTarget != prev / kGroupTarget || (g > 0 && shorts[i] / g != shorts[i - 1] / g))
+        if (i == 0 || cost / T != prev / T || (g > 0 && shorts[i] / g != shorts[i - 1] / g))
             gfirst.push_back((int64_t)i);
         prev = cost;
-        cost += shlen[i] + kRowCost;
+        cost += shlen[i] + T / 32;
     }
     plan.n_groups = (int64_t)gfirst.size();
     gfirst.push_back((int64_t)shorts.size());
@@ -569,19 +575,20 @@ __global__ void plan_fill_kernel(int64_t m, const int64_t *__restrict__ rowptr, 
     }
 }
 
-// Groups of whole rows.  Cost of list entry i: its entries plus kRowCost.
-__global__ void group_cost_kernel(int64_t n, const int32_t *__restrict__ short_len, int32_t *__restrict__ cost) {
+// Groups of whole rows.  Cost of list entry i: its entries plus target / 32.
+__global__ void group_cost_kernel(int64_t n, const int32_t *__restrict__ short_len, int target,
+                                  int32_t *__restrict__ cost) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) cost[i] = short_len[i] + kRowCost;
+    if (i < n) cost[i] = short_len[i] + target / 32;
 }
 
 // 1 where a group starts: the running cost V (exclusive scan of the costs)
-// enters a new multiple of kGroupTarget, or the row a new stride block.
+// enters a new multiple of the target, or the row a new stride block.
 __global__ void group_flag_kernel(int64_t n, const int64_t *__restrict__ V, const int32_t *__restrict__ short_rows,
-                                  int64_t stride, int32_t *__restrict__ flag) {
+                                  int target, int64_t stride, int32_t *__restrict__ flag) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    bool f = i == 0 || V[i] / kGroupTarget != V[i - 1] / kGroupTarget;
+    bool f = i == 0 || V[i] / target != V[i - 1] / target;
     if (stride > 0 && i > 0) f = f || short_rows[i] / stride != short_rows[i - 1] / stride;
     flag[i] = f ? 1 : 0;
 }
@@ -731,14 +738,15 @@ cudaError_t build_spmm_plans_device(const DeviceCSR *const *mats, SpmmPlan *cons
         const int64_t n = plan.n_short;
         if (n == 0) continue;
         const unsigned g = (unsigned)ceil_div(n, 256);
-        group_cost_kernel<<<g, 256, 0, s>>>(n, plan.short_len, q.is_short);
+        group_cost_kernel<<<g, 256, 0, s>>>(n, plan.short_len, group_target_of(plan), q.is_short);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess ||
             (e = exclusive_scan_i32_to_i64(q.is_short, q.short_pos, n, scan_scratch, s)) != cudaSuccess) {
             err = "spmm plan: group pass failed";
             return e;
         }
-        group_flag_kernel<<<g, 256, 0, s>>>(n, q.short_pos, plan.short_rows, plan.group_stride, q.is_long);
+        group_flag_kernel<<<g, 256, 0, s>>>(n, q.short_pos, plan.short_rows, group_target_of(plan),
+                                             plan.group_stride, q.is_long);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess ||
             (e = exclusive_scan_i32_to_i64(q.is_long, q.long_pos, n, scan_scratch, s)) != cudaSuccess ||
@@ -811,6 +819,7 @@ cudaError_t plan_panel_offsets(const SpmmPlan &plan, int64_t npanels, int64_t st
 cudaError_t build_panel_plan(PanelCSR &pc, DevBuf &scratch, DevBuf &scan_scratch, cudaStream_t s, std::string &err) {
     pc.plan.skip_empty = true;
     pc.plan.group_stride = pc.src_rows;
+    pc.plan.group_target = FRPCA_SPMM_GROUP_ACC;
     const DeviceCSR *mats[1] = {&pc.virt};
     SpmmPlan *plans[1] = {&pc.plan};
     cudaError_t e = build_spmm_plans_device(mats, plans, 1, scratch, scan_scratch, s, err);
