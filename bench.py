@@ -45,7 +45,8 @@ PRECISIONS = ("fp32", "fp64", "fp32_dfgram")
 # (2,944 MB on average over its two launches), and the A^T pass's four panel
 # launches 6,114 MB in all (~1,665 MB per full panel).  Scaled to the full
 # passes by their entries (x 12.0): 35.3 GB and 73.3 GB.  Valid only while the
-# SpMM kernels are unchanged since that capture.
+# SpMM kernels are unchanged since that capture (taken with 512-entry groups for
+# every plan; the writing plans now group 1,024 entries, same kernels).
 NCU_SPMM_TRAFFIC = {(WORKLOAD, "f32", 5): (3 * 35.31e9 + 2 * 73.34e9) / 5}
 # Rows of the headline workload the oracle runs on for the CPU baseline.
 ORACLE_SAMPLE_ROWS = {WORKLOAD: 500_000}
