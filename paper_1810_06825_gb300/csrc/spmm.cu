@@ -9,9 +9,11 @@
 // broadcasts them with shuffles and gathers the X rows as 16-byte loads
 // through the read-only path, accumulating in registers in CSR order.  Rows
 // longer than `seg` entries are cut into segments whose partial rows are
-// summed in segment order by a fix-up kernel, so the result is deterministic
-// and no float atomics are used.  The work lists (the plan) are built once
-// per matrix, on the device.
+// summed in segment order (by a fix-up kernel, or in an accumulating launch by
+// the warp that finishes the row's last segment).  An accumulating launch
+// adds each row's sum to the output with L2 reductions, the only addition
+// each output element gets in that launch, so every result is deterministic.
+// The work lists (the plan) are built once per matrix, on the device.
 #include <climits>
 #include <type_traits>
 #include <vector>
@@ -83,8 +85,8 @@ __device__ inline int64_t shfl_i64(int64_t v, int src) { return (int64_t)__shfl_
 // last segment (the arrival count says which; no warp waits for another)
 // adds the row's partial rows in segment order and adds that sum to the row.
 // Out of line, so the gather loop's registers are not sized for it.  (A
-// writing launch leaves the sums to spmm_fixup_kernel: the call cost its
-// gather loop more than the extra launch, which runs once per pass.)
+// writing launch leaves the sums to spmm_fixup_kernel, one small launch per
+// pass; the accumulating panel passes would need one per panel.)
 template <typename T, int NV, bool ACC>
 __device__ __noinline__ void finish_segment(int64_t w, const int32_t *__restrict__ seg_owner, int64_t seg_base,
                                             const int32_t *__restrict__ long_rows,
