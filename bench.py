@@ -41,13 +41,12 @@ PRECISIONS = ("fp32", "fp64", "fp32_dfgram")
 # averaged over the q = 5 schedule (3 passes with A, 2 with A^T).  The headline
 # workload is too large for a multi-metric capture, so the counters come from
 # the same generator at 1,000,000 x 320,000 (40.0M nnz, the same 262,144-row
-# panels of the gathered block): the A pass read 2,450 MB and wrote 496 MB
-# (2,944 MB on average over its two launches), and the A^T pass's four panel
+# panels of the gathered block): the A pass read 2,435 MB and wrote 487 MB
+# (2,921 MB on average over its two launches), and the A^T pass's four panel
 # launches 6,114 MB in all (~1,665 MB per full panel).  Scaled to the full
-# passes by their entries (x 12.0): 35.3 GB and 73.3 GB.  Valid only while the
-# SpMM kernels are unchanged since that capture (taken with 512-entry groups for
-# every plan; the writing plans now group 1,024 entries, same kernels).
-NCU_SPMM_TRAFFIC = {(WORKLOAD, "f32", 5): (3 * 35.31e9 + 2 * 73.34e9) / 5}
+# passes by their entries (x 12.0): 35.05 GB and 73.34 GB.  Valid only while
+# the SpMM kernels and plans are unchanged since that capture.
+NCU_SPMM_TRAFFIC = {(WORKLOAD, "f32", 5): (3 * 35.05e9 + 2 * 73.34e9) / 5}
 # Rows of the headline workload the oracle runs on for the CPU baseline.
 ORACLE_SAMPLE_ROWS = {WORKLOAD: 500_000}
 
